@@ -1,0 +1,25 @@
+"""FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product (``paper_2006_04391_gb300``) never imports it, and it imports nothing
+from the product: the two share no code.
+
+Contents
+--------
+* ``material`` -- ctypes wrappers of ``gsm_oracle.cpp``: the implicit-Euler
+  GSM update (Sec. 4.1, Eq. implicit_euler and Eq. tangent_formula of
+  AutoMat, arXiv 2006.04391), hand-derived potentials and an independent
+  radial return (the conventional strategy of Sec. 4).
+* ``ms`` -- the Moulinec-Suquet basic scheme (cited by the paper in Sec. 1 and
+  Sec. 3 "Material Law Evaluations") written with ``numpy.fft``.
+
+Parity with the paper's printed numbers is unpinned (the paper prints no
+field values for a reproducible case); every function is pinned against
+closed forms, finite differences, invariants and special cases instead.
+"""
+from .material import (  # noqa: F401
+    KIND_ELASTIC, KIND_NORTON, lame, update, radial_return, psi, psi_y, psi_yy,
+    phi, phi_v, phi_vv, residual, newton_matrix, incremental_potential, stress,
+    max_threads, P_MATRIX, G_MATRIX,
+)

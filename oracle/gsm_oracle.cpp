@@ -1,0 +1,567 @@
+// FP64 CPU oracle for the implicit-Euler update of a generalized standard
+// material (GSM) -- TEST INFRASTRUCTURE ONLY.
+//
+// Only the test suite, the smoke check and the CPU-baseline leg of the
+// benchmark may load this library.  It shares no code with the CUDA path: all
+// derivatives below are derived by hand (no automatic differentiation), the
+// linear algebra is written out, and the data layout is array-of-structs.
+//
+// What it computes (paper: AutoMat, Bluehdorn/Gauger/Kabel, arXiv 2006.04391):
+//   * Sec. 2, Eq. (gsm_sigma): sigma = d psi / d eps.
+//   * Sec. 4.1, Eq. (implicit_euler): one implicit Euler step for the internal
+//     variables, solved by Newton.  We use the dissipation (dual) form of the
+//     evolution law, d psi/dz (eps, z) + d phi/dzdot ((z - z_n)/h) = 0, which
+//     for a convex dual pair (Psi = phi*) has the same solution as the force-
+//     potential form of Eq. (gsm_internal).  Sec. 2 states that the dual
+//     potential exists but is not used in the paper; the Norton phi below is
+//     the exact dual of the paper's Psi of Eq. (michel_suquet_psi) with
+//     sigma_Y = 0 and H = 0.
+//   * Sec. 4.1, Eq. (tangent_formula): consistent tangent by the implicit
+//     function theorem, C_t = psi_ee + psi_ey dy/deps, K dy/deps = -psi_ye.
+//   * Sec. 4 (conventional strategy, Simo-Hughes radial return): an
+//     independent scalar reduction used only as a pin of the generic solver.
+//
+// Conventions (Sec. 3 uses Voigt notation; H = diag(H,H,H,H/2,H/2,H/2) in
+// Eq. (michel_suquet_omega) fixes engineering shears for strain vectors):
+//   strain-like  (e11, e22, e33, g23, g13, g12), g_ij = 2 e_ij
+//   stress-like  (s11, s22, s33, s23, s13, s12)
+//   internal variable z = eps_vp, deviatoric (Sec. 6: one component is
+//   eliminated), unknowns y = (z11, z22, g23, g13, g12), z33 = -z11 - z22,
+//   i.e. z = P y with the 6x5 matrix P below.
+//
+// Parity with the paper's own numbers is unpinned: the paper prints no field
+// values for a reproducible case.  Every function here is pinned in the tests
+// against closed forms, finite differences, invariants and an independent
+// radial return (see tests/test_oracle_material.py).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------- constants
+
+// z = P y: deviatoric viscoplastic strain from its 5 independent components.
+const double P[6][5] = {
+    {1, 0, 0, 0, 0},
+    {0, 1, 0, 0, 0},
+    {-1, -1, 0, 0, 0},
+    {0, 0, 1, 0, 0},
+    {0, 0, 0, 1, 0},
+    {0, 0, 0, 0, 1},
+};
+
+// Equivalent strain rate |v|_eq^2 = (2/3) zdot:zdot written on the Voigt
+// vector with engineering shears: weights 2/3 on normal, 1/3 on shear entries.
+const double W[6] = {2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};
+
+struct Law {
+  int kind;         // 0 = linear elastic, 1 = elastic + deviatoric Norton viscoplastic
+  double lam, mu;   // Lame constants from (E, nu)
+  double sigma0;    // drag stress
+  double edot0;     // reference strain rate
+  double n;         // rate sensitivity exponent
+  double C[6][6];   // isotropic stiffness in Voigt notation
+  double G[5][5];   // P^T diag(W) P
+};
+
+void make_law(int kind, const double* prm, Law* L) {
+  const double E = prm[0], nu = prm[1];
+  L->kind = kind;
+  L->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  L->mu = E / (2.0 * (1.0 + nu));
+  L->sigma0 = kind == 1 ? prm[2] : 0.0;
+  L->edot0 = kind == 1 ? prm[3] : 1.0;
+  L->n = kind == 1 ? prm[4] : 1.0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) L->C[i][j] = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) L->C[i][j] = L->lam;
+    L->C[i][i] = L->lam + 2.0 * L->mu;
+    L->C[3 + i][3 + i] = L->mu;
+  }
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      double s = 0.0;
+      for (int i = 0; i < 6; ++i) s += P[i][a] * W[i] * P[i][b];
+      L->G[a][b] = s;
+    }
+}
+
+// ------------------------------------------------------------ free energy psi
+// psi(eps, y) = 1/2 (eps - P y)^T C (eps - P y)   (Eq. michel_suquet_omega, H = 0)
+
+void elastic_strain(const double eps[6], const double y[5], double e[6]) {
+  for (int i = 0; i < 6; ++i) {
+    double pz = 0.0;
+    for (int a = 0; a < 5; ++a) pz += P[i][a] * y[a];
+    e[i] = eps[i] - pz;
+  }
+}
+
+void stress(const Law& L, const double eps[6], const double y[5], double sig[6]) {
+  double e[6];
+  elastic_strain(eps, y, e);
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 6; ++j) s += L.C[i][j] * e[j];
+    sig[i] = s;
+  }
+}
+
+double psi(const Law& L, const double eps[6], const double y[5]) {
+  double e[6], sig[6];
+  elastic_strain(eps, y, e);
+  stress(L, eps, y, sig);
+  double s = 0.0;
+  for (int i = 0; i < 6; ++i) s += e[i] * sig[i];
+  return 0.5 * s;
+}
+
+// d psi / d y = -P^T C (eps - P y) = -P^T sigma
+void psi_y(const Law& L, const double eps[6], const double y[5], double g[5]) {
+  double sig[6];
+  stress(L, eps, y, sig);
+  for (int a = 0; a < 5; ++a) {
+    double s = 0.0;
+    for (int i = 0; i < 6; ++i) s += P[i][a] * sig[i];
+    g[a] = -s;
+  }
+}
+
+// d2 psi / dy2 = P^T C P (constant)
+void psi_yy(const Law& L, double H[5][5]) {
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      double s = 0.0;
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) s += P[i][a] * L.C[i][j] * P[j][b];
+      H[a][b] = s;
+    }
+}
+
+// ------------------------------------------------------- dissipation phi (Norton)
+// phi(v) = sigma0 edot0 n/(n+1) (s/edot0)^((n+1)/n),  s = sqrt(v^T G v)
+// (convex dual of the paper's Psi, Eq. michel_suquet_psi, at sigma_Y = 0, H = 0)
+
+double eqrate(const Law& L, const double v[5], double Gv[5]) {
+  double q = 0.0;
+  for (int a = 0; a < 5; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < 5; ++b) s += L.G[a][b] * v[b];
+    Gv[a] = s;
+    q += v[a] * s;
+  }
+  return std::sqrt(q);
+}
+
+double phi(const Law& L, const double v[5]) {
+  double Gv[5];
+  const double s = eqrate(L, v, Gv);
+  return L.sigma0 * L.edot0 * L.n / (L.n + 1.0) * std::pow(s / L.edot0, (L.n + 1.0) / L.n);
+}
+
+// phi_v = sigma0 edot0^(-1/n) s^(1/n - 1) G v   (= 0 at v = 0 by continuity)
+void phi_v(const Law& L, const double v[5], double g[5]) {
+  double Gv[5];
+  const double s = eqrate(L, v, Gv);
+  if (s == 0.0) {
+    for (int a = 0; a < 5; ++a) g[a] = 0.0;
+    return;
+  }
+  const double c = L.sigma0 * std::pow(L.edot0, -1.0 / L.n) * std::pow(s, 1.0 / L.n - 1.0);
+  for (int a = 0; a < 5; ++a) g[a] = c * Gv[a];
+}
+
+// phi_vv = sigma0 edot0^(-1/n) [ s^(1/n-1) G + (1/n - 1) s^(1/n-3) (Gv)(Gv)^T ]
+// At s = 0 it is finite only for n = 1; returns false otherwise.
+bool phi_vv(const Law& L, const double v[5], double H[5][5]) {
+  double Gv[5];
+  const double s = eqrate(L, v, Gv);
+  const double k = L.sigma0 * std::pow(L.edot0, -1.0 / L.n);
+  if (s == 0.0) {
+    if (L.n != 1.0) return false;
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) H[a][b] = k * L.G[a][b];
+    return true;
+  }
+  const double c1 = k * std::pow(s, 1.0 / L.n - 1.0);
+  const double c2 = k * (1.0 / L.n - 1.0) * std::pow(s, 1.0 / L.n - 3.0);
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) H[a][b] = c1 * L.G[a][b] + c2 * Gv[a] * Gv[b];
+  return true;
+}
+
+// ------------------------------------------------- implicit Euler step pieces
+// Incremental potential Pi(y) = psi(eps, y) + h phi((y - y_n)/h); its
+// stationarity condition R(y) = psi_y + phi_v((y - y_n)/h) = 0 is the dual
+// form of Eq. (implicit_euler); Newton matrix K = psi_yy + phi_vv / h.
+
+void rate(const double y[5], const double yn[5], double h, double v[5]) {
+  for (int a = 0; a < 5; ++a) v[a] = (y[a] - yn[a]) / h;
+}
+
+double Pi(const Law& L, const double eps[6], const double y[5], const double yn[5], double h) {
+  double v[5];
+  rate(y, yn, h, v);
+  return psi(L, eps, y) + h * phi(L, v);
+}
+
+void residual(const Law& L, const double eps[6], const double y[5], const double yn[5], double h,
+              double R[5]) {
+  double v[5], g1[5], g2[5];
+  rate(y, yn, h, v);
+  psi_y(L, eps, y, g1);
+  phi_v(L, v, g2);
+  for (int a = 0; a < 5; ++a) R[a] = g1[a] + g2[a];
+}
+
+bool newton_matrix(const Law& L, const double y[5], const double yn[5], double h, double K[5][5]) {
+  double v[5], H1[5][5], H2[5][5];
+  rate(y, yn, h, v);
+  psi_yy(L, H1);
+  if (!phi_vv(L, v, H2)) return false;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) K[a][b] = H1[a][b] + H2[a][b] / h;
+  return true;
+}
+
+// Dense Cholesky solve of A x = b (A symmetric positive definite, n <= 6).
+bool chol_solve(int n, const double* A, const double* b, double* x) {
+  double Lm[36];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= Lm[i * n + k] * Lm[j * n + k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        Lm[i * n + i] = std::sqrt(s);
+      } else {
+        Lm[i * n + j] = s / Lm[j * n + j];
+      }
+    }
+  double t[6];
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= Lm[i * n + k] * t[k];
+    t[i] = s / Lm[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = t[i];
+    for (int k = i + 1; k < n; ++k) s -= Lm[k * n + i] * x[k];
+    x[i] = s / Lm[i * n + i];
+  }
+  return true;
+}
+
+double maxabs(int n, const double* a) {
+  double m = 0.0;
+  for (int i = 0; i < n; ++i) m = std::fmax(m, std::fabs(a[i]));
+  return m;
+}
+
+// Per-voxel diagnostics: line-search iterations, Newton iterations, flags.
+enum { F_CONVERGED = 1, F_NONFINITE = 2, F_CAP = 4, F_NOT_SPD = 8 };
+struct Info {
+  int line_iters, newton_iters, flags;
+};
+
+// ------------------------------------------------ the implicit Euler update
+// Newton start (reading of the singular dual form at y = y_n, where
+// phi_vv ~ s^(1/n - 1) is unbounded for n > 1; the force-potential Newton of
+// Sec. 4.1 starts at a_n and is regular there):
+//   1. if psi_y(eps, y_n) = 0, then y = y_n solves R = 0;
+//   2. psi-Newton predictor d = -psi_yy^{-1} psi_y(eps, y_n);
+//   3. minimise Pi exactly on the segment y_n + theta d, theta in (0, 1]:
+//      g(theta) = d.R(y_n + theta d) is increasing (Pi convex), g(0+) < 0,
+//      g(1) > 0; safeguarded Newton on g with bisection fallback;
+//   4. full Newton on R with Armijo backtracking on Pi until
+//      |dy|_inf <= 1e-14 max(1, |y|_inf); at most 50 iterations.
+void update_vp(const Law& L, const double eps[6], const double zn[6], double h, double sig[6],
+               double z[6], double Ct[6][6], Info* info) {
+  info->line_iters = 0;
+  info->newton_iters = 0;
+  info->flags = 0;
+  double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
+  double y[5];
+  for (int a = 0; a < 5; ++a) y[a] = yn[a];
+
+  double r0[5];
+  psi_y(L, eps, yn, r0);
+  bool relaxed = maxabs(5, r0) > 0.0;
+  if (relaxed) {
+    double H[5][5], d[5], mr0[5];
+    psi_yy(L, H);
+    for (int a = 0; a < 5; ++a) mr0[a] = -r0[a];
+    if (!chol_solve(5, &H[0][0], mr0, d)) info->flags |= F_NOT_SPD;
+
+    auto g_of = [&](double th, double* gp) {
+      double yt[5], R[5], K[5][5];
+      for (int a = 0; a < 5; ++a) yt[a] = yn[a] + th * d[a];
+      residual(L, eps, yt, yn, h, R);
+      newton_matrix(L, yt, yn, h, K);
+      double g = 0.0, q = 0.0;
+      for (int a = 0; a < 5; ++a) {
+        g += d[a] * R[a];
+        for (int b = 0; b < 5; ++b) q += d[a] * K[a][b] * d[b];
+      }
+      *gp = q;
+      return g;
+    };
+    double lo = 0.0, hi = 1.0, th = 1.0;
+    for (int it = 0; it < 400; ++it) {
+      ++info->line_iters;
+      double gp;
+      const double g = g_of(th, &gp);
+      if (g == 0.0) break;
+      if (g > 0.0) hi = th; else lo = th;
+      double tn = th - g / gp;
+      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+      if (tn == th || !(hi - lo > 4.0 * std::numeric_limits<double>::epsilon() * hi)) {
+        th = tn;
+        break;
+      }
+      th = tn;
+    }
+    for (int a = 0; a < 5; ++a) y[a] = yn[a] + th * d[a];
+
+    for (int k = 0; k < 50; ++k) {
+      ++info->newton_iters;
+      double R[5], K[5][5], dy[5], mR[5];
+      residual(L, eps, y, yn, h, R);
+      if (!newton_matrix(L, y, yn, h, K)) { info->flags |= F_NOT_SPD; break; }
+      for (int a = 0; a < 5; ++a) mR[a] = -R[a];
+      if (!chol_solve(5, &K[0][0], mR, dy)) { info->flags |= F_NOT_SPD; break; }
+      const bool small = maxabs(5, dy) <= 1e-14 * std::fmax(1.0, maxabs(5, y));
+      double alpha = 1.0;
+      if (!small) {
+        const double P0 = Pi(L, eps, y, yn, h);
+        double slope = 0.0;
+        for (int a = 0; a < 5; ++a) slope += R[a] * dy[a];
+        for (int ls = 0; ls < 40; ++ls) {
+          double yt[5];
+          for (int a = 0; a < 5; ++a) yt[a] = y[a] + alpha * dy[a];
+          const double P1 = Pi(L, eps, yt, yn, h);
+          if (P1 <= P0 + 1e-4 * alpha * slope + 8.0 * std::numeric_limits<double>::epsilon() * std::fabs(P0))
+            break;
+          alpha *= 0.5;
+        }
+      }
+      for (int a = 0; a < 5; ++a) y[a] += alpha * dy[a];
+      if (small) { info->flags |= F_CONVERGED; break; }
+    }
+    if (!(info->flags & F_CONVERGED) && !(info->flags & F_NOT_SPD)) info->flags |= F_CAP;
+  } else {
+    info->flags |= F_CONVERGED;
+  }
+
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+    for (int a = 0; a < 5; ++a) s += P[i][a] * y[a];
+    z[i] = s;
+  }
+  stress(L, eps, y, sig);
+
+  if (Ct) {
+    // C_t = C - C P K^{-1} P^T C  (Eq. tangent_formula with psi_ee = C,
+    // psi_ey = -C P, K dy/deps = -psi_ye = P^T C).  Where K is unbounded
+    // (y = y_n with n > 1) dy/deps = 0 and C_t = C.
+    double K[5][5];
+    const bool finite_K = newton_matrix(L, y, yn, h, K);
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) Ct[i][j] = L.C[i][j];
+    if (finite_K) {
+      double PtC[5][6];
+      for (int a = 0; a < 5; ++a)
+        for (int j = 0; j < 6; ++j) {
+          double s = 0.0;
+          for (int i = 0; i < 6; ++i) s += P[i][a] * L.C[i][j];
+          PtC[a][j] = s;
+        }
+      for (int j = 0; j < 6; ++j) {
+        double col[5], dyde[5];
+        for (int a = 0; a < 5; ++a) col[a] = PtC[a][j];
+        if (!chol_solve(5, &K[0][0], col, dyde)) { info->flags |= F_NOT_SPD; continue; }
+        for (int i = 0; i < 6; ++i) {
+          double s = 0.0;
+          for (int a = 0; a < 5; ++a) s += PtC[a][i] * dyde[a];  // (C P)_ia = (P^T C)_ai
+          Ct[i][j] -= s;
+        }
+      }
+    }
+  }
+  bool fin = true;
+  for (int i = 0; i < 6; ++i) fin = fin && std::isfinite(sig[i]) && std::isfinite(z[i]);
+  if (!fin) info->flags |= F_NONFINITE;
+}
+
+void update_elastic(const Law& L, const double eps[6], double sig[6], double Ct[6][6]) {
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 6; ++j) s += L.C[i][j] * eps[j];
+    sig[i] = s;
+  }
+  if (Ct)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) Ct[i][j] = L.C[i][j];
+}
+
+// --------------------------------------------- independent radial return
+// The paper's conventional strategy (Sec. 4, Simo-Hughes): with a deviatoric
+// flow direction the implicit Euler step reduces to one scalar equation for
+// the equivalent viscoplastic increment dp,
+//   sigma_eq_trial - 3 mu dp = sigma0 (dp / (h edot0))^(1/n),
+// after which z = z_n + 3/2 dp s_trial / sigma_eq_trial.  Written on 3x3
+// tensors (not on the 5-vector y) so that it shares nothing with update_vp.
+void voigt_to_tensor(const double v[6], double T[3][3], bool engineering) {
+  const double f = engineering ? 0.5 : 1.0;
+  T[0][0] = v[0]; T[1][1] = v[1]; T[2][2] = v[2];
+  T[1][2] = T[2][1] = f * v[3];
+  T[0][2] = T[2][0] = f * v[4];
+  T[0][1] = T[1][0] = f * v[5];
+}
+
+void tensor_to_voigt(const double T[3][3], double v[6], bool engineering) {
+  const double f = engineering ? 2.0 : 1.0;
+  v[0] = T[0][0]; v[1] = T[1][1]; v[2] = T[2][2];
+  v[3] = f * T[1][2]; v[4] = f * T[0][2]; v[5] = f * T[0][1];
+}
+
+void radial_return(const Law& L, const double eps[6], const double zn[6], double h, double sig[6],
+                   double z[6]) {
+  double Et[3][3], Zt[3][3], Ee[3][3], S[3][3], Sd[3][3];
+  voigt_to_tensor(eps, Et, true);
+  voigt_to_tensor(zn, Zt, true);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Ee[i][j] = Et[i][j] - Zt[i][j];
+  const double tr = Ee[0][0] + Ee[1][1] + Ee[2][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = 2.0 * L.mu * Ee[i][j] + (i == j ? L.lam * tr : 0.0);
+  const double p = (S[0][0] + S[1][1] + S[2][2]) / 3.0;
+  double ss = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Sd[i][j] = S[i][j] - (i == j ? p : 0.0);
+      ss += Sd[i][j] * Sd[i][j];
+    }
+  const double seq = std::sqrt(1.5 * ss);
+  double dp = 0.0;
+  if (seq > 0.0) {
+    // f(dp) = seq - 3 mu dp - sigma0 (dp/(h edot0))^(1/n): decreasing, f(0) > 0,
+    // f(seq / 3mu) < 0.  Bracketed Newton with bisection fallback.
+    auto f = [&](double x, double* fp) {
+      const double r = std::pow(x / (h * L.edot0), 1.0 / L.n);
+      *fp = -3.0 * L.mu - (x > 0.0 ? L.sigma0 * r / (L.n * x) : std::numeric_limits<double>::infinity());
+      return seq - 3.0 * L.mu * x - L.sigma0 * r;
+    };
+    double lo = 0.0, hi = seq / (3.0 * L.mu), x = hi;
+    for (int it = 0; it < 400; ++it) {
+      double fp;
+      const double fx = f(x, &fp);
+      if (fx == 0.0) break;
+      if (fx > 0.0) lo = x; else hi = x;
+      double xn = x - fx / fp;
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      if (xn == x || !(hi - lo > 4.0 * std::numeric_limits<double>::epsilon() * hi)) { x = xn; break; }
+      x = xn;
+    }
+    dp = x;
+  }
+  double Zn1[3][3], Sig[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double dz = seq > 0.0 ? 1.5 * dp * Sd[i][j] / seq : 0.0;
+      Zn1[i][j] = Zt[i][j] + dz;
+      Sig[i][j] = S[i][j] - 2.0 * L.mu * dz;
+    }
+  tensor_to_voigt(Zn1, z, true);
+  tensor_to_voigt(Sig, sig, false);
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+// Field arrays are array-of-structs: eps[n][6], z_n[n][6], sigma[n][6], z[n][6],
+// tangent[n][6][6] (may be NULL), info[n][3] (may be NULL).
+// params = {E, nu, sigma0, edot0, n}; kind 0 = elastic, 1 = elastic-viscoplastic.
+
+extern "C" {
+
+int ora_max_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int ora_update(int kind, const double* params, int64_t n, const double* eps, const double* zn,
+               double h, double* sigma, double* z, double* tangent, int32_t* info) {
+  if (kind != 0 && kind != 1) return -1;
+  Law L;
+  make_law(kind, params, &L);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    double(*Ct)[6] = tangent ? reinterpret_cast<double(*)[6]>(tangent + 36 * i) : nullptr;
+    if (kind == 0) {
+      update_elastic(L, eps + 6 * i, sigma + 6 * i, Ct);
+      for (int k = 0; k < 6; ++k) z[6 * i + k] = zn[6 * i + k];
+      if (info) { info[3 * i] = 0; info[3 * i + 1] = 0; info[3 * i + 2] = F_CONVERGED; }
+    } else {
+      Info inf;
+      update_vp(L, eps + 6 * i, zn + 6 * i, h, sigma + 6 * i, z + 6 * i, Ct, &inf);
+      if (info) { info[3 * i] = inf.line_iters; info[3 * i + 1] = inf.newton_iters; info[3 * i + 2] = inf.flags; }
+    }
+  }
+  return 0;
+}
+
+int ora_radial_return(const double* params, int64_t n, const double* eps, const double* zn, double h,
+                      double* sigma, double* z) {
+  Law L;
+  make_law(1, params, &L);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) radial_return(L, eps + 6 * i, zn + 6 * i, h, sigma + 6 * i, z + 6 * i);
+  return 0;
+}
+
+// Single-point accessors of the hand-derived potentials (used by the
+// finite-difference and invariant pins).
+double ora_psi(const double* params, const double* eps, const double* y) {
+  Law L; make_law(1, params, &L); return psi(L, eps, y);
+}
+void ora_psi_y(const double* params, const double* eps, const double* y, double* g) {
+  Law L; make_law(1, params, &L); psi_y(L, eps, y, g);
+}
+void ora_psi_yy(const double* params, double* H) {
+  Law L; make_law(1, params, &L); psi_yy(L, reinterpret_cast<double(*)[5]>(H));
+}
+void ora_stress(const double* params, const double* eps, const double* y, double* sig) {
+  Law L; make_law(1, params, &L); stress(L, eps, y, sig);
+}
+double ora_phi(const double* params, const double* v) {
+  Law L; make_law(1, params, &L); return phi(L, v);
+}
+void ora_phi_v(const double* params, const double* v, double* g) {
+  Law L; make_law(1, params, &L); phi_v(L, v, g);
+}
+int ora_phi_vv(const double* params, const double* v, double* H) {
+  Law L; make_law(1, params, &L); return phi_vv(L, v, reinterpret_cast<double(*)[5]>(H)) ? 0 : -1;
+}
+void ora_residual(const double* params, const double* eps, const double* y, const double* yn, double h,
+                  double* R) {
+  Law L; make_law(1, params, &L); residual(L, eps, y, yn, h, R);
+}
+int ora_newton_matrix(const double* params, const double* y, const double* yn, double h, double* K) {
+  Law L; make_law(1, params, &L); return newton_matrix(L, y, yn, h, reinterpret_cast<double(*)[5]>(K)) ? 0 : -1;
+}
+double ora_Pi(const double* params, const double* eps, const double* y, const double* yn, double h) {
+  Law L; make_law(1, params, &L); return Pi(L, eps, y, yn, h);
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+"""ctypes wrappers around the C++ FP64 oracle (test infrastructure only).
+
+Array layout is array-of-structs: ``eps[n, 6]``, ``z_n[n, 6]``.  Voigt order
+(11, 22, 33, 23, 13, 12); strain-like vectors carry engineering shears,
+stress-like vectors tensor shears (Sec. 3 of the paper: Voigt notation, and
+H = diag(H,H,H,H/2,H/2,H/2) in Eq. michel_suquet_omega).
+
+``params`` is ``(E, nu, sigma0, edot0, n)`` for the elastic-viscoplastic
+(Norton) law and ``(E, nu)`` for the linear-elastic law.
+"""
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+KIND_ELASTIC = 0
+KIND_NORTON = 1
+
+# z = P y with y = (z11, z22, g23, g13, g12) and z33 = -z11 - z22 (Sec. 6:
+# one component of the deviatoric viscoplastic strain is eliminated).
+P_MATRIX = np.array([
+    [1, 0, 0, 0, 0],
+    [0, 1, 0, 0, 0],
+    [-1, -1, 0, 0, 0],
+    [0, 0, 1, 0, 0],
+    [0, 0, 0, 1, 0],
+    [0, 0, 0, 0, 1],
+], dtype=np.float64)
+_W = np.diag([2 / 3, 2 / 3, 2 / 3, 1 / 3, 1 / 3, 1 / 3])
+G_MATRIX = P_MATRIX.T @ _W @ P_MATRIX
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.ora_update.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp, ctypes.c_double,
+                                   _dp, _dp, _dp, _ip]
+        lib.ora_update.restype = ctypes.c_int
+        lib.ora_radial_return.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, _dp]
+        lib.ora_psi.argtypes = [_dp, _dp, _dp]
+        lib.ora_psi.restype = ctypes.c_double
+        lib.ora_psi_y.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_psi_yy.argtypes = [_dp, _dp]
+        lib.ora_stress.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_phi.argtypes = [_dp, _dp]
+        lib.ora_phi.restype = ctypes.c_double
+        lib.ora_phi_v.argtypes = [_dp, _dp, _dp]
+        lib.ora_phi_vv.argtypes = [_dp, _dp, _dp]
+        lib.ora_phi_vv.restype = ctypes.c_int
+        lib.ora_residual.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, _dp]
+        lib.ora_newton_matrix.argtypes = [_dp, _dp, _dp, ctypes.c_double, _dp]
+        lib.ora_newton_matrix.restype = ctypes.c_int
+        lib.ora_Pi.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double]
+        lib.ora_Pi.restype = ctypes.c_double
+        lib.ora_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _params(params):
+    p = list(params) + [0.0] * (5 - len(params))
+    if len(params) == 2:
+        p[3] = 1.0
+        p[4] = 1.0
+    return _f64(p)
+
+
+def max_threads() -> int:
+    """Number of OpenMP threads the oracle's voxel loops use."""
+    return int(_load().ora_max_threads())
+
+
+def lame(E, nu):
+    """Lame constants (lambda, mu) of an isotropic material."""
+    return E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+
+
+def update(kind, params, eps, z_n, h, tangent=False, info=False):
+    """Implicit-Euler GSM update of ``n`` independent voxels (Sec. 4.1).
+
+    Returns ``sigma[n,6]``, ``z[n,6]`` and optionally ``C_t[n,6,6]`` (Eq.
+    tangent_formula) and ``info[n,3]`` = (line-search iterations, Newton
+    iterations, flags with 1=converged, 2=non-finite, 4=cap, 8=not SPD).
+    """
+    lib = _load()
+    eps = _f64(eps, (-1, 6))
+    n = eps.shape[0]
+    z_n = _f64(z_n, (n, 6))
+    sig = np.empty((n, 6))
+    z = np.empty((n, 6))
+    Ct = np.empty((n, 6, 6)) if tangent else None
+    inf = np.empty((n, 3), dtype=np.int32) if info else None
+    rc = lib.ora_update(int(kind), _ptr(_params(params)), n, _ptr(eps), _ptr(z_n), float(h),
+                        _ptr(sig), _ptr(z), _ptr(Ct) if tangent else None,
+                        inf.ctypes.data_as(_ip) if info else None)
+    if rc != 0:
+        raise ValueError(f"ora_update failed with code {rc}")
+    out = [sig, z]
+    if tangent:
+        out.append(Ct)
+    if info:
+        out.append(inf)
+    return tuple(out)
+
+
+def radial_return(params, eps, z_n, h):
+    """Conventional scalar radial return (Sec. 4, Simo-Hughes) -- an independent pin."""
+    lib = _load()
+    eps = _f64(eps, (-1, 6))
+    n = eps.shape[0]
+    z_n = _f64(z_n, (n, 6))
+    sig = np.empty((n, 6))
+    z = np.empty((n, 6))
+    lib.ora_radial_return(_ptr(_params(params)), n, _ptr(eps), _ptr(z_n), float(h), _ptr(sig), _ptr(z))
+    return sig, z
+
+
+def psi(params, eps, y):
+    return _load().ora_psi(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)))
+
+
+def psi_y(params, eps, y):
+    g = np.empty(5)
+    _load().ora_psi_y(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)), _ptr(g))
+    return g
+
+
+def psi_yy(params):
+    H = np.empty((5, 5))
+    _load().ora_psi_yy(_ptr(_params(params)), _ptr(H))
+    return H
+
+
+def stress(params, eps, y):
+    s = np.empty(6)
+    _load().ora_stress(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)), _ptr(s))
+    return s
+
+
+def phi(params, v):
+    return _load().ora_phi(_ptr(_params(params)), _ptr(_f64(v)))
+
+
+def phi_v(params, v):
+    g = np.empty(5)
+    _load().ora_phi_v(_ptr(_params(params)), _ptr(_f64(v)), _ptr(g))
+    return g
+
+
+def phi_vv(params, v):
+    H = np.empty((5, 5))
+    rc = _load().ora_phi_vv(_ptr(_params(params)), _ptr(_f64(v)), _ptr(H))
+    return H if rc == 0 else None
+
+
+def residual(params, eps, y, y_n, h):
+    R = np.empty(5)
+    _load().ora_residual(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)), _ptr(_f64(y_n)),
+                         float(h), _ptr(R))
+    return R
+
+
+def newton_matrix(params, y, y_n, h):
+    K = np.empty((5, 5))
+    rc = _load().ora_newton_matrix(_ptr(_params(params)), _ptr(_f64(y)), _ptr(_f64(y_n)), float(h), _ptr(K))
+    return K if rc == 0 else None
+
+
+def incremental_potential(params, eps, y, y_n, h):
+    """Pi(y) = psi(eps, y) + h phi((y - y_n)/h)."""
+    return _load().ora_Pi(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)), _ptr(_f64(y_n)), float(h))
+
+

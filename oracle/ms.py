@@ -1,0 +1,187 @@
+"""Moulinec-Suquet basic scheme in plain numpy, FP64 -- TEST INFRASTRUCTURE ONLY.
+
+The paper drives the material law by the FFT-based basic scheme of Moulinec
+and Suquet (Sec. 1; Sec. 3 "Material Law Evaluations": a reference stiffness
+C^ref, fixed or updated per step, and one material evaluation without tangent
+per iteration and voxel).  The paper cites the scheme without restating its
+formulas; this module writes out the standard scheme:
+
+  * periodic cell [0,1)^3 on an N^3 voxel grid, frequencies xi = 2 pi k,
+    k in {0..ceil(N/2)-1, -floor(N/2)..-1} per axis;
+  * isotropic reference medium (lambda0, mu0) = midpoints of the phases'
+    elastic Lame constants (fixed C^ref, Sec. 3);
+  * Green operator applied to a symmetric tau with q = tau xi:
+      (Gamma0 : tau)_kh = (xi_h q_k + xi_k q_h) / (2 mu0 |xi|^2)
+                          - (lambda0 + mu0) / (mu0 (lambda0 + 2 mu0)) (xi.q) xi_k xi_h / |xi|^4
+  * iteration  eps^(i+1)^(xi) = eps^i^(xi) - Gamma0(xi) : sigma^i^(xi)  (xi != 0),
+               eps^(i+1)^(0)  = N^3 E_k;
+  * equilibrium error e = sqrt(sum_xi |xi . c(xi)|^2) / |<sigma>|_F with
+    c = sigma^ / N^3 (|.|_F the tensor Frobenius norm);
+  * load step k: eps <- eps + (E_k - E_{k-1}) uniformly, iterate until
+    e < tol, then z_n <- z and Sigma_k = <sigma>.
+
+Even-N convention (a reading; the paper is silent): a mode whose index
+vector contains the Nyquist index N/2 together with any other nonzero index
+has no Hermitian-consistent Green operator (xi_i xi_j flips sign between the
+two aliases); there Gamma0 := 0 and the mode is excluded from the error sum.
+Pure-axis Nyquist modes (N/2, 0, 0) etc. keep the exact operator.
+
+Strain-like Voigt vectors carry engineering shears, so the strain update of a
+shear component is 2 (Gamma0 : tau)_ij.
+"""
+import numpy as np
+
+from . import material as M
+
+VOIGT = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def reference_medium(laws):
+    """(lambda0, mu0): midpoints over the phases' elastic Lame constants."""
+    lm = [M.lame(p[1][0], p[1][1]) for p in laws]
+    lams = [a for a, _ in lm]
+    mus = [b for _, b in lm]
+    return 0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus))
+
+
+def wavevectors(N):
+    """Integer frequency vectors k (3, N, N, N) and the mask of excluded modes."""
+    k1 = np.fft.fftfreq(N, d=1.0 / N).round().astype(np.int64)
+    kx, ky, kz = np.meshgrid(k1, k1, k1, indexing="ij")
+    k = np.stack([kx, ky, kz]).astype(np.float64)
+    excluded = np.zeros((N, N, N), dtype=bool)
+    if N % 2 == 0:
+        nyq = [np.abs(c) == N // 2 for c in (kx, ky, kz)]
+        nonzero = [c != 0 for c in (kx, ky, kz)]
+        n_nonzero = nonzero[0].astype(int) + nonzero[1] + nonzero[2]
+        any_nyq = nyq[0] | nyq[1] | nyq[2]
+        excluded = any_nyq & (n_nonzero >= 2)
+    return k, excluded
+
+
+def voigt_to_tensor_field(a, engineering):
+    """(..., 6) Voigt -> (3, 3, ...) symmetric tensor field."""
+    f = 0.5 if engineering else 1.0
+    T = np.empty((3, 3) + a.shape[:-1], dtype=a.dtype)
+    for c, (i, j) in enumerate(VOIGT):
+        s = a[..., c] * (f if i != j else 1.0)
+        T[i, j] = s
+        T[j, i] = s
+    return T
+
+
+def gamma0_apply(tau_hat, lam0, mu0, N):
+    """Gamma0 : tau for every mode; tau_hat (3, 3, N, N, N) complex.
+
+    Returns the strain-like Voigt field (N, N, N, 6) with engineering shears;
+    the zero mode and the excluded Nyquist modes are set to 0.
+    """
+    k, excluded = wavevectors(N)
+    xi = 2.0 * np.pi * k
+    xi2 = (xi ** 2).sum(axis=0)
+    xi2_safe = np.where(xi2 == 0, 1.0, xi2)
+    q = np.einsum("ij...,j...->i...", tau_hat, xi)
+    xq = np.einsum("i...,i...->...", xi, q)
+    a = 1.0 / (2.0 * mu0 * xi2_safe)
+    b = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0)) / xi2_safe ** 2
+    out = np.empty((N, N, N, 6), dtype=np.complex128)
+    for c, (i, j) in enumerate(VOIGT):
+        d = a * (xi[j] * q[i] + xi[i] * q[j]) - b * xq * xi[i] * xi[j]
+        out[..., c] = d if i == j else 2.0 * d
+    kill = (xi2 == 0) | excluded
+    out[kill] = 0.0
+    return out
+
+
+def equilibrium_error(sig_hat, mean_sig, N, floor):
+    """e = sqrt(sum |xi . c|^2) / max(|<sigma>|_F, floor), c = sigma^/N^3."""
+    k, excluded = wavevectors(N)
+    xi = 2.0 * np.pi * k
+    T = voigt_to_tensor_field(np.moveaxis(sig_hat, 0, -1), engineering=False) / N ** 3
+    q = np.einsum("ij...,j...->i...", T, xi)
+    w = (np.abs(q) ** 2).sum(axis=0)
+    w[excluded] = 0.0
+    num = np.sqrt(w.sum())
+    Sm = voigt_to_tensor_field(np.asarray(mean_sig), engineering=False)
+    den = max(np.sqrt((Sm ** 2).sum()), floor)
+    return num / den
+
+
+def material(eps, z_n, phase, laws, h, tangent=False):
+    """One material evaluation of every voxel: laws[p] = (kind, params) for phase p."""
+    n = eps.shape[0]
+    sig = np.empty((n, 6))
+    z = np.empty((n, 6))
+    Ct = np.empty((n, 6, 6)) if tangent else None
+    for p, (kind, params) in enumerate(laws):
+        idx = np.nonzero(phase == p)[0]
+        if idx.size == 0:
+            continue
+        out = M.update(kind, params, eps[idx], z_n[idx], h, tangent=tangent)
+        sig[idx] = out[0]
+        z[idx] = out[1]
+        if tangent:
+            Ct[idx] = out[2]
+    return (sig, z, Ct) if tangent else (sig, z)
+
+
+def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
+          eps0=None, zn0=None, E_prev0=None, record=False):
+    """Load-history solve of the basic scheme.
+
+    phase : (N, N, N) uint8 phase ids, voxel (i, j, k) with k fastest.
+    laws  : list of (kind, params) per phase id.
+    loads : (n_steps, 6) macroscopic strains E_k (engineering shears).
+    hs    : step sizes h_k.
+    forced_iters : optional per-step number of material evaluations to run
+                   regardless of tol (used for iteration-matched parity).
+
+    Returns dict with Sigma (n_steps, 6), iters (n_steps,), errors (list per
+    step), eps and z (N^3, 6) at the end, and the per-step (eps, z) history if
+    ``record``.
+    """
+    phase = np.asarray(phase)
+    N = phase.shape[0]
+    nvox = N ** 3
+    ph = phase.reshape(-1)
+    lam0, mu0 = reference_medium(laws)
+    loads = np.asarray(loads, dtype=np.float64).reshape(-1, 6)
+    eps = np.zeros((nvox, 6)) if eps0 is None else np.array(eps0, dtype=np.float64).reshape(nvox, 6)
+    z_n = np.zeros((nvox, 6)) if zn0 is None else np.array(zn0, dtype=np.float64).reshape(nvox, 6)
+    E_prev = np.zeros(6) if E_prev0 is None else np.asarray(E_prev0, dtype=np.float64)
+    floor = mu0 * 1e-6
+    Sigma, iters, errors, hist = [], [], [], []
+    for step, (E_k, h) in enumerate(zip(loads, hs)):
+        eps = eps + (E_k - E_prev)[None, :]
+        errs = []
+        n_eval = 0
+        while True:
+            sig, z = material(eps, z_n, ph, laws, h)
+            n_eval += 1
+            sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
+            mean_sig = sig.mean(axis=0)
+            e = equilibrium_error(sig_hat, mean_sig, N, floor)
+            errs.append(e)
+            if forced_iters is not None:
+                if n_eval >= forced_iters[step]:
+                    break
+            elif e < tol or n_eval >= max_iter:
+                break
+            tau = voigt_to_tensor_field(np.moveaxis(sig_hat, 0, -1), engineering=False)
+            d_hat = gamma0_apply(tau, lam0, mu0, N)
+            eps_hat = np.stack([np.fft.fftn(eps[:, c].reshape(N, N, N)) for c in range(6)], axis=-1)
+            eps_hat = eps_hat - d_hat
+            eps_hat[0, 0, 0, :] = nvox * E_k
+            eps = np.stack([np.fft.ifftn(eps_hat[..., c]).real.reshape(-1) for c in range(6)], axis=-1)
+        z_n = z
+        E_prev = E_k
+        Sigma.append(mean_sig)
+        iters.append(n_eval)
+        errors.append(errs)
+        if record:
+            hist.append((eps.copy(), z_n.copy(), sig.copy()))
+    out = {"Sigma": np.array(Sigma), "iters": np.array(iters), "errors": errors,
+           "eps": eps, "z": z_n, "sigma": sig, "lam0": lam0, "mu0": mu0}
+    if record:
+        out["history"] = hist
+    return out

@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This package holds input recipes only -- random draws, microstructure
+geometry and load histories -- and none of the material-law or basic-scheme
+arithmetic.  It imports neither the CUDA package nor the oracle.
+
+Recipes (the paper's workload -- a 150^3 GeoDict short-fibre metal-matrix
+composite, Sec. 3 -- is not available; these stand in for it):
+
+* ``material_batch``: independent voxels, eps ~ U[-a, a]^6 on the Voigt vector
+  (engineering shears), deviatoric z_n with (z11, z22, g23, g13, g12) ~
+  U[-b, b]^5 i.i.d. and z33 = -z11 - z22.
+* ``sphere_phase``: one centred spherical inclusion; a voxel (i, j, k) is
+  inside when its centre (i+1/2, j+1/2, k+1/2) lies within r of (N/2,N/2,N/2),
+  r = (3 f N^3 / (4 pi))^(1/3).
+* ``rsa_cylinders``: random sequential adsorption of straight cylinders with
+  axes in the x-y plane, uniform centres, angle U[0, pi), periodic images;
+  a candidate is accepted when its axis keeps a distance >= 2r + 1 from every
+  accepted axis; stops at the target volume fraction.
+* ``rsa_spheres``: the same for spheres of radius r (distance >= 2r + 1).
+* ``laminate_phase``: two layers normal to x.
+* load histories: ``ramp`` (E_k = (k/n) * E_final).
+"""
+import math
+
+import numpy as np
+
+
+def material_batch(n, seed=0, eps_amp=0.02, z_amp=0.005):
+    """(eps[n,6], z_n[n,6]) float64, AoS."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eps = rng.uniform(-eps_amp, eps_amp, size=(n, 6))
+    y = rng.uniform(-z_amp, z_amp, size=(n, 5))
+    zn = np.empty((n, 6))
+    zn[:, 0] = y[:, 0]
+    zn[:, 1] = y[:, 1]
+    zn[:, 2] = -y[:, 0] - y[:, 1]
+    zn[:, 3:] = y[:, 2:]
+    return eps, zn
+
+
+def sphere_radius(N, frac):
+    return (3.0 * frac * N ** 3 / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def sphere_phase(N, frac):
+    """uint8 (N,N,N): 1 inside the centred sphere, 0 elsewhere."""
+    r = sphere_radius(N, frac)
+    c = np.arange(N) + 0.5 - N / 2.0
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    return ((X * X + Y * Y + Z * Z) <= r * r).astype(np.uint8)
+
+
+def laminate_phase(N, n_first):
+    """uint8 (N,N,N): phase 1 for x-index < n_first, else 0."""
+    ph = np.zeros((N, N, N), dtype=np.uint8)
+    ph[:n_first] = 1
+    return ph
+
+
+def _periodic_delta(d, N):
+    return d - N * np.round(d / N)
+
+
+def _seg_point_dist2(p, a, b):
+    ab = b - a
+    t = np.clip(np.dot(p - a, ab) / max(np.dot(ab, ab), 1e-300), 0.0, 1.0)
+    d = p - (a + t * ab)
+    return float(np.dot(d, d))
+
+
+def _segments_intersect_2d(a, b, c, d):
+    def orient(p, q, r):
+        return (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0])
+    o1, o2 = orient(a, b, c), orient(a, b, d)
+    o3, o4 = orient(c, d, a), orient(c, d, b)
+    return (o1 * o2 < 0) and (o3 * o4 < 0)
+
+
+def _seg_seg_dist_2d(a, b, c, d):
+    if _segments_intersect_2d(a, b, c, d):
+        return 0.0
+    return math.sqrt(min(_seg_point_dist2(a, c, d), _seg_point_dist2(b, c, d),
+                         _seg_point_dist2(c, a, b), _seg_point_dist2(d, a, b)))
+
+
+def _rasterize_cylinder(ph, centre, theta, radius, length):
+    N = ph.shape[0]
+    u = np.array([math.cos(theta), math.sin(theta)])
+    half = 0.5 * length
+    ext_x = abs(u[0]) * half + radius + 1
+    ext_y = abs(u[1]) * half + radius + 1
+    xs = np.arange(int(math.floor(centre[0] - ext_x)), int(math.ceil(centre[0] + ext_x)) + 1)
+    ys = np.arange(int(math.floor(centre[1] - ext_y)), int(math.ceil(centre[1] + ext_y)) + 1)
+    zs = np.arange(int(math.floor(centre[2] - radius - 1)), int(math.ceil(centre[2] + radius + 1)) + 1)
+    X, Y, Z = np.meshgrid(xs + 0.5, ys + 0.5, zs + 0.5, indexing="ij")
+    dx, dy, dz = X - centre[0], Y - centre[1], Z - centre[2]
+    t = np.clip(dx * u[0] + dy * u[1], -half, half)
+    px, py = dx - t * u[0], dy - t * u[1]
+    inside = px * px + py * py + dz * dz <= radius * radius
+    I, J, K = np.nonzero(inside)
+    ph[xs[I] % N, ys[J] % N, zs[K] % N] = 1
+
+
+def rsa_cylinders(N, radius, frac, length, seed=0, max_tries=200000):
+    """Periodic RSA of x-y-plane cylinders; returns (uint8 phase, achieved fraction, n_fibres)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ph = np.zeros((N, N, N), dtype=np.uint8)
+    accepted = []
+    target = frac * N ** 3
+    half = 0.5 * length
+    tries = 0
+    while ph.sum(dtype=np.int64) < target and tries < max_tries:
+        tries += 1
+        c = rng.uniform(0, N, size=3)
+        th = rng.uniform(0, math.pi)
+        u = np.array([math.cos(th), math.sin(th)])
+        a, b = c[:2] - half * u, c[:2] + half * u
+        ok = True
+        for (c2, th2) in accepted:
+            dz = abs(_periodic_delta(c[2] - c2[2], N))
+            if dz >= 2 * radius + 1:
+                continue
+            u2 = np.array([math.cos(th2), math.sin(th2)])
+            for sx in (-N, 0, N):
+                for sy in (-N, 0, N):
+                    cc = c2[:2] + np.array([sx, sy])
+                    d2 = _seg_seg_dist_2d(a, b, cc - half * u2, cc + half * u2)
+                    if math.sqrt(d2 * d2 + dz * dz) < 2 * radius + 1:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            accepted.append((c, th))
+            _rasterize_cylinder(ph, c, th, radius, length)
+    return ph, float(ph.mean()), len(accepted)
+
+
+def rsa_spheres(N, radius, frac, seed=0, max_tries=200000):
+    """Periodic RSA of spheres; returns (uint8 phase, achieved fraction, n_spheres)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ph = np.zeros((N, N, N), dtype=np.uint8)
+    centres = []
+    target = frac * N ** 3
+    tries = 0
+    r_int = int(math.ceil(radius)) + 1
+    offs = np.arange(-r_int, r_int + 1)
+    while ph.sum(dtype=np.int64) < target and tries < max_tries:
+        tries += 1
+        c = rng.uniform(0, N, size=3)
+        ok = all(np.linalg.norm(_periodic_delta(c - c2, N)) >= 2 * radius + 1 for c2 in centres)
+        if not ok:
+            continue
+        centres.append(c)
+        base = np.floor(c).astype(int)
+        X, Y, Z = np.meshgrid(base[0] + offs, base[1] + offs, base[2] + offs, indexing="ij")
+        d2 = (X + 0.5 - c[0]) ** 2 + (Y + 0.5 - c[1]) ** 2 + (Z + 0.5 - c[2]) ** 2
+        m = d2 <= radius * radius
+        ph[X[m] % N, Y[m] % N, Z[m] % N] = 1
+    return ph, float(ph.mean()), len(centres)
+
+
+def ramp(n_steps, E_final):
+    """E_k = (k / n_steps) E_final, k = 1..n_steps -> (n_steps, 6)."""
+    E_final = np.asarray(E_final, dtype=np.float64)
+    return np.array([(k / n_steps) * E_final for k in range(1, n_steps + 1)])
+
+
+# Named workloads ----------------------------------------------------------
+
+# Matrix: elastic-viscoplastic, Norton dissipation (E, nu, sigma0, edot0, n).
+MATRIX_16 = (70.0, 0.3, 0.1, 1.0, 5.0)
+INCLUSION_16 = (400.0, 0.2)
+FIBRE_256 = (72.0, 0.22)
+MATRIX_256 = (70.0, 0.3, 0.1, 1.0, 10.0)
+
+
+def sphere_composite_16():
+    """16^3 centred sphere (10 %), uniaxial strain ramp to 1 % in 10 steps, h = 0.1."""
+    ph = sphere_phase(16, 0.10)
+    loads = ramp(10, [0.01, 0, 0, 0, 0, 0])
+    return ph, loads, [0.1] * 10
+
+
+def shear_tension_load(n_steps=20, amp=0.02):
+    """E_k = (k/n) amp (1,0,0,0,0,1)/sqrt(2) with engineering g12; h = 0.1."""
+    d = np.array([1, 0, 0, 0, 0, 1], dtype=np.float64) / math.sqrt(2.0)
+    return ramp(n_steps, amp * d), [0.1] * n_steps
+
+
+def fibre_composite(N=256, seed=0):
+    """RSA cylinders r=6, length 180 (aspect 15), 15 % volume fraction."""
+    return rsa_cylinders(N, 6.0, 0.15, min(180.0, 0.7 * N), seed=seed)

@@ -1,0 +1,204 @@
+/*
+ * gsm.h -- C ABI of the GB300 (sm_103a) library for generalized standard
+ * materials (GSM) and the Moulinec-Suquet basic scheme.
+ *
+ * Method: AutoMat (Bluehdorn, Gauger, Kabel; arXiv 2006.04391).
+ *   Sec. 2, Eq. (gsm_sigma), (gsm_internal): a GSM is given by a free energy
+ *     psi(eps, z) and a dissipation potential phi (the convex dual of the
+ *     paper's force potential Psi); sigma = d psi/d eps.
+ *   Sec. 4.1, Eq. (implicit_euler): one implicit Euler step per voxel,
+ *     d psi/dz (eps, z) + d phi/dzdot ((z - z_n)/h) = 0, solved by Newton with
+ *     first and second derivatives of psi and phi from reverse-mode AD.
+ *   Sec. 4.1, Eq. (tangent_formula): consistent tangent by the implicit
+ *     function theorem.
+ *   Sec. 3 "Material Law Evaluations": the basic scheme calls the law once
+ *     per voxel and iteration without tangent; fixed reference stiffness.
+ *
+ * Conventions for every field array:
+ *   - Voigt order (11, 22, 33, 23, 13, 12).  Strain-like arrays (eps, z_n, z,
+ *     macroscopic strains E) carry ENGINEERING shears (g_ij = 2 eps_ij);
+ *     stress-like arrays (sigma, Sigma) carry tensor shears.  The tangent maps
+ *     strain-like to stress-like vectors.
+ *   - Structure of arrays: component c of voxel i is at base[c * ld + i].
+ *   - Tangent: 21 components, the upper triangle of the symmetric 6x6 matrix
+ *     in row-major order (C11, C12, ..., C16, C22, ..., C66), SoA as above.
+ *   - All field pointers are DEVICE pointers owned by the caller unless a
+ *     function says otherwise.  The library never frees them.
+ *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *     stream) unless documented as synchronous.
+ *   - Return value: GSM_OK (0) or a negative GSM_E* code; no exception ever
+ *     crosses the ABI.  gsm_strerror() gives a static message.
+ *
+ * Per-voxel status word (int32, optional output of gsm_update):
+ *   bits 0-7 line-search iterations, bits 8-15 Newton iterations (including
+ *   FP64 corrections), bit 16 converged, bit 17 non-finite input or result,
+ *   bit 18 iteration cap reached, bit 19 Newton matrix not positive definite.
+ */
+#ifndef GSM_GB300_H
+#define GSM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ errors */
+#define GSM_OK 0
+#define GSM_EINVAL (-1)    /* bad argument: kind, parameter, pointer, size */
+#define GSM_ENOMEM (-2)    /* device or host allocation failed             */
+#define GSM_ECUDA (-3)     /* a CUDA or cuFFT call failed                  */
+#define GSM_ENOTCONV (-4)  /* iteration cap reached (see status / result)  */
+#define GSM_ENOTSUP (-5)   /* combination not supported                    */
+
+/* ------------------------------------------------------------------- kinds */
+#define GSM_PSI_ELASTIC 0        /* psi = 1/2 eps:C:eps, no internal variables      */
+#define GSM_PSI_ELASTIC_VP_DEV 1 /* psi = 1/2 (eps-z):C:(eps-z), z deviatoric (5 dof) */
+#define GSM_PHI_NONE 0
+#define GSM_PHI_NORTON 1         /* phi = sigma0 edot0 n/(n+1) (|zdot|_eq/edot0)^((n+1)/n) */
+
+#define GSM_FP64 0               /* every step in FP64                                 */
+#define GSM_FP32_FP64FIX 1       /* FP32 Newton, then FP64 correction (FP64 in/out)    */
+#define GSM_FP32 2               /* FP32 in, out and arithmetic                        */
+
+typedef struct gsm_material* gsm_handle;
+
+/*
+ * gsm_create -- define a material law (Sec. 2: the law is its two potentials).
+ *   psi_kind, phi_kind: GSM_PSI_ELASTIC with GSM_PHI_NONE, or
+ *                       GSM_PSI_ELASTIC_VP_DEV with GSM_PHI_NORTON.
+ *   params: host array; {E, nu} (n_params = 2) for the elastic law,
+ *           {E, nu, sigma0, edot0, n} (n_params = 5) for the Norton law.
+ *           Requires E > 0, -1 < nu < 0.5, sigma0 > 0, edot0 > 0, n > 0.
+ *   precision: GSM_FP64, GSM_FP32_FP64FIX or GSM_FP32.
+ *   out: receives an opaque handle owned by the library (gsm_destroy).
+ * Synchronous, host only.  Errors: GSM_EINVAL, GSM_ENOMEM.
+ */
+int gsm_create(gsm_handle* out, int psi_kind, int phi_kind, const double* params, int n_params,
+               int precision);
+
+/* gsm_destroy -- release a handle (NULL is accepted). */
+int gsm_destroy(gsm_handle h);
+
+/*
+ * gsm_update -- one implicit-Euler material update of n_vox independent
+ * voxels (Sec. 4.1, Eq. implicit_euler; tangent by Eq. tangent_formula).
+ *   eps     [6][ld]  strain at t_{n+1}               (in)
+ *   z_n     [6][ld]  internal variables at t_n        (in; deviatoric, the
+ *                    33 component is recomputed as -z11-z22; ignored and may
+ *                    be NULL for the elastic law)
+ *   h       step size t_{n+1} - t_n > 0
+ *   sigma   [6][ld]  stress at t_{n+1}               (out)
+ *   z       [6][ld]  internal variables at t_{n+1}    (out; copy of z_n for
+ *                    the elastic law, may be NULL then)
+ *   tangent [21][ld] consistent tangent               (out, may be NULL)
+ *   status  [ld]     per-voxel status word            (out, may be NULL)
+ * Element type: double for GSM_FP64 and GSM_FP32_FP64FIX, float for
+ * GSM_FP32.  ld >= n_vox.  n_vox = 0 is a no-op.  Arrays must not overlap.
+ * Asynchronous on `stream` (a cudaStream_t).  Errors: GSM_EINVAL, GSM_ECUDA.
+ * A voxel that hits the Newton cap is reported in `status`, not by the
+ * return value.
+ */
+int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, int64_t ld, double step_h,
+               void* sigma, void* z, void* tangent, int32_t* status, void* stream);
+
+/* gsm_strerror -- static message for a return code. */
+const char* gsm_strerror(int code);
+
+/* gsm_kernel_launches -- number of kernels this library has launched in the
+ * calling process (all entry points, all devices); for instrumentation. */
+int64_t gsm_kernel_launches(void);
+
+/* ================================================ Moulinec-Suquet basic scheme
+ *
+ * Periodic unit cell discretised by N^3 voxels; voxel (i, j, k) with k the
+ * fastest index has linear index (i*N + j)*N + k.  Each voxel carries a phase
+ * id (uint8) that selects one of n_phases materials.  Reference medium:
+ * isotropic, Lame constants at the midpoints of the phases' elastic ranges
+ * (fixed C^ref, Sec. 3).  Load step k: eps <- eps + (E_k - E_{k-1}), then
+ * iterate
+ *     sigma = law(eps, z_n, h_k)               (material kernel)
+ *     sigma^ = FFT(sigma)                      (cuFFT R2C)
+ *     e = sqrt(sum_xi |xi.sigma^/N^3|^2) / |<sigma>|_F   (FP64 reduction)
+ *     eps^(xi) -= Gamma0(xi) : sigma^(xi), eps^(0) = N^3 E_k   (fused kernel)
+ *     eps = IFFT(eps^)                         (cuFFT C2R)
+ * until e < tol; then z_n <- z and Sigma_k = <sigma> (FP64).  xi = 2 pi k with
+ * k the signed integer frequency; on even grids a mode with the Nyquist index
+ * together with any other nonzero index has Gamma0 := 0 and is left out of e.
+ */
+
+#define MS_PREC_FP64 0       /* all fields, FFTs and laws in FP64                  */
+#define MS_PREC_FP32_BULK 1  /* FP32 fields/FFTs/laws until e < switch_tol or e
+                                stalls, then FP64 iterations to tol; residual and
+                                mean-stress reductions always in FP64           */
+
+typedef struct ms_problem {
+  int N;                      /* grid size per axis, 2 <= N <= 1024            */
+  const uint8_t* phase;       /* device [N^3] phase ids < n_phases             */
+  int n_phases;               /* 1 .. 16                                       */
+  const gsm_handle* laws;     /* host [n_phases] materials (precision ignored) */
+  int precision;              /* MS_PREC_*                                     */
+} ms_problem;
+
+typedef struct ms_load {
+  int n_steps;                /* number of load steps >= 1                     */
+  const double* E;            /* host [n_steps][6] macroscopic strains E_k     */
+  const double* h;            /* host [n_steps] step sizes h_k > 0             */
+  double tol;                 /* equilibrium tolerance on e                    */
+  int max_iter;               /* iteration cap per step (material evaluations) */
+  const int32_t* forced_iters;/* host [n_steps] or NULL: run exactly this many
+                                 material evaluations per step (ignores tol)   */
+  double switch_tol;          /* MS_PREC_FP32_BULK: FP32 -> FP64 switch (<=0: 1e-5) */
+} ms_load;
+
+typedef struct ms_state {
+  double* eps;                /* device [6][N^3] strain; in/out if resume     */
+  double* z;                  /* device [6][N^3] internal variables (z_n)     */
+  int resume;                 /* 0: start from eps = 0, z = 0, E_prev = 0;
+                                 1: continue from eps, z, E_prev              */
+  double E_prev[6];           /* macroscopic strain of the previous step      */
+} ms_state;
+
+typedef struct ms_result {
+  double* Sigma;              /* host [n_steps][6] mean stress per step (out)  */
+  int32_t* iters;             /* host [n_steps] material evaluations per step */
+  double* final_error;        /* host [n_steps] e at the end of each step     */
+  int32_t* fp32_iters;        /* host [n_steps] of which in FP32 (may be NULL) */
+  int64_t total_iters;        /* out                                          */
+} ms_result;
+
+typedef struct ms_context* ms_handle;
+
+/*
+ * ms_create -- plan a basic-scheme solver for one problem: allocates the
+ * device workspace (fields, FFT buffers, reduction scratch) and cuFFT plans
+ * on the current device and binds them to `stream`.  The phase pointer and
+ * the laws must stay valid until ms_destroy.  Synchronous.
+ * Errors: GSM_EINVAL, GSM_ENOMEM, GSM_ECUDA.
+ */
+int ms_create(ms_handle* out, const ms_problem* prob, void* stream);
+int ms_destroy(ms_handle h);
+
+/* ms_workspace_bytes -- device bytes ms_create will allocate for `prob`
+ * (fields, FFT buffers and cuFFT work areas); for admission control. */
+size_t ms_workspace_bytes(const ms_problem* prob);
+
+/*
+ * ms_run -- solve a load history on a planned context.  `state` may be NULL
+ * (fresh start, internal fields); otherwise state->eps / state->z are device
+ * [6][N^3] FP64 arrays used as the solver's fields (read when resume = 1,
+ * always written back).  Synchronous: reads one FP64 residual per iteration.
+ * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTCONV (some step hit max_iter; the
+ * result is still filled in).
+ */
+int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result);
+
+/* ms_solve -- one-shot ms_create + ms_run + ms_destroy. */
+int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_result* result, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSM_GB300_H */

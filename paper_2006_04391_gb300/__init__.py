@@ -1,0 +1,260 @@
+"""Python binding of the GB300 GSM library (``include/gsm.h``).
+
+Argument marshalling only: every step of the material update and of the
+basic scheme runs in the library's CUDA kernels (and cuFFT).  Tensors are
+PyTorch CUDA tensors in structure-of-arrays layout ``[components, ld]``;
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+shared library has not been built, :func:`load` raises.
+
+Names follow the C ABI: :func:`gsm_create`, :func:`gsm_update`,
+:func:`gsm_destroy`, :func:`ms_create`, :func:`ms_run`, :func:`ms_solve`,
+:func:`ms_destroy`, :func:`ms_workspace_bytes`.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgsm_gb300.so")
+
+GSM_OK, GSM_EINVAL, GSM_ENOMEM, GSM_ECUDA, GSM_ENOTCONV, GSM_ENOTSUP = 0, -1, -2, -3, -4, -5
+GSM_PSI_ELASTIC, GSM_PSI_ELASTIC_VP_DEV = 0, 1
+GSM_PHI_NONE, GSM_PHI_NORTON = 0, 1
+GSM_FP64, GSM_FP32_FP64FIX, GSM_FP32 = 0, 1, 2
+MS_PREC_FP64, MS_PREC_FP32_BULK = 0, 1
+
+ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 << 19
+
+# Exported symbols declared in include/gsm.h.
+EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kernel_launches",
+           "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve")
+
+_lib = None
+
+
+class GsmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().gsm_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+class ms_problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int),
+                ("laws", ctypes.POINTER(ctypes.c_void_p)), ("precision", ctypes.c_int)]
+
+
+class ms_load(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int), ("E", ctypes.POINTER(ctypes.c_double)),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("forced_iters", ctypes.POINTER(ctypes.c_int32)), ("switch_tol", ctypes.c_double)]
+
+
+class ms_state(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_void_p), ("z", ctypes.c_void_p), ("resume", ctypes.c_int),
+                ("E_prev", ctypes.c_double * 6)]
+
+
+class ms_result(ctypes.Structure):
+    _fields_ = [("Sigma", ctypes.POINTER(ctypes.c_double)), ("iters", ctypes.POINTER(ctypes.c_int32)),
+                ("final_error", ctypes.POINTER(ctypes.c_double)),
+                ("fp32_iters", ctypes.POINTER(ctypes.c_int32)), ("total_iters", ctypes.c_int64)]
+
+
+def load(path=None):
+    """Load the CUDA library (built by ``__graft_entry__.build()``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.gsm_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl),
+                               ctypes.c_int, ctypes.c_int]
+    lib.gsm_destroy.argtypes = [vp]
+    lib.gsm_update.argtypes = [vp, i64, vp, vp, i64, dbl, vp, vp, vp, vp, vp]
+    lib.gsm_strerror.restype = ctypes.c_char_p
+    lib.gsm_strerror.argtypes = [ctypes.c_int]
+    lib.gsm_kernel_launches.restype = i64
+    for name in ("ms_create", "ms_destroy", "ms_run", "ms_solve", "ms_workspace_bytes"):
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            if name == "ms_create":
+                fn.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ms_problem), vp]
+            elif name == "ms_destroy":
+                fn.argtypes = [vp]
+            elif name == "ms_run":
+                fn.argtypes = [vp, ctypes.POINTER(ms_load), ctypes.POINTER(ms_state), ctypes.POINTER(ms_result)]
+            elif name == "ms_solve":
+                fn.argtypes = [ctypes.POINTER(ms_problem), ctypes.POINTER(ms_load), ctypes.POINTER(ms_state),
+                               ctypes.POINTER(ms_result), vp]
+            elif name == "ms_workspace_bytes":
+                fn.argtypes = [ctypes.POINTER(ms_problem)]
+                fn.restype = ctypes.c_size_t
+    _lib = lib
+    return lib
+
+
+def _check(rc, where):
+    if rc != GSM_OK:
+        raise GsmError(rc, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def kernel_launches():
+    return int(load().gsm_kernel_launches())
+
+
+# ------------------------------------------------------------------ materials
+
+class Material:
+    """Owns a ``gsm_handle`` (see :func:`gsm_create`)."""
+
+    def __init__(self, handle, psi_kind, phi_kind, params, precision):
+        self.handle = handle
+        self.psi_kind, self.phi_kind = psi_kind, phi_kind
+        self.params, self.precision = tuple(params), precision
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.gsm_destroy(self.handle)
+            self.handle = None
+
+
+def gsm_create(psi_kind, phi_kind, params, precision=GSM_FP64):
+    lib = load()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    _check(lib.gsm_create(ctypes.byref(h), psi_kind, phi_kind, arr, len(params), precision), "gsm_create")
+    return Material(h, psi_kind, phi_kind, params, precision)
+
+
+def norton(E, nu, sigma0, edot0, n, precision=GSM_FP64):
+    return gsm_create(GSM_PSI_ELASTIC_VP_DEV, GSM_PHI_NORTON, (E, nu, sigma0, edot0, n), precision)
+
+
+def elastic(E, nu, precision=GSM_FP64):
+    return gsm_create(GSM_PSI_ELASTIC, GSM_PHI_NONE, (E, nu), precision)
+
+
+def gsm_destroy(mat):
+    if mat.handle:
+        load().gsm_destroy(mat.handle)
+        mat.handle = None
+
+
+def gsm_update(mat, eps, z_n, h, sigma, z, tangent=None, status=None, stream=None, n_vox=None):
+    """Material update of ``n_vox`` voxels; tensors ``[6, ld]`` (tangent ``[21, ld]``, status ``[ld]``)."""
+    lib = load()
+    ld = eps.shape[1]
+    n = ld if n_vox is None else int(n_vox)
+    for t, rows in ((eps, 6), (z_n, 6), (sigma, 6), (z, 6), (tangent, 21)):
+        if t is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != ld or not t.is_contiguous()):
+            raise ValueError("fields must be contiguous [components, ld] tensors with a common ld")
+    rc = lib.gsm_update(mat.handle, n, _ptr(eps), _ptr(z_n), ld, float(h), _ptr(sigma), _ptr(z),
+                        _ptr(tangent), _ptr(status), _stream_ptr(stream))
+    _check(rc, "gsm_update")
+
+
+# -------------------------------------------------------------- basic scheme
+
+class MsContext:
+    def __init__(self, handle, N, laws, phase):
+        self.handle, self.N, self.laws, self.phase = handle, N, laws, phase
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ms_destroy(self.handle)
+            self.handle = None
+
+
+def _problem(phase, laws, precision):
+    N = int(phase.shape[0])
+    arr = (ctypes.c_void_p * len(laws))(*[m.handle.value for m in laws])
+    prob = ms_problem(N, phase.data_ptr(), len(laws), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), precision)
+    return prob, arr
+
+
+def ms_workspace_bytes(N, n_phases=2, precision=MS_PREC_FP64):
+    lib = load()
+    prob = ms_problem(int(N), None, int(n_phases), None, int(precision))
+    return int(lib.ms_workspace_bytes(ctypes.byref(prob)))
+
+
+def ms_create(phase, laws, precision=MS_PREC_FP64, stream=None):
+    """Plan a basic-scheme solver; ``phase`` is a uint8 CUDA tensor (N, N, N)."""
+    lib = load()
+    prob, arr = _problem(phase, laws, precision)
+    h = ctypes.c_void_p()
+    _check(lib.ms_create(ctypes.byref(h), ctypes.byref(prob), _stream_ptr(stream)), "ms_create")
+    ctx = MsContext(h, int(phase.shape[0]), list(laws), phase)
+    ctx._arr = arr
+    return ctx
+
+
+def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol):
+    E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
+    hs = np.ascontiguousarray(np.asarray(hs, dtype=np.float64).reshape(-1))
+    n = E.shape[0]
+    if hs.shape[0] != n:
+        raise ValueError("one step size per load step")
+    f = None
+    keep = [E, hs]
+    if forced_iters is not None:
+        f = np.ascontiguousarray(np.asarray(forced_iters, dtype=np.int32).reshape(-1))
+        keep.append(f)
+    ld = ms_load(n, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
+                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if f is not None else None, float(switch_tol))
+    return ld, keep, n
+
+
+def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=None, resume=False,
+           E_prev=None, switch_tol=0.0, check=True):
+    """Solve a load history.  Returns dict(Sigma, iters, final_error, fp32_iters, total_iters, rc)."""
+    lib = load()
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol)
+    Sigma = np.zeros((n, 6))
+    iters = np.zeros(n, dtype=np.int32)
+    ferr = np.zeros(n)
+    f32 = np.zeros(n, dtype=np.int32)
+    res = ms_result(Sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    ferr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    f32.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0)
+    st = None
+    if eps is not None or z is not None:
+        st = ms_state(eps.data_ptr(), z.data_ptr(), 1 if resume else 0,
+                      (ctypes.c_double * 6)(*(E_prev if E_prev is not None else [0.0] * 6)))
+    rc = lib.ms_run(ctx.handle, ctypes.byref(ld), ctypes.byref(st) if st is not None else None, ctypes.byref(res))
+    if check and rc not in (GSM_OK, GSM_ENOTCONV):
+        _check(rc, "ms_run")
+    return {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32,
+            "total_iters": int(res.total_iters), "rc": rc}
+
+
+def ms_destroy(ctx):
+    if ctx.handle:
+        load().ms_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def ms_solve(phase, laws, E, hs, precision=MS_PREC_FP64, stream=None, **kw):
+    """One-shot basic-scheme solve (ms_create + ms_run + ms_destroy)."""
+    ctx = ms_create(phase, laws, precision, stream)
+    try:
+        return ms_run(ctx, E, hs, **kw)
+    finally:
+        ms_destroy(ctx)

@@ -1,0 +1,65 @@
+// Internal definitions shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/gsm.h"
+#include "laws.cuh"
+
+namespace gsm {
+
+// Material handle behind gsm_handle.
+struct Material {
+  int psi_kind, phi_kind, precision;
+  double params[5];
+  LawParams<double> p64;
+  LawParams<float> p32;
+};
+
+inline LawParams<double> make_params(const double* prm, bool norton) {
+  LawParams<double> p;
+  const double E = prm[0], nu = prm[1];
+  p.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  p.mu = E / (2.0 * (1.0 + nu));
+  if (norton) {
+    const double s0 = prm[2], e0 = prm[3], n = prm[4];
+    p.a_phi = (n + 1.0) / (2.0 * n);
+    p.c_phi = s0 * e0 * n / (n + 1.0) * std::pow(e0, -(n + 1.0) / n);
+  } else {
+    p.a_phi = 1.0;
+    p.c_phi = 0.0;
+  }
+  p.inv_h_unused = 0.0;
+  return p;
+}
+
+inline LawParams<float> to_float(const LawParams<double>& p) {
+  LawParams<float> q;
+  q.lam = (float)p.lam;
+  q.mu = (float)p.mu;
+  q.c_phi = (float)p.c_phi;
+  q.a_phi = (float)p.a_phi;
+  q.inv_h_unused = 0.0f;
+  return q;
+}
+
+// Process-wide count of kernel launches made by this library.
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace gsm

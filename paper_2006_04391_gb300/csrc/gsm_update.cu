@@ -1,0 +1,245 @@
+// gsm_create / gsm_update / gsm_destroy: the batched per-voxel material
+// update (AutoMat, arXiv 2006.04391, Sec. 4.1 and Sec. 6) on sm_103a.
+//
+// One thread per voxel, as in the paper (Sec. 6), but with the fields
+// resident in HBM in structure-of-arrays layout (the paper staged chunks
+// through pinned host memory over PCIe): every component load and store of a
+// warp is one coalesced 256-byte (FP64) transaction.  The grid is a
+// persistent grid-stride loop sized from the occupancy of the instantiation;
+// the loop bound is uniform per block so every lane of a warp takes part in
+// the Newton convergence votes (padding lanes are inactive).
+#include <cstdio>
+#include <mutex>
+
+#include "common.cuh"
+#include "voxel.cuh"
+
+namespace gsm {
+
+std::atomic<int64_t> g_launches{0};
+
+namespace {
+
+constexpr int kBlock = 128;
+
+template <class T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Viscoplastic (Norton) voxels.
+template <int MODE, bool TAN>
+__global__ void __launch_bounds__(kBlock) norton_kernel(int64_t n, int64_t ld, LawParams<double> p,
+                                                        LawParams<float> pf, double h,
+                                                        const void* __restrict__ eps_,
+                                                        const void* __restrict__ zn_, void* __restrict__ sig_,
+                                                        void* __restrict__ z_, void* __restrict__ tan_,
+                                                        int32_t* __restrict__ status) {
+  using IO = std::conditional_t<MODE == MODE_FP32, float, double>;
+  const IO* eps = static_cast<const IO*>(eps_);
+  const IO* zn = static_cast<const IO*>(zn_);
+  IO* sig = static_cast<IO*>(sig_);
+  IO* z = static_cast<IO*>(z_);
+  IO* tan = static_cast<IO*>(tan_);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool active = i < n;
+    IO e[6], zi[6], s[6], zo[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      e[c] = active ? ldg(eps + c * ld + i) : IO(0);
+      zi[c] = active ? ldg(zn + c * ld + i) : IO(0);
+    }
+    IO t[21];
+    unsigned st;
+    if constexpr (MODE == MODE_FP64) {
+      st = voxel_fp64<NortonDev>(p, e, zi, h, active, s, zo, TAN ? t : nullptr);
+    } else if constexpr (MODE == MODE_FP32_FIX) {
+      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, h, active, s, zo, TAN ? t : nullptr);
+    } else {
+      st = voxel_fp32<NortonDev>(pf, e, zi, (float)h, active, s, zo, TAN ? t : nullptr);
+    }
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) fin = fin && isfinite(s[c]) && isfinite(zo[c]);
+    if (!fin) st |= ST_NONFINITE;
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sig[c * ld + i] = s[c];
+        z[c * ld + i] = zo[c];
+      }
+      if (TAN) {
+#pragma unroll
+        for (int c = 0; c < 21; ++c) tan[c * ld + i] = t[c];
+      }
+      if (status) status[i] = (int32_t)st;
+    }
+  }
+}
+
+// Linear-elastic voxels.
+template <class IO, bool TAN>
+__global__ void __launch_bounds__(kBlock) elastic_kernel(int64_t n, int64_t ld, LawParams<IO> p,
+                                                         const IO* __restrict__ eps, const IO* __restrict__ zn,
+                                                         IO* __restrict__ sig, IO* __restrict__ z,
+                                                         IO* __restrict__ tan, int32_t* __restrict__ status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    IO e[6], s[6], t[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = ldg(eps + c * ld + i);
+    voxel_elastic<IO>(p, e, s, TAN ? t : nullptr);
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      sig[c * ld + i] = s[c];
+      fin = fin && isfinite(s[c]);
+    }
+    if (z) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) z[c * ld + i] = zn ? ldg(zn + c * ld + i) : IO(0);
+    }
+    if (TAN) {
+#pragma unroll
+      for (int c = 0; c < 21; ++c) tan[c * ld + i] = t[c];
+    }
+    if (status) status[i] = (int32_t)(ST_CONVERGED | (fin ? 0u : ST_NONFINITE));
+  }
+}
+
+template <class K> int grid_for(K kernel, int64_t n) {
+  static int per_sm = 0;  // one static per kernel instantiation
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b <= 0) b = 1;
+    per_sm = b;
+  }
+  const int64_t need = (n + kBlock - 1) / kBlock;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  return (int)(need < cap ? need : cap);
+}
+
+template <int MODE, bool TAN>
+cudaError_t launch_norton(const Material& m, int64_t n, int64_t ld, double h, const void* eps, const void* zn,
+                          void* sig, void* z, void* tan, int32_t* status, cudaStream_t s) {
+  auto k = norton_kernel<MODE, TAN>;
+  norton_kernel<MODE, TAN><<<grid_for(k, n), kBlock, 0, s>>>(n, ld, m.p64, m.p32, h, eps, zn, sig, z, tan, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class IO, bool TAN>
+cudaError_t launch_elastic(const LawParams<IO>& p, int64_t n, int64_t ld, const void* eps, const void* zn,
+                           void* sig, void* z, void* tan, int32_t* status, cudaStream_t s) {
+  auto k = elastic_kernel<IO, TAN>;
+  elastic_kernel<IO, TAN><<<grid_for(k, n), kBlock, 0, s>>>(
+      n, ld, p, static_cast<const IO*>(eps), static_cast<const IO*>(zn), static_cast<IO*>(sig),
+      static_cast<IO*>(z), static_cast<IO*>(tan), status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+// Launch the update of one material on n voxels (also used by the basic scheme).
+int material_update(const Material& m, int64_t n, const void* eps, const void* zn, int64_t ld, double h,
+                    void* sig, void* z, void* tan, int32_t* status, cudaStream_t s) {
+  cudaError_t err;
+  const bool t = tan != nullptr;
+  if (m.psi_kind == GSM_PSI_ELASTIC) {
+    if (m.precision == GSM_FP32)
+      err = t ? launch_elastic<float, true>(m.p32, n, ld, eps, zn, sig, z, tan, status, s)
+              : launch_elastic<float, false>(m.p32, n, ld, eps, zn, sig, z, tan, status, s);
+    else
+      err = t ? launch_elastic<double, true>(m.p64, n, ld, eps, zn, sig, z, tan, status, s)
+              : launch_elastic<double, false>(m.p64, n, ld, eps, zn, sig, z, tan, status, s);
+  } else {
+    switch (m.precision) {
+      case GSM_FP64:
+        err = t ? launch_norton<MODE_FP64, true>(m, n, ld, h, eps, zn, sig, z, tan, status, s)
+                : launch_norton<MODE_FP64, false>(m, n, ld, h, eps, zn, sig, z, tan, status, s);
+        break;
+      case GSM_FP32_FP64FIX:
+        err = t ? launch_norton<MODE_FP32_FIX, true>(m, n, ld, h, eps, zn, sig, z, tan, status, s)
+                : launch_norton<MODE_FP32_FIX, false>(m, n, ld, h, eps, zn, sig, z, tan, status, s);
+        break;
+      default:
+        err = t ? launch_norton<MODE_FP32, true>(m, n, ld, h, eps, zn, sig, z, tan, status, s)
+                : launch_norton<MODE_FP32, false>(m, n, ld, h, eps, zn, sig, z, tan, status, s);
+        break;
+    }
+  }
+  return err == cudaSuccess ? GSM_OK : GSM_ECUDA;
+}
+
+int validate_material(int psi_kind, int phi_kind, const double* prm, int n_params, int precision) {
+  if (!prm) return GSM_EINVAL;
+  if (precision < GSM_FP64 || precision > GSM_FP32) return GSM_EINVAL;
+  if (psi_kind == GSM_PSI_ELASTIC && phi_kind == GSM_PHI_NONE) {
+    if (n_params != 2) return GSM_EINVAL;
+  } else if (psi_kind == GSM_PSI_ELASTIC_VP_DEV && phi_kind == GSM_PHI_NORTON) {
+    if (n_params != 5) return GSM_EINVAL;
+    if (!finite_pos(prm[2]) || !finite_pos(prm[3]) || !finite_pos(prm[4])) return GSM_EINVAL;
+  } else {
+    return GSM_EINVAL;
+  }
+  if (!finite_pos(prm[0]) || !std::isfinite(prm[1]) || !(prm[1] > -1.0 && prm[1] < 0.5)) return GSM_EINVAL;
+  return GSM_OK;
+}
+
+}  // namespace gsm
+
+using namespace gsm;
+
+extern "C" {
+
+int gsm_create(gsm_handle* out, int psi_kind, int phi_kind, const double* params, int n_params, int precision) {
+  if (!out) return GSM_EINVAL;
+  *out = nullptr;
+  const int rc = validate_material(psi_kind, phi_kind, params, n_params, precision);
+  if (rc != GSM_OK) return rc;
+  Material* m = new (std::nothrow) Material;
+  if (!m) return GSM_ENOMEM;
+  m->psi_kind = psi_kind;
+  m->phi_kind = phi_kind;
+  m->precision = precision;
+  for (int i = 0; i < 5; ++i) m->params[i] = i < n_params ? params[i] : 0.0;
+  m->p64 = make_params(params, psi_kind == GSM_PSI_ELASTIC_VP_DEV);
+  m->p32 = to_float(m->p64);
+  *out = reinterpret_cast<gsm_handle>(m);
+  return GSM_OK;
+}
+
+int gsm_destroy(gsm_handle h) {
+  delete reinterpret_cast<Material*>(h);
+  return GSM_OK;
+}
+
+int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, int64_t ld, double step_h,
+               void* sigma, void* z, void* tangent, int32_t* status, void* stream) {
+  if (!h || n_vox < 0 || ld < n_vox) return GSM_EINVAL;
+  if (n_vox == 0) return GSM_OK;
+  const Material& m = *reinterpret_cast<const Material*>(h);
+  if (!eps || !sigma) return GSM_EINVAL;
+  if (m.psi_kind == GSM_PSI_ELASTIC_VP_DEV && (!z_n || !z)) return GSM_EINVAL;
+  if (!(std::isfinite(step_h) && step_h > 0.0)) return GSM_EINVAL;
+  return material_update(m, n_vox, eps, z_n, ld, step_h, sigma, z, tangent, status,
+                         static_cast<cudaStream_t>(stream));
+}
+
+const char* gsm_strerror(int code) {
+  switch (code) {
+    case GSM_OK: return "ok";
+    case GSM_EINVAL: return "invalid argument";
+    case GSM_ENOMEM: return "out of memory";
+    case GSM_ECUDA: return "CUDA or cuFFT error";
+    case GSM_ENOTCONV: return "iteration cap reached";
+    case GSM_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+int64_t gsm_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

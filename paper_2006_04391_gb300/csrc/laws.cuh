@@ -1,0 +1,83 @@
+// Potentials of the generalized standard materials (GSM) the library ships.
+//
+// AutoMat (arXiv 2006.04391) reduces a material law to two potentials
+// (Sec. 2, Eq. gsm_sigma / gsm_internal); everything else -- the implicit
+// Euler Newton solve, the stress and the consistent tangent -- is obtained
+// by automatic differentiation (Sec. 4.1, Sec. 5).  A law here is a struct
+// with two templated functions written once on AD leaf packs:
+//
+//   psi(eps, y, p)  free energy, eps = strain (6 leaves), y = internal
+//                   variables (NY leaves);
+//   phi(v, p)       dissipation potential of the rate v = (y - y_n)/h.
+//
+// We use the dissipation form of the evolution law, d psi/dy + d phi/dv = 0,
+// which for a convex dual pair (phi = Psi*) is equivalent to the paper's
+// force-potential form (the paper notes the dual exists, Sec. 2).
+//
+// Voigt conventions: strain-like vectors (e11,e22,e33,g23,g13,g12) with
+// engineering shears g = 2 e_ij (the H = diag(H,H,H,H/2,H/2,H/2) of Eq.
+// michel_suquet_omega implies them), stress-like vectors with tensor shears.
+#pragma once
+
+#include "ad.cuh"
+
+namespace gsm {
+
+template <class T> struct LawParams {
+  T lam, mu;      // Lame constants
+  T c_phi;        // phi = c_phi * q^a_phi  (see NortonDev)
+  T a_phi;
+  T inv_h_unused; // keeps the struct 8-byte aligned for both precisions
+};
+
+// Linear elasticity: psi = 1/2 eps^T C eps, no internal variables.
+struct Elastic {
+  static constexpr int NY = 0;
+  template <class EP, class P> AD_HD static auto psi(const EP& e, const P& p) {
+    using ad::get;
+    const auto& e0 = get<0>(e); const auto& e1 = get<1>(e); const auto& e2 = get<2>(e);
+    const auto& e3 = get<3>(e); const auto& e4 = get<4>(e); const auto& e5 = get<5>(e);
+    auto tr = e0 + e1 + e2;
+    return (p.lam * 0.5) * sq(tr) + p.mu * (sq(e0) + sq(e1) + sq(e2)) +
+           (p.mu * 0.5) * (sq(e3) + sq(e4) + sq(e5));
+  }
+};
+
+// Elastic-viscoplastic GSM of Sec. 3 (Eq. michel_suquet_omega / _psi) with
+// sigma_Y = 0 and H = 0: the viscoplastic strain z is deviatoric and carried
+// by NY = 5 unknowns y = (z11, z22, g23, g13, g12), z33 = -z11 - z22 (Sec. 6
+// eliminates one component).  psi = 1/2 (eps - z)^T C (eps - z).
+// phi is the Norton potential, the convex dual of the paper's Psi:
+//   phi(v) = sigma0 edot0 n/(n+1) (s/edot0)^((n+1)/n),  s^2 = (2/3) zdot:zdot,
+// written as c_phi * q^a_phi with q = s^2, a_phi = (n+1)/(2n),
+// c_phi = sigma0 edot0 n/(n+1) edot0^(-(n+1)/n).
+struct NortonDev {
+  static constexpr int NY = 5;
+
+  template <class EP, class YP, class P> AD_HD static auto psi(const EP& e, const YP& y, const P& p) {
+    using ad::get;
+    const auto& y0 = get<0>(y); const auto& y1 = get<1>(y); const auto& y2 = get<2>(y);
+    const auto& y3 = get<3>(y); const auto& y4 = get<4>(y);
+    auto a0 = get<0>(e) - y0;
+    auto a1 = get<1>(e) - y1;
+    auto a2 = get<2>(e) + (y0 + y1);
+    auto a3 = get<3>(e) - y2;
+    auto a4 = get<4>(e) - y3;
+    auto a5 = get<5>(e) - y4;
+    auto tr = a0 + a1 + a2;
+    return (p.lam * 0.5) * sq(tr) + p.mu * (sq(a0) + sq(a1) + sq(a2)) +
+           (p.mu * 0.5) * (sq(a3) + sq(a4) + sq(a5));
+  }
+
+  template <class VP, class P> AD_HD static auto phi(const VP& v, const P& p) {
+    using ad::get;
+    const auto& v0 = get<0>(v); const auto& v1 = get<1>(v); const auto& v2 = get<2>(v);
+    const auto& v3 = get<3>(v); const auto& v4 = get<4>(v);
+    using S = typename std::decay_t<decltype(v0)>::scalar;
+    // q = (2/3) zdot:zdot with zdot33 = -v0 - v1 and engineering shears
+    auto q = S(4.0 / 3.0) * (sq(v0) + sq(v1) + v0 * v1) + S(1.0 / 3.0) * (sq(v2) + sq(v3) + sq(v4));
+    return p.c_phi * pow(q, p.a_phi);
+  }
+};
+
+}  // namespace gsm

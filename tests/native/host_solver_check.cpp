@@ -1,0 +1,65 @@
+// Test-only host build of the device headers (AD, potentials, per-voxel
+// solver), so the CPU suite can check the AD derivatives and the solve
+// logic without a GPU.  Never part of the product library.
+#include <cstdint>
+
+#include "../../paper_2006_04391_gb300/csrc/common.cuh"
+#include "../../paper_2006_04391_gb300/csrc/voxel.cuh"
+
+using namespace gsm;
+
+extern "C" {
+
+// params = {E, nu, sigma0, edot0, n}; fields AoS [n][6]; tangent [n][21] or NULL.
+int host_update(int mode, const double* prm, int64_t n, const double* eps, const double* zn, double h,
+                double* sig, double* z, double* tan, int32_t* status) {
+  const LawParams<double> p = make_params(prm, true);
+  const LawParams<float> pf = to_float(p);
+  for (int64_t i = 0; i < n; ++i) {
+    double e[6], zi[6], s[6], zo[6];
+    for (int c = 0; c < 6; ++c) { e[c] = eps[6 * i + c]; zi[c] = zn[6 * i + c]; }
+    unsigned st;
+    if (mode == 0) {
+      st = voxel_fp64<NortonDev>(p, e, zi, h, true, s, zo, tan ? tan + 21 * i : nullptr);
+    } else {
+      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, h, true, s, zo, tan ? tan + 21 * i : nullptr);
+    }
+    for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
+    status[i] = (int32_t)st;
+  }
+  return 0;
+}
+
+// AD derivatives of the shipped potentials at one point.
+void host_psi_derivs(const double* prm, const double* eps, const double* y, double* g, double* H) {
+  const LawParams<double> p = make_params(prm, true);
+  double e[6], yy[5], gg[5], HH[5][5];
+  for (int c = 0; c < 6; ++c) e[c] = eps[c];
+  for (int a = 0; a < 5; ++a) yy[a] = y[a];
+  psi_y_yy<NortonDev>(p, e, yy, gg, HH);
+  for (int a = 0; a < 5; ++a) { g[a] = gg[a]; for (int b = 0; b < 5; ++b) H[5 * a + b] = HH[a][b]; }
+}
+
+void host_phi_derivs(const double* prm, const double* v, double* g, double* H) {
+  const LawParams<double> p = make_params(prm, true);
+  double vv[5], gg[5], HH[5][5];
+  for (int a = 0; a < 5; ++a) vv[a] = v[a];
+  phi_v_vv<NortonDev>(p, vv, gg, HH);
+  for (int a = 0; a < 5; ++a) { g[a] = gg[a]; for (int b = 0; b < 5; ++b) H[5 * a + b] = HH[a][b]; }
+}
+
+void host_psi_blocks(const double* prm, const double* eps, const double* y, double* sig, double* Cee,
+                     double* Cey) {
+  const LawParams<double> p = make_params(prm, true);
+  double e[6], yy[5], s[6], A[6][6], B[6][5], Ct[5][6];
+  for (int c = 0; c < 6; ++c) e[c] = eps[c];
+  for (int a = 0; a < 5; ++a) yy[a] = y[a];
+  psi_blocks<NortonDev>(p, e, yy, s, A, B, Ct);
+  for (int i = 0; i < 6; ++i) {
+    sig[i] = s[i];
+    for (int j = 0; j < 6; ++j) Cee[6 * i + j] = A[i][j];
+    for (int j = 0; j < 5; ++j) Cey[5 * i + j] = B[i][j];
+  }
+}
+
+}  // extern "C"

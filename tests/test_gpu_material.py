@@ -1,0 +1,143 @@
+"""GPU parity of gsm_update (C ABI) against the FP64 oracle.
+
+Tolerance: per-voxel normwise relative error <= 1e-10 for sigma, z and the
+tangent in the FP64 and FP32-bulk + FP64-correction modes (the FP64 root of
+the strictly convex incremental potential is unique; both sides reach it up
+to rounding).  FP32 mode is held to 5e-4 (FP32 rounding of sigma = C(eps - z)
+with |C eps| / |sigma| up to ~20 on these inputs).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def soa(a, ld=None, dtype=None):
+    import torch
+    a = np.asarray(a)
+    n = a.shape[0]
+    ld = ld or n
+    out = np.zeros((a.shape[1], ld), dtype=dtype or a.dtype)
+    out[:, :n] = a.T
+    return torch.from_numpy(out).cuda()
+
+
+def run(G, mat, eps, zn, h, tangent=False, ld=None, dtype=np.float64):
+    import torch
+    n = eps.shape[0]
+    ld = ld or n
+    e = soa(eps, ld, dtype)
+    z0 = soa(zn, ld, dtype)
+    sig = torch.full_like(e, float("nan"))
+    z = torch.full_like(e, float("nan"))
+    tan = torch.full((21, ld), float("nan"), dtype=e.dtype, device="cuda") if tangent else None
+    st = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    G.gsm_update(mat, e, z0, h, sig, z, tan, st, n_vox=n)
+    torch.cuda.synchronize()
+    out = [sig.cpu().numpy()[:, :n].T, z.cpu().numpy()[:, :n].T, st.cpu().numpy()[:n]]
+    if tangent:
+        out.append(tan.cpu().numpy()[:, :n].T)
+    return out
+
+
+def rel_rows(a, b):
+    return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), 1e-300)
+
+
+def packed(C):
+    iu = np.triu_indices(6)
+    return C[:, iu[0], iu[1]]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_exp,h", [(5.0, 0.01), (1.0, 0.1), (3.0, 1e-3), (10.0, 0.1)])
+def test_update_matches_oracle(gsm, precision, n_exp, h):
+    prm = synth.MATRIX_16[:4] + (n_exp,)
+    n = 3 * 4096 + 37                      # several blocks and a ragged tail
+    eps, zn = synth.material_batch(n, seed=int(n_exp * 10 + precision))
+    mat = gsm.norton(*prm, precision=precision)
+    sig, z, st, tan = run(gsm, mat, eps, zn, h, tangent=True, ld=n + 11)
+    s2, z2, C2 = O.update(O.KIND_NORTON, prm, eps, zn, h, tangent=True)
+    assert np.all(st & gsm.ST_CONVERGED), "every voxel converged"
+    assert rel_rows(sig, s2).max() < TOL
+    assert rel_rows(z, z2).max() < TOL
+    assert rel_rows(tan, packed(C2)).max() < TOL
+
+
+def test_fp32_mode_accuracy(gsm):
+    prm = synth.MATRIX_16
+    eps, zn = synth.material_batch(5000, seed=2)
+    mat = gsm.norton(*prm, precision=gsm.GSM_FP32)
+    sig, z, st = run(gsm, mat, eps, zn, 0.01, dtype=np.float32)
+    s2, z2 = O.update(O.KIND_NORTON, prm, eps, zn, 0.01)
+    assert np.all(st & gsm.ST_CONVERGED)
+    assert rel_rows(sig.astype(np.float64), s2).max() < 5e-4
+    assert rel_rows(z.astype(np.float64), z2).max() < 5e-4
+
+
+def test_elastic_law(gsm):
+    eps, zn = synth.material_batch(1000, seed=4)
+    mat = gsm.elastic(400.0, 0.2)
+    sig, z, st, tan = run(gsm, mat, eps, zn, 0.1, tangent=True)
+    s2, _, C2 = O.update(O.KIND_ELASTIC, (400.0, 0.2), eps, zn, 0.1, tangent=True)
+    assert rel_rows(sig, s2).max() < 1e-14
+    assert np.max(np.abs(tan - packed(C2))) < 1e-12
+    assert np.array_equal(z, zn)
+
+
+def test_degenerate_inputs(gsm):
+    """Stress-free state (no flow, zero iterations), hydrostatic strain, and a
+    non-finite input flagged in the status word."""
+    prm = synth.MATRIX_16
+    eps = np.array([[0, 0, 0, 0, 0, 0], [0.01, 0.01, 0.01, 0, 0, 0], [np.nan, 0, 0, 0, 0, 0]], dtype=np.float64)
+    zn = np.zeros((3, 6))
+    for prec in (0, 1):
+        mat = gsm.norton(*prm, precision=prec)
+        sig, z, st = run(gsm, mat, eps, zn, 0.01)
+        s2, z2 = O.update(O.KIND_NORTON, prm, eps[:2], zn[:2], 0.01)
+        assert np.array_equal(z[0], np.zeros(6)) and np.array_equal(sig[0], np.zeros(6))
+        assert (st[0] & 0xffff) == 0 and st[0] & gsm.ST_CONVERGED
+        assert np.max(np.abs(z[1])) < 1e-20 and rel_rows(sig[1:2], s2[1:2]).max() < 1e-14
+        assert st[2] & gsm.ST_NONFINITE
+
+
+def test_invalid_arguments(gsm):
+    import torch
+    with pytest.raises(gsm.GsmError):
+        gsm.norton(70.0, 0.3, -0.1, 1.0, 5.0)
+    with pytest.raises(gsm.GsmError):
+        gsm.norton(70.0, 0.5, 0.1, 1.0, 5.0)
+    mat = gsm.norton(*synth.MATRIX_16)
+    e = torch.zeros(6, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update(mat, e, e, 0.0, e.clone(), e.clone())
+    # n_vox = 0 is a no-op
+    gsm.gsm_update(mat, e, e, 0.1, e.clone(), e.clone(), n_vox=0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_sampled(gsm, precision):
+    """2^24 voxels in the benchmark's launch configuration; 3000 sampled
+    voxels checked one by one against the oracle."""
+    import torch
+    n = 1 << 24
+    eps, zn = synth.material_batch(n, seed=2024)
+    e = torch.from_numpy(np.ascontiguousarray(eps.T)).cuda()
+    z0 = torch.from_numpy(np.ascontiguousarray(zn.T)).cuda()
+    sig = torch.empty_like(e)
+    z = torch.empty_like(e)
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    mat = gsm.norton(*synth.MATRIX_16[:4] + (5.0,), precision=precision)
+    gsm.gsm_update(mat, e, z0, 0.01, sig, z, None, st)
+    torch.cuda.synchronize()
+    stn = st.cpu().numpy()
+    assert np.all(stn & gsm.ST_CONVERGED)
+    idx = np.random.default_rng(7).choice(n, 3000, replace=False)
+    s2, z2 = O.update(O.KIND_NORTON, synth.MATRIX_16, eps[idx], zn[idx], 0.01)
+    assert rel_rows(sig.cpu().numpy()[:, idx].T, s2).max() < TOL
+    assert rel_rows(z.cpu().numpy()[:, idx].T, z2).max() < TOL

@@ -1,0 +1,99 @@
+"""Host (g++) build of the device headers: expression-template AD derivatives
+against finite differences, and the AD-driven per-voxel solve against the
+FP64 oracle.  Checks the algorithm without a GPU; the GPU parity tests are in
+tests/test_gpu_*.py."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "native", "host_solver_check.cpp")
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.fixture(scope="module")
+def hlib(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("hsc") / "hsc.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I/usr/local/cuda/include", SRC, "-o", out],
+                   check=True)
+    return ctypes.CDLL(out)
+
+
+def P(a):
+    return a.ctypes.data_as(_dp)
+
+
+def test_ad_derivatives_match_finite_differences(hlib):
+    rng = np.random.default_rng(0)
+    for n in (1.0, 5.0, 10.0):
+        prm = np.array(synth.MATRIX_16[:4] + (n,))
+        eps = rng.uniform(-0.02, 0.02, 6)
+        y = rng.uniform(-0.005, 0.005, 5)
+        v = rng.uniform(-1, 1, 5)
+        g, H = np.empty(5), np.empty((5, 5))
+        hlib.host_psi_derivs(P(prm), P(eps), P(y), P(g), P(H))
+        # psi is quadratic: its gradient is linear in y, so differences are exact up to rounding
+        for a in range(5):
+            yp, ym = y.copy(), y.copy()
+            yp[a] += 1e-6
+            ym[a] -= 1e-6
+            gp, gm, Hd = np.empty(5), np.empty(5), np.empty((5, 5))
+            hlib.host_psi_derivs(P(prm), P(eps), P(yp), P(gp), P(Hd))
+            hlib.host_psi_derivs(P(prm), P(eps), P(ym), P(gm), P(Hd))
+            assert np.max(np.abs((gp - gm) / 2e-6 - H[:, a])) < 1e-6 * np.max(np.abs(H))
+            # the gradient itself against differences of the oracle's psi
+            fd = (O.psi(tuple(prm), eps, yp) - O.psi(tuple(prm), eps, ym)) / 2e-6
+            assert abs(fd - g[a]) < 1e-7 * max(1.0, np.max(np.abs(g)))
+        gv, Hv = np.empty(5), np.empty((5, 5))
+        hlib.host_phi_derivs(P(prm), P(v), P(gv), P(Hv))
+        for a in range(5):
+            vp, vm = v.copy(), v.copy()
+            vp[a] += 1e-6
+            vm[a] -= 1e-6
+            gp, gm, Hd = np.empty(5), np.empty(5), np.empty((5, 5))
+            hlib.host_phi_derivs(P(prm), P(vp), P(gp), P(Hd))
+            hlib.host_phi_derivs(P(prm), P(vm), P(gm), P(Hd))
+            assert np.max(np.abs((gp - gm) / 2e-6 - Hv[:, a])) < 1e-6 * np.max(np.abs(Hv))
+            fd = (O.phi(tuple(prm), vp) - O.phi(tuple(prm), vm)) / 2e-6
+            assert abs(fd - gv[a]) < 1e-7 * max(1.0, np.max(np.abs(gv)))
+
+
+def test_ad_second_order_blocks(hlib):
+    """sigma = psi_eps and its second-order blocks: psi_ee = C, psi_ey = -C P."""
+    prm = np.array(synth.MATRIX_16)
+    eps = np.array([0.01, -0.004, 0.002, 0.003, -0.001, 0.005])
+    y = np.array([0.001, -0.002, 0.0005, 0.0, 0.0007])
+    sig, Cee, Cey = np.empty(6), np.empty((6, 6)), np.empty((6, 5))
+    hlib.host_psi_blocks(P(prm), P(eps), P(y), P(sig), P(Cee), P(Cey))
+    assert np.max(np.abs(sig - O.stress(tuple(prm), eps, y))) < 1e-14
+    lam, mu = O.lame(70.0, 0.3)
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    C[:3, :3] += 2 * mu * np.eye(3)
+    C[3:, 3:] = mu * np.eye(3)
+    assert np.max(np.abs(Cee - C)) < 1e-12
+    assert np.max(np.abs(Cey + C @ O.P_MATRIX)) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_host_solver_matches_oracle(hlib, mode):
+    prm = np.array(synth.MATRIX_16)
+    eps, zn = synth.material_batch(3000, seed=5)
+    n = eps.shape[0]
+    for h in (1e-3, 1e-2, 1e-1):
+        sig, z, tan = np.empty((n, 6)), np.empty((n, 6)), np.empty((n, 21))
+        st = np.empty(n, dtype=np.int32)
+        hlib.host_update(mode, P(prm), ctypes.c_int64(n), P(eps), P(zn), ctypes.c_double(h), P(sig), P(z), P(tan),
+                         st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        s2, z2, C2 = O.update(O.KIND_NORTON, tuple(prm), eps, zn, h, tangent=True)
+        iu = np.triu_indices(6)
+        assert np.all((st >> 16) & 1)
+        assert (np.abs(sig - s2).max(1) / np.abs(s2).max(1)).max() < 1e-11
+        assert (np.abs(z - z2).max(1) / np.abs(z2).max(1)).max() < 1e-11
+        assert (np.abs(tan - C2[:, iu[0], iu[1]]).max(1) / np.abs(C2).max((1, 2))).max() < 1e-11

@@ -301,8 +301,8 @@ def bench_ms(G, torch):
     import synth
     ph, frac, nf = synth.fibre_composite(256, seed=0)
     phase = torch.from_numpy(ph).cuda()
-    res = {"workload": "256^3 RSA cylinders r=6 L=180, 15% (achieved %.4f, %d fibres), n=10, shear+tension"
-                       % (frac, nf)}
+    res = {"workload": f"256^3 RSA cylinders r=6 L=180, 15 percent (achieved {frac:.4f}, {nf} fibres), "
+                       "n=10, shear+tension"}
     loads, hs = synth.shear_tension_load(20, 0.02)
     for name, prec in (("fp64", G.MS_PREC_FP64), ("fp32_bulk", G.MS_PREC_FP32_BULK)):
         laws = [G.norton(*synth.MATRIX_256), G.elastic(*synth.FIBRE_256)]

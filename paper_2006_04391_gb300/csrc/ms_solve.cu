@@ -576,7 +576,8 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
       rc = step_start<float>(c, E, E_prev);
       double best = 1e300;
       int since_best = 0;
-      while (rc == GSM_OK && n_eval < cap) {
+      // leave at least one evaluation for the FP64 phase
+      while (rc == GSM_OK && n_eval < cap - 1) {
         rc = evaluate<float>(c, hk);
         if (rc != GSM_OK) break;
         ++n_eval;
@@ -589,9 +590,13 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
       // hand the FP32 strain (eps_raw of the last evaluation) to FP64
       if (rc == GSM_OK) {
         convert<float, double>(c, H.eps_raw, F.eps_raw, n6, 1.0);
-        const double zero[6] = {0, 0, 0, 0, 0, 0};
         rc = step_start<double>(c, E, E);  // no increment: already at E_k
-        (void)zero;
+        // resynthesise the FP64 strain from the spectrum so that its mean is E_k exactly
+        if (rc == GSM_OK) {
+          cudaMemcpyAsync(F.sig_hat, F.eps_hat, 6 * c.nmodes * sizeof(cufftDoubleComplex), cudaMemcpyDeviceToDevice,
+                          c.stream);
+          rc = inverse<double>(c);
+        }
       }
     } else {
       rc = step_start<double>(c, E, E_prev);

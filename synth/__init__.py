@@ -99,44 +99,67 @@ def _rasterize_cylinder(ph, centre, theta, radius, length):
     px, py = dx - t * u[0], dy - t * u[1]
     inside = px * px + py * py + dz * dz <= radius * radius
     I, J, K = np.nonzero(inside)
-    ph[xs[I] % N, ys[J] % N, zs[K] % N] = 1
+    flat = np.unique(np.ravel_multi_index((xs[I] % N, ys[J] % N, zs[K] % N), ph.shape))
+    new = int(np.count_nonzero(ph.flat[flat] == 0))
+    ph.flat[flat] = 1
+    return new
+
+
+def _pt_seg_d2(p, a, b):
+    """Squared distance of points p to segments [a, b] (broadcast over leading axes)."""
+    ab = b - a
+    den = np.maximum(np.sum(ab * ab, axis=-1), 1e-300)
+    t = np.clip(np.sum((p - a) * ab, axis=-1) / den, 0.0, 1.0)
+    d = p - (a + t[..., None] * ab)
+    return np.sum(d * d, axis=-1)
+
+
+def _seg_seg_dist_2d_many(a, b, C, D):
+    """Distances of one 2-D segment [a, b] to many segments [C_i, D_i]."""
+    def orient(p, q, r):
+        return (q[..., 0] - p[..., 0]) * (r[..., 1] - p[..., 1]) - (q[..., 1] - p[..., 1]) * (r[..., 0] - p[..., 0])
+    o1, o2 = orient(a, b, C), orient(a, b, D)
+    o3, o4 = orient(C, D, a), orient(C, D, b)
+    cross = (o1 * o2 < 0) & (o3 * o4 < 0)
+    d2 = np.minimum.reduce([_pt_seg_d2(a, C, D), _pt_seg_d2(b, C, D), _pt_seg_d2(C, a, b), _pt_seg_d2(D, a, b)])
+    return np.where(cross, 0.0, np.sqrt(d2))
 
 
 def rsa_cylinders(N, radius, frac, length, seed=0, max_tries=200000):
     """Periodic RSA of x-y-plane cylinders; returns (uint8 phase, achieved fraction, n_fibres)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     ph = np.zeros((N, N, N), dtype=np.uint8)
-    accepted = []
+    A = np.zeros((0, 2))
+    B = np.zeros((0, 2))
+    Zc = np.zeros(0)
     target = frac * N ** 3
     half = 0.5 * length
+    shifts = np.array([(sx, sy) for sx in (-N, 0, N) for sy in (-N, 0, N)], dtype=np.float64)
     tries = 0
-    while ph.sum(dtype=np.int64) < target and tries < max_tries:
+    n_acc = 0
+    filled = 0
+    while filled < target and tries < max_tries:
         tries += 1
         c = rng.uniform(0, N, size=3)
         th = rng.uniform(0, math.pi)
         u = np.array([math.cos(th), math.sin(th)])
         a, b = c[:2] - half * u, c[:2] + half * u
-        ok = True
-        for (c2, th2) in accepted:
-            dz = abs(_periodic_delta(c[2] - c2[2], N))
-            if dz >= 2 * radius + 1:
-                continue
-            u2 = np.array([math.cos(th2), math.sin(th2)])
-            for sx in (-N, 0, N):
-                for sy in (-N, 0, N):
-                    cc = c2[:2] + np.array([sx, sy])
-                    d2 = _seg_seg_dist_2d(a, b, cc - half * u2, cc + half * u2)
-                    if math.sqrt(d2 * d2 + dz * dz) < 2 * radius + 1:
-                        ok = False
-                        break
-                if not ok:
-                    break
-            if not ok:
-                break
-        if ok:
-            accepted.append((c, th))
-            _rasterize_cylinder(ph, c, th, radius, length)
-    return ph, float(ph.mean()), len(accepted)
+        if n_acc:
+            dz = np.abs(_periodic_delta(c[2] - Zc, N))
+            near = dz < 2 * radius + 1
+            if near.any():
+                Cs = A[near][None, :, :] + shifts[:, None, :]
+                Ds = B[near][None, :, :] + shifts[:, None, :]
+                d2d = _seg_seg_dist_2d_many(a, b, Cs, Ds)
+                d3 = np.sqrt(d2d ** 2 + dz[near][None, :] ** 2)
+                if np.any(d3 < 2 * radius + 1):
+                    continue
+        A = np.vstack([A, a[None]])
+        B = np.vstack([B, b[None]])
+        Zc = np.append(Zc, c[2])
+        n_acc += 1
+        filled += _rasterize_cylinder(ph, c, th, radius, length)
+    return ph, float(ph.mean()), n_acc
 
 
 def rsa_spheres(N, radius, frac, seed=0, max_tries=200000):

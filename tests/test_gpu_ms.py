@@ -1,0 +1,163 @@
+"""GPU parity of the basic scheme (ms_create / ms_run / ms_solve) against the
+FP64 oracle and the closed-form laminate.
+
+Iteration-matched parity: the GPU runs exactly the oracle's number of
+material evaluations per step (forced_iters); the two then differ only by FFT
+rounding, which the contracting fixed-point iteration does not amplify, so
+the per-step mean stress must agree to 1e-10 (relative to max |Sigma|) and
+the final fields to 1e-9.  Free runs to tol agree to O(tol).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.ms as OMS
+import synth
+from test_oracle_ms import laminate_exact, stiffness
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_laws(G, laws):
+    out = []
+    for kind, prm in laws:
+        out.append(G.norton(*prm) if kind == O.KIND_NORTON else G.elastic(*prm))
+    return out
+
+
+def rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b))
+
+
+@pytest.fixture(scope="module")
+def sphere16_ref():
+    ph, loads, hs = synth.sphere_composite_16()
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    ref = OMS.solve(ph, laws, loads, hs, tol=1e-8)
+    return ph, loads, hs, laws, ref
+
+
+@pytest.mark.parametrize("N,nf", [(8, 3), (9, 4), (16, 5)])
+def test_laminate_closed_form(gsm, N, nf):
+    import torch
+    E = np.array([0.01, 0.002, -0.003, 0.004, 0.001, 0.005])
+    ph = synth.laminate_phase(N, nf)
+    laws = [gsm.elastic(70.0, 0.3), gsm.elastic(400.0, 0.2)]
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), laws, E[None], [0.1], tol=1e-13, max_iter=3000)
+    exact = laminate_exact(stiffness(400.0, 0.2), stiffness(70.0, 0.3), nf / N, E)
+    assert out["rc"] == 0
+    assert rel(out["Sigma"][0], exact) < 1e-11
+
+
+def test_config1_iteration_matched(gsm, sphere16_ref):
+    """16^3 sphere composite, 10 steps, FP64: Sigma_k and final fields."""
+    import torch
+    ph, loads, hs, laws, ref = sphere16_ref
+    N = ph.shape[0]
+    eps = torch.zeros(6, N ** 3, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(eps)
+    ctx = gsm.ms_create(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws))
+    out = gsm.ms_run(ctx, loads, hs, forced_iters=ref["iters"], eps=eps, z=z)
+    assert out["rc"] == 0
+    assert list(out["iters"]) == list(ref["iters"])
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-10
+    assert rel(eps.cpu().numpy().T, ref["eps"]) < 1e-9
+    assert rel(z.cpu().numpy().T, ref["z"]) < 1e-9
+    # final errors are the oracle's last errors
+    last = np.array([e[-1] for e in ref["errors"]])
+    assert np.max(np.abs(out["final_error"] - last) / last) < 1e-6
+
+
+def test_config1_free_run(gsm, sphere16_ref):
+    import torch
+    ph, loads, hs, laws, ref = sphere16_ref
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, hs, tol=1e-8)
+    assert out["rc"] == 0
+    assert np.all(np.abs(out["iters"] - ref["iters"]) <= 1)
+    assert np.all(out["final_error"] < 1e-8)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-7
+
+
+@pytest.mark.parametrize("N", [9, 12])
+def test_odd_and_even_grids(gsm, N):
+    import torch
+    ph = synth.sphere_phase(N, 0.15)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16[:4] + (3.0,)), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(2, [0.004, -0.001, 0.0, 0.002, 0.0, 0.003])
+    ref = OMS.solve(ph, laws, loads, [0.05, 0.05], tol=1e-9)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.05, 0.05],
+                       forced_iters=ref["iters"])
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-10
+
+
+def test_fp32_bulk_then_fp64(gsm, sphere16_ref):
+    """FP32 fields/FFTs/laws until e < 1e-5, then FP64 to tol: the mean stress
+    matches the FP64 oracle to O(tol)."""
+    import torch
+    ph, loads, hs, laws, ref = sphere16_ref
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, hs, tol=1e-8,
+                       precision=gsm.MS_PREC_FP32_BULK)
+    assert out["rc"] == 0
+    assert np.all(out["fp32_iters"] > 0) and np.all(out["fp32_iters"] < out["iters"])
+    assert np.all(out["final_error"] < 1e-8)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-6
+
+
+def test_resume_equals_straight_run(gsm):
+    import torch
+    ph = synth.sphere_phase(10, 0.1)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(4, [0.004, 0, 0, 0, 0, 0])
+    hs = [0.1] * 4
+    glaws = gpu_laws(gsm, laws)
+    phase = torch.from_numpy(ph).cuda()
+    ctx = gsm.ms_create(phase, glaws)
+    full = gsm.ms_run(ctx, loads, hs, forced_iters=[40] * 4)
+    eps = torch.zeros(6, 1000, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(eps)
+    a = gsm.ms_run(ctx, loads[:2], hs[:2], forced_iters=[40] * 2, eps=eps, z=z)
+    b = gsm.ms_run(ctx, loads[2:], hs[2:], forced_iters=[40] * 2, eps=eps, z=z, resume=True, E_prev=loads[1])
+    both = np.vstack([a["Sigma"], b["Sigma"]])
+    assert rel(both, full["Sigma"]) < 1e-12
+
+
+def test_homogeneous_grid_converges_at_first_evaluation(gsm):
+    import torch
+    ph = np.zeros((8, 8, 8), dtype=np.uint8)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), [gsm.elastic(70.0, 0.3)],
+                       np.array([[0.01, 0, 0, 0, 0, 0.002]]), [0.1], tol=1e-14)
+    assert list(out["iters"]) == [1] and out["final_error"][0] < 1e-14
+    assert rel(out["Sigma"][0], stiffness(70.0, 0.3) @ np.array([0.01, 0, 0, 0, 0, 0.002])) < 1e-14
+
+
+def test_iteration_cap_reports_not_converged(gsm, sphere16_ref):
+    import torch
+    ph, loads, hs, laws, ref = sphere16_ref
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads[:1], hs[:1], tol=1e-12,
+                       max_iter=5)
+    assert out["rc"] == gsm.GSM_ENOTCONV and out["iters"][0] == 5
+
+
+@pytest.fixture(scope="module")
+def fibre256():
+    return synth.fibre_composite(256, seed=0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fibre_composite_256_first_evaluation(gsm, precision, fibre256):
+    """256^3 RSA fibre composite in the benchmark configuration.  With uniform
+    strain E_1 the first evaluation's mean stress is the phase-weighted
+    single-voxel response, which the oracle computes one voxel per phase."""
+    import torch
+    ph, frac, nf = fibre256
+    loads, hs = synth.shear_tension_load(20, 0.02)
+    laws = [(O.KIND_NORTON, synth.MATRIX_256), (O.KIND_ELASTIC, synth.FIBRE_256)]
+    ctx = gsm.ms_create(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), precision)
+    out = gsm.ms_run(ctx, loads[:1], hs[:1], forced_iters=[1], switch_tol=1e30)
+    f = ph.mean(dtype=np.float64)
+    s_m, _ = O.update(O.KIND_NORTON, synth.MATRIX_256, loads[:1], np.zeros((1, 6)), hs[0])
+    s_f, _ = O.update(O.KIND_ELASTIC, synth.FIBRE_256, loads[:1], np.zeros((1, 6)), hs[0])
+    expect = (1 - f) * s_m[0] + f * s_f[0]
+    assert rel(out["Sigma"][0], expect) < 1e-12
+    more = gsm.ms_run(ctx, loads[:1], hs[:1], forced_iters=[6], switch_tol=1e30)
+    assert np.isfinite(more["Sigma"]).all() and more["final_error"][0] < out["final_error"][0]

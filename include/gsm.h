@@ -197,6 +197,30 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
 /* ms_solve -- one-shot ms_create + ms_run + ms_destroy. */
 int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_result* result, void* stream);
 
+/*
+ * ms_evaluate_noalloc -- one FP64 material evaluation of an N^3 phase field
+ * and its FP64 mean stress, without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a process whose device memory belongs to another allocator, or
+ * code that must not allocate or synchronise while it runs).
+ *   N        grid size, 2 <= N <= 1024 (larger N returns GSM_EINVAL)
+ *   phase    device [N^3] phase ids < n_phases (1 <= n_phases <= 16)
+ *   laws     host [n_phases] materials
+ *   eps      device [6][N^3] strain (normalised, engineering shears)   (in)
+ *   z_n      device [6][N^3] internal variables at t_n                  (in)
+ *   sigma    device [6][N^3] stress                                     (out)
+ *   z        device [6][N^3] internal variables at t_{n+1}; 0 in elastic phases (out)
+ *   mean     device [6] FP64 mean of sigma                              (out)
+ * Same kernel and reduction as the material step of ms_run.  Its scratch is
+ * a file-scope device array of 6*1024+8 doubles that every GPU loading the
+ * library holds until exit; all calls share it, so calls whose work overlaps
+ * on the GPU race.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress): make that first call before any stream
+ * capture.  Asynchronous on `stream`.  Errors: GSM_EINVAL, GSM_ECUDA.
+ */
+int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, const gsm_handle* laws, double step_h,
+                        const double* eps, const double* z_n, double* sigma, double* z, double* mean, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

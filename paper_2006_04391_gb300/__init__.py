@@ -28,7 +28,7 @@ ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 <<
 
 # Exported symbols declared in include/gsm.h.
 EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kernel_launches",
-           "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve")
+           "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc")
 
 _lib = None
 
@@ -79,6 +79,9 @@ def load(path=None):
     lib.gsm_strerror.restype = ctypes.c_char_p
     lib.gsm_strerror.argtypes = [ctypes.c_int]
     lib.gsm_kernel_launches.restype = i64
+    if hasattr(lib, "ms_evaluate_noalloc"):
+        lib.ms_evaluate_noalloc.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp), dbl, vp, vp, vp, vp,
+                                            vp, vp]
     for name in ("ms_create", "ms_destroy", "ms_run", "ms_solve", "ms_workspace_bytes"):
         if hasattr(lib, name):
             fn = getattr(lib, name)
@@ -243,6 +246,19 @@ def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=
         _check(rc, "ms_run")
     return {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32,
             "total_iters": int(res.total_iters), "rc": rc}
+
+
+def ms_evaluate_noalloc(phase, laws, h, eps, z_n, sigma, z, mean, stream=None):
+    """Allocation-free material evaluation of a phase field (see include/gsm.h).
+
+    All tensors are caller-allocated CUDA tensors: ``eps``, ``z_n``, ``sigma``,
+    ``z`` are [6, N^3] float64, ``mean`` is [6] float64."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(laws))(*[m.handle.value for m in laws])
+    rc = lib.ms_evaluate_noalloc(int(phase.shape[0]), phase.data_ptr(), len(laws),
+                                 ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), float(h), _ptr(eps), _ptr(z_n),
+                                 _ptr(sigma), _ptr(z), _ptr(mean), _stream_ptr(stream))
+    _check(rc, "ms_evaluate_noalloc")
 
 
 def ms_destroy(ctx):

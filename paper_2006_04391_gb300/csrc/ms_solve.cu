@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -647,3 +648,91 @@ int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_re
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free variant
+// ms_evaluate_noalloc: one material evaluation of a microstructure plus its
+// FP64 mean stress, for callers that cannot allocate device memory (a process
+// whose device memory is owned by another allocator, or code running where a
+// cudaMalloc would be illegal or would synchronise).  It runs the same kernel
+// as the basic scheme's material step (ms_material_kernel, FP64) and the same
+// fixed-order reduction, but its block partial sums live in the file-scope
+// array below instead of a context's workspace.
+//
+// The array is part of the library's device image: every GPU that loads the
+// library holds it (48 KB + 64 B) until the process exits.  In host code its
+// name is only a stand-in, so its device address is fetched once per device
+// with cudaGetSymbolAddress and passed to the kernels.  All calls share the
+// array: two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.  Each block writes its own partial sum
+// before the reduction reads it, so nothing has to be cleared between calls.
+static constexpr int kNoAllocMaxBlocks = 1024;
+static __device__ __align__(256) double g_ms_eval_scratch[6 * kNoAllocMaxBlocks + 8];
+
+namespace gsm {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up on the
+// first call per device).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GSM_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return GSM_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ms_eval_scratch) != cudaSuccess || !p) return GSM_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GSM_OK;
+}
+
+}  // namespace
+}  // namespace gsm
+
+extern "C" int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, const gsm_handle* laws, double step_h,
+                                   const double* eps, const double* z_n, double* sigma, double* z, double* mean,
+                                   void* stream) {
+  using namespace gsm;
+  if (N < 2 || N > 1024 || !phase || n_phases < 1 || n_phases > kMaxPhases || !laws || !eps || !z_n || !sigma ||
+      !z || !mean || !(std::isfinite(step_h) && step_h > 0.0))
+    return GSM_EINVAL;
+  PhaseTable tab;
+  std::memset(&tab, 0, sizeof(tab));
+  for (int p = 0; p < n_phases; ++p) {
+    const Material* m = reinterpret_cast<const Material*>(laws[p]);
+    if (!m) return GSM_EINVAL;
+    tab.kind[p] = m->psi_kind;
+    tab.p64[p] = m->p64;
+    tab.p32[p] = m->p32;
+  }
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != GSM_OK) return rc;
+  const int64_t nvox = (int64_t)N * N * N;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_kernel<double, MODE_FP64>, kMatBlock, 0) !=
+            cudaSuccess ||
+        b <= 0)
+      b = 1;
+    per_sm = b;
+  }
+  const int grid = std::min(grid_cap(nvox, kMatBlock, per_sm), kNoAllocMaxBlocks);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* partials = scratch;                                    // [6][grid]
+  Reduced* red = reinterpret_cast<Reduced*>(scratch + 6 * kNoAllocMaxBlocks);
+  ms_material_kernel<double, MODE_FP64><<<grid, kMatBlock, 0, s>>>(nvox, phase, tab, step_h, 1.0, eps, z_n, sigma, z,
+                                                                   partials);
+  ms_finalize_kernel<<<1, 32, 0, s>>>(partials, grid, nullptr, 0, 1.0 / (double)nvox, 1.0, red);
+  count_launch(2);
+  if (cudaGetLastError() != cudaSuccess) return GSM_ECUDA;
+  if (cudaMemcpyAsync(mean, red->mean, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GSM_ECUDA;
+  return GSM_OK;
+}

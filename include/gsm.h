@@ -32,7 +32,8 @@
  * Per-voxel status word (int32, optional output of gsm_update):
  *   bits 0-7 line-search iterations, bits 8-15 Newton iterations (including
  *   FP64 corrections), bit 16 converged, bit 17 non-finite input or result,
- *   bit 18 iteration cap reached, bit 19 Newton matrix not positive definite.
+ *   bit 18 iteration cap reached, bit 19 Newton matrix not positive definite,
+ *   bits 20-23 FP64 corrections (GSM_FP32_FP64FIX).
  */
 #ifndef GSM_GB300_H
 #define GSM_GB300_H
@@ -137,7 +138,10 @@ typedef struct ms_problem {
   int N;                      /* grid size per axis, 2 <= N <= 1024            */
   const uint8_t* phase;       /* device [N^3] phase ids < n_phases             */
   int n_phases;               /* 1 .. 16                                       */
-  const gsm_handle* laws;     /* host [n_phases] materials (precision ignored) */
+  const gsm_handle* laws;     /* host [n_phases] materials; a viscoplastic law
+                                 created with GSM_FP32_FP64FIX or GSM_FP32 is
+                                 evaluated as FP32 Newton + FP64 correction in
+                                 the FP64 iterations, GSM_FP64 in FP64      */
   int precision;              /* MS_PREC_*                                     */
 } ms_problem;
 
@@ -196,6 +200,92 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
 
 /* ms_solve -- one-shot ms_create + ms_run + ms_destroy. */
 int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_result* result, void* stream);
+
+/* ============================================ adjoint of the load history
+ *
+ * Gradient of J = w . Sigma_K (the last step's mean stress) with respect to
+ * the parameters (E, sigma0, n) of one Norton phase, through the whole load
+ * history: material update and basic scheme, discrete adjoint with per-step
+ * checkpoints (the paper's AD is local to a voxel, Sec. 4.1/5; this is its
+ * continuation to the homogenization run).  Backward over the steps, each
+ * step solves the adjoint equilibrium P_V(C_t lam) = P_V(a_u) by the
+ * basic-scheme fixed point with the consistent tangent field C_t.
+ */
+typedef struct ms_tape* ms_tape_handle;
+
+/* ms_run_taped -- ms_run from a fresh state (no resume) that keeps the
+ * checkpoints (eps_k, z_{k-1}) of every step on the device (2 * 6 * N^3
+ * doubles per step) plus adjoint work arrays (53 * N^3 doubles).  The tape
+ * refers to the context, which must outlive it.  Errors as ms_run. */
+int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_handle* tape);
+
+/* ms_adjoint -- dJ/d(E, sigma0, n) of the Norton phase `phase_id` for the
+ * weights w (host [6], tensor-shear Voigt pairing with Sigma_K) into grad
+ * (host [3]).  Each adjoint equilibrium is solved until its residual falls
+ * by `tol`, at most max_iter iterations (lam_iters: host [n_steps] or NULL).
+ * Synchronous.  Errors: GSM_EINVAL, GSM_ECUDA. */
+int ms_adjoint(ms_tape_handle tape, const double* w, int phase_id, double tol, int max_iter, double* grad,
+               int32_t* lam_iters);
+int ms_tape_destroy(ms_tape_handle tape);
+
+/* ===================================================== serving (batched jobs)
+ *
+ * A server keeps many basic-scheme jobs resident on one GPU and advances all
+ * active jobs by one iteration per serve_tick: one material launch, one
+ * Green-operator launch and one reduction launch cover every active job (per-
+ * job cuFFT calls in between), then one device-to-host copy of all jobs'
+ * errors.  Jobs that arrive while others run are admitted first come first
+ * served at the next tick when a slot (max_active) and the HBM budget allow;
+ * finished jobs release their memory at once.  A job's arithmetic does not
+ * depend on the other jobs: its results are bit-identical alone or in a mix.
+ * (The paper has no serving layer; this is the continuous-batching engine
+ * around its material law and basic scheme.)
+ */
+
+typedef struct serve_job {
+  int N;                      /* grid size, 2 <= N <= 1024                    */
+  const uint8_t* phase;       /* HOST [N^3] phase ids (copied at submission)  */
+  int n_phases;               /* 1 .. 16                                      */
+  const gsm_handle* laws;     /* host [n_phases] (copied at submission)       */
+  int precision;              /* MS_PREC_*                                    */
+  int n_steps;                /* load history, as in ms_load                  */
+  const double* E;            /* host [n_steps][6]                            */
+  const double* h;            /* host [n_steps]                               */
+  double tol;
+  int max_iter;
+  double switch_tol;          /* <= 0: 1e-5                                   */
+} serve_job;
+
+typedef struct serve_server* serve_handle;
+
+/* serve_create -- server with an HBM budget (bytes for job fields, work areas
+ * and cuFFT plans) and at most max_active (1..256) jobs per tick, on `stream`.
+ * Errors: GSM_EINVAL, GSM_ENOMEM. */
+int serve_create(serve_handle* out, size_t hbm_budget_bytes, int max_active, void* stream);
+int serve_destroy(serve_handle h);
+
+/* serve_submit -- queue a job (host copies of all inputs; the caller's arrays
+ * may be freed on return) and return its id.  GSM_ENOMEM if the job alone
+ * exceeds the budget, GSM_EINVAL on bad input. */
+int serve_submit(serve_handle h, const serve_job* job, int64_t* id);
+
+/* serve_tick -- admit queued jobs, run one iteration of every active job,
+ * retire finished ones.  Synchronous (one device-to-host copy per tick).
+ * Outputs (may be NULL): active, queued and finished-but-unfetched counts. */
+int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_finished);
+
+/* serve_job_state -- 0 queued, 1 active, 2 done, 3 done with a step at
+ * max_iter; also the current step and the material evaluations so far. */
+int serve_job_state(serve_handle h, int64_t id, int32_t* state, int32_t* step, int64_t* total_iters);
+
+/* serve_fetch -- results of a finished job (host [n_steps][6] Sigma,
+ * [n_steps] iterations and final errors); forgets the job.  Returns
+ * GSM_ENOTCONV if a step hit max_iter, GSM_EINVAL if not finished. */
+int serve_fetch(serve_handle h, int64_t id, double* Sigma, int32_t* iters, double* final_error);
+
+/* serve_job_bytes -- device bytes a job of this size takes from the budget
+ * (fields, work areas, and its cuFFT plans if none of that size exist yet). */
+size_t serve_job_bytes(int N, int precision);
 
 /*
  * ms_evaluate_noalloc -- one FP64 material evaluation of an N^3 phase field

@@ -564,4 +564,26 @@ double ora_Pi(const double* params, const double* eps, const double* y, const do
   Law L; make_law(1, params, &L); return Pi(L, eps, y, yn, h);
 }
 
+// Batched Newton matrix K = psi_yy + phi_vv/h and dissipation Hessian phi_vv
+// at converged states (n voxels, y and y_n [n][5]); for the adjoint.
+// Voxels with y = y_n (no flow) get K = psi_yy + 0 and phi_vv = 0 when n > 1
+// (the unbounded Hessian multiplies a zero adjoint there: dy/dy_n = 0).
+void ora_newton_matrix_batch(const double* params, int64_t n, const double* y, const double* yn, double h,
+                             double* K, double* Hphi) {
+  Law L; make_law(1, params, &L);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double v[5], H1[5][5], H2[5][5];
+    rate(y + 5 * i, yn + 5 * i, h, v);
+    psi_yy(L, H1);
+    const bool finite = phi_vv(L, v, H2);
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) {
+        const double hp = finite ? H2[a][b] : 0.0;
+        Hphi[25 * i + 5 * a + b] = hp;
+        K[25 * i + 5 * a + b] = H1[a][b] + hp / h;
+      }
+  }
+}
+
 }  // extern "C"

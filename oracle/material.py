@@ -60,6 +60,7 @@ def _load():
         lib.ora_Pi.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double]
         lib.ora_Pi.restype = ctypes.c_double
         lib.ora_max_threads.restype = ctypes.c_int
+        lib.ora_newton_matrix_batch.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -189,3 +190,14 @@ def incremental_potential(params, eps, y, y_n, h):
     return _load().ora_Pi(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(y)), _ptr(_f64(y_n)), float(h))
 
 
+
+
+def newton_matrix_batch(params, y, y_n, h):
+    """K = psi_yy + phi_vv/h and phi_vv at n states; y, y_n [n, 5] -> ([n,5,5], [n,5,5])."""
+    y = _f64(y, (-1, 5))
+    n = y.shape[0]
+    y_n = _f64(y_n, (n, 5))
+    K = np.empty((n, 5, 5))
+    H = np.empty((n, 5, 5))
+    _load().ora_newton_matrix_batch(_ptr(_params(params)), n, _ptr(y), _ptr(y_n), float(h), _ptr(K), _ptr(H))
+    return K, H

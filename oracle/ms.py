@@ -185,3 +185,136 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     if record:
         out["history"] = hist
     return out
+
+
+# ------------------------------------------------------------------ adjoint
+# Gradient of J = w . Sigma_K (final mean stress) with respect to the
+# parameters theta = (E, sigma0, n) of one Norton phase, through the whole
+# load history (the paper's AD is local to a voxel, Sec. 5; this is the
+# discrete adjoint of the implicit-Euler update plus the basic scheme).
+#
+# Step k maps (z_{k-1}, theta) to (sigma_k, z_k) through the equilibrium
+# constraint P_V sigma(E_k + u) = 0 on compatible zero-mean fluctuations u.
+# Given adjoints (g_sig, g_z) of (sigma_k, z_k):
+#   a_u   = C_t^T g_sig + (dz/deps)^T g_z,          dz/deps = P K^-1 P^T C
+#   find compatible zero-mean lam with P_V (C_t lam) = P_V a_u
+#   a     = g_sig - lam
+#   b     = K^-1 (P^T g_z - P^T C a)
+#   g_{z,k-1} = (phi_vv / h) b   on the components (11, 22, 23, 13, 12)
+#   dJ/dtheta += sum_x a . d sigma/d theta|_y - b . dR/d theta
+# with R = psi_y + phi_v and, at the converged state, phi_v = P^T sigma:
+#   d sigma/dE|_y = sigma/E, dR/dE = -P^T sigma/E,
+#   dR/d sigma0 = P^T sigma / sigma0,
+#   dR/dn = P^T sigma * (-ln(s/edot0) / n^2),  s = sqrt(v^T G v), v = (y - y_n)/h.
+# Voxels without flow (y = y_n exactly) have dy/dy_n = I: g_{z,k-1} = P^T g_z - P^T C a.
+
+Y_IDX = [0, 1, 3, 4, 5]
+
+
+def stiffness_voigt(E, nu):
+    lam, mu = M.lame(E, nu)
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    C[:3, :3] += 2 * mu * np.eye(3)
+    C[3:, 3:] = mu * np.eye(3)
+    return C
+
+
+def solve_taped(phase, laws, loads, hs, tol=1e-12, max_iter=100000):
+    """Forward solve keeping per-step checkpoints (eps_k, z_{k-1})."""
+    r = solve(phase, laws, loads, hs, tol=tol, max_iter=max_iter, record=True)
+    nvox = np.asarray(phase).size
+    tape = []
+    z_prev = np.zeros((nvox, 6))
+    for eps_k, z_k, _ in r["history"]:
+        tape.append((eps_k, z_prev))
+        z_prev = z_k
+    r["tape"] = tape
+    return r
+
+
+def _lambda_solve(Ct, a_u, N, lam0, mu0, tol, max_iter):
+    """Compatible zero-mean lam with P_V(C_t lam) = P_V(a_u) by the basic-scheme fixed point."""
+    nvox = N ** 3
+    lam = np.zeros((nvox, 6))
+    first = None
+    for it in range(max_iter):
+        tau = np.einsum("nij,nj->ni", Ct, lam) - a_u
+        tau_hat = np.stack([np.fft.fftn(tau[:, c].reshape(N, N, N)) for c in range(6)])
+        k, excluded = wavevectors(N)
+        xi = 2 * np.pi * k
+        T = voigt_to_tensor_field(np.moveaxis(tau_hat, 0, -1), engineering=False)
+        q = np.einsum("ij...,j...->i...", T, xi)
+        wq = (np.abs(q) ** 2).sum(axis=0)
+        wq[excluded] = 0.0
+        err = np.sqrt(wq.sum())
+        first = err if first is None else first
+        if err <= tol * max(first, 1e-300):
+            break
+        d_hat = gamma0_apply(voigt_to_tensor_field(np.moveaxis(tau_hat, 0, -1), engineering=False), lam0, mu0, N)
+        lam_hat = np.stack([np.fft.fftn(lam[:, c].reshape(N, N, N)) for c in range(6)], axis=-1) - d_hat
+        lam_hat[0, 0, 0, :] = 0.0
+        lam = np.stack([np.fft.ifftn(lam_hat[..., c]).real.reshape(-1) for c in range(6)], axis=-1)
+    return lam, it + 1
+
+
+def adjoint(phase, laws, loads, hs, tape, w, phase_id, tol=1e-12, max_iter=100000):
+    """dJ/d(E, sigma0, n) of phase `phase_id` for J = w . Sigma_K."""
+    ph = np.asarray(phase).reshape(-1)
+    N = np.asarray(phase).shape[0]
+    nvox = N ** 3
+    lam0, mu0 = reference_medium(laws)
+    kind, prm = laws[phase_id]
+    assert kind == M.KIND_NORTON
+    E_mod, nu, sigma0, edot0, n_exp = prm
+    Pm = M.P_MATRIX
+    Gm = M.G_MATRIX
+    w = np.asarray(w, dtype=np.float64)
+    K_steps = len(tape)
+    g_z = np.zeros((nvox, 6))
+    grad = np.zeros(3)
+    lam_iters = []
+    for k in range(K_steps - 1, -1, -1):
+        eps_k, z_prev = tape[k]
+        h = hs[k]
+        g_sig = np.tile(w / nvox, (nvox, 1)) if k == K_steps - 1 else np.zeros((nvox, 6))
+        Ct = np.zeros((nvox, 6, 6))
+        a_u = np.zeros((nvox, 6))
+        local = {}
+        for p, (kind_p, prm_p) in enumerate(laws):
+            idx = np.nonzero(ph == p)[0]
+            if idx.size == 0:
+                continue
+            sig, z, Ct_p = M.update(kind_p, prm_p, eps_k[idx], z_prev[idx], h, tangent=True)
+            Ct[idx] = Ct_p
+            if kind_p == M.KIND_NORTON:
+                y, yn = z[:, Y_IDX], z_prev[idx][:, Y_IDX]
+                Kmat, Hphi = M.newton_matrix_batch(prm_p, y, yn, h)
+                C = stiffness_voigt(prm_p[0], prm_p[1])
+                gy = g_z[idx] @ Pm                           # P^T g_z
+                t = np.linalg.solve(Kmat, gy[..., None])[..., 0]
+                a_u[idx] = np.einsum("nji,nj->ni", Ct_p, g_sig[idx]) + (t @ Pm.T) @ C.T  # C_t^T g + C P t
+                local[p] = (idx, sig, y, yn, Kmat, Hphi, C)
+            else:
+                a_u[idx] = np.einsum("nji,nj->ni", Ct_p, g_sig[idx])
+        lam, it = _lambda_solve(Ct, a_u, N, lam0, mu0, tol, max_iter)
+        lam_iters.append(it)
+        a = g_sig - lam
+        g_z_prev = np.zeros((nvox, 6))
+        for p, (idx, sig, y, yn, Kmat, Hphi, C) in local.items():
+            rhs = g_z[idx] @ Pm - (a[idx] @ C.T) @ Pm      # P^T g_z - P^T C a
+            b = np.linalg.solve(Kmat, rhs[..., None])[..., 0]
+            flow = np.any(y != yn, axis=1)
+            g_yn = np.where(flow[:, None], np.einsum("nij,nj->ni", Hphi, b) / h, rhs)
+            g_z_prev[idx[:, None], np.array(Y_IDX)[None, :]] = g_yn
+            if p != phase_id:
+                continue
+            Pts = sig @ Pm                                   # P^T sigma
+            v = (y - yn) / h
+            s = np.sqrt(np.einsum("ni,ij,nj->n", v, Gm, v))
+            logt = np.where(s > 0, np.log(np.where(s > 0, s, 1.0) / edot0), 0.0)
+            grad[0] += np.sum(a[idx] * sig) / E_mod + np.sum(b * Pts) / E_mod
+            grad[1] += -np.sum(b * Pts) / sigma0
+            grad[2] += np.sum(np.sum(b * Pts, axis=1) * logt) / n_exp ** 2
+        g_z = g_z_prev
+    return grad, lam_iters

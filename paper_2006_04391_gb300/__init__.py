@@ -28,7 +28,9 @@ ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 <<
 
 # Exported symbols declared in include/gsm.h.
 EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kernel_launches",
-           "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc")
+           "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc",
+           "serve_create", "serve_destroy", "serve_submit", "serve_tick", "serve_job_state", "serve_fetch",
+           "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy")
 
 _lib = None
 
@@ -54,6 +56,13 @@ class ms_load(ctypes.Structure):
 class ms_state(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_void_p), ("z", ctypes.c_void_p), ("resume", ctypes.c_int),
                 ("E_prev", ctypes.c_double * 6)]
+
+
+class serve_job(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int),
+                ("laws", ctypes.POINTER(ctypes.c_void_p)), ("precision", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("E", ctypes.POINTER(ctypes.c_double)), ("h", ctypes.POINTER(ctypes.c_double)),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("switch_tol", ctypes.c_double)]
 
 
 class ms_result(ctypes.Structure):
@@ -82,6 +91,20 @@ def load(path=None):
     if hasattr(lib, "ms_evaluate_noalloc"):
         lib.ms_evaluate_noalloc.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp), dbl, vp, vp, vp, vp,
                                             vp, vp]
+    i32p, i64p, dblp = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(dbl)
+    if hasattr(lib, "serve_create"):
+        lib.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ctypes.c_int, vp]
+        lib.serve_destroy.argtypes = [vp]
+        lib.serve_submit.argtypes = [vp, ctypes.POINTER(serve_job), i64p]
+        lib.serve_tick.argtypes = [vp, i32p, i32p, i32p]
+        lib.serve_job_state.argtypes = [vp, i64, i32p, i32p, i64p]
+        lib.serve_fetch.argtypes = [vp, i64, dblp, i32p, dblp]
+        lib.serve_job_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.serve_job_bytes.restype = ctypes.c_size_t
+    if hasattr(lib, "ms_run_taped"):
+        lib.ms_run_taped.argtypes = [vp, ctypes.POINTER(ms_load), ctypes.POINTER(ms_result), ctypes.POINTER(vp)]
+        lib.ms_adjoint.argtypes = [vp, dblp, ctypes.c_int, dbl, ctypes.c_int, dblp, i32p]
+        lib.ms_tape_destroy.argtypes = [vp]
     for name in ("ms_create", "ms_destroy", "ms_run", "ms_solve", "ms_workspace_bytes"):
         if hasattr(lib, name):
             fn = getattr(lib, name)
@@ -261,6 +284,55 @@ def ms_evaluate_noalloc(phase, laws, h, eps, z_n, sigma, z, mean, stream=None):
     _check(rc, "ms_evaluate_noalloc")
 
 
+class Tape:
+    """Checkpoints of a load history (``ms_run_taped``); keeps its context alive."""
+
+    def __init__(self, handle, ctx, n_steps):
+        self.handle, self.ctx, self.n_steps = handle, ctx, n_steps
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ms_tape_destroy(self.handle)
+            self.handle = None
+
+
+def _result_struct(n):
+    Sigma = np.zeros((n, 6))
+    iters = np.zeros(n, dtype=np.int32)
+    ferr = np.zeros(n)
+    f32 = np.zeros(n, dtype=np.int32)
+    res = ms_result(Sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    ferr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    f32.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0)
+    return res, {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32}
+
+
+def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000):
+    """Load history from a fresh state keeping per-step checkpoints; returns (result, Tape)."""
+    lib = load()
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, None, 0.0)
+    res, out = _result_struct(n)
+    th = ctypes.c_void_p()
+    rc = lib.ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th))
+    if rc not in (GSM_OK, GSM_ENOTCONV):
+        _check(rc, "ms_run_taped")
+    out["rc"] = rc
+    return out, Tape(th, ctx, n)
+
+
+def ms_adjoint(tape, w, phase_id=0, tol=1e-10, max_iter=20000):
+    """dJ/d(E, sigma0, n) of a Norton phase for J = w . Sigma_K; returns (grad[3], lam_iters)."""
+    lib = load()
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(6))
+    grad = np.zeros(3)
+    its = np.zeros(tape.n_steps, dtype=np.int32)
+    _check(lib.ms_adjoint(tape.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(phase_id),
+                          float(tol), int(max_iter), grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "ms_adjoint")
+    return grad, its
+
+
 def ms_destroy(ctx):
     if ctx.handle:
         load().ms_destroy(ctx.handle)
@@ -274,3 +346,119 @@ def ms_solve(phase, laws, E, hs, precision=MS_PREC_FP64, stream=None, **kw):
         return ms_run(ctx, E, hs, **kw)
     finally:
         ms_destroy(ctx)
+
+
+# ------------------------------------------------------------------ serving
+
+SERVE_QUEUED, SERVE_ACTIVE, SERVE_DONE, SERVE_DONE_NOTCONV = 0, 1, 2, 3
+
+
+class Server:
+    """A serving engine (``serve_create``): jobs are basic-scheme solves that
+    are admitted by an HBM budget and advanced together, one batched
+    iteration per :meth:`tick`."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, stream=None):
+        lib = load()
+        self.handle = ctypes.c_void_p()
+        _check(lib.serve_create(ctypes.byref(self.handle), int(hbm_budget_bytes), int(max_active),
+                                _stream_ptr(stream)), "serve_create")
+        self.n_steps = {}
+
+    def submit(self, phase, laws, E, hs, tol=1e-6, max_iter=20000, precision=MS_PREC_FP32_BULK, switch_tol=0.0):
+        """Queue a job; ``phase`` is a host uint8 array (N, N, N).  Returns the job id."""
+        lib = load()
+        ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
+        hs = np.ascontiguousarray(np.asarray(hs, dtype=np.float64).reshape(-1))
+        arr = (ctypes.c_void_p * len(laws))(*[m.handle.value for m in laws])
+        job = serve_job(int(ph.shape[0]), ph.ctypes.data, len(laws), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
+                        int(precision), E.shape[0], E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
+                        float(switch_tol))
+        jid = ctypes.c_int64()
+        _check(lib.serve_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)), "serve_submit")
+        self.n_steps[jid.value] = E.shape[0]
+        return jid.value
+
+    def tick(self):
+        """One batched iteration; returns (active, queued, finished) counts."""
+        a, q, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().serve_tick(self.handle, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)), "serve_tick")
+        return a.value, q.value, f.value
+
+    def state(self, jid):
+        st, step, it = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().serve_job_state(self.handle, int(jid), ctypes.byref(st), ctypes.byref(step),
+                                      ctypes.byref(it)), "serve_job_state")
+        return st.value, step.value, it.value
+
+    def fetch(self, jid):
+        n = self.n_steps.pop(jid)
+        Sigma = np.zeros((n, 6))
+        iters = np.zeros(n, dtype=np.int32)
+        ferr = np.zeros(n)
+        rc = load().serve_fetch(self.handle, int(jid), Sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                ferr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if rc not in (GSM_OK, GSM_ENOTCONV):
+            _check(rc, "serve_fetch")
+        return {"Sigma": Sigma, "iters": iters, "final_error": ferr, "rc": rc}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+
+def serve_job_bytes(N, precision=MS_PREC_FP32_BULK):
+    return int(load().serve_job_bytes(int(N), int(precision)))
+
+
+# ------------------------------------------------- differentiable homogenization
+
+def _effective_stress_function():
+    import torch
+
+    class EffectiveStress(torch.autograd.Function):
+        """Sigma_K(theta) for theta = (E, sigma0, n) of the Norton phase; the
+        backward pass is the hand-written adjoint of the load history."""
+
+        @staticmethod
+        def forward(ctx, theta, phase, E_loads, hs, other_laws, nu, edot0, tol, adj_tol, precision):
+            th = theta.detach().cpu().double().numpy()
+            laws = [norton(float(th[0]), nu, float(th[1]), edot0, float(th[2]), precision=precision)]
+            laws += [elastic(*p) for p in other_laws]
+            mctx = ms_create(phase, laws, MS_PREC_FP64)
+            res, tape = ms_run_taped(mctx, E_loads, hs, tol=tol)
+            ctx.tape = tape
+            ctx.adj_tol = adj_tol
+            ctx.laws = laws
+            return torch.tensor(res["Sigma"][-1], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            grad, _ = ms_adjoint(ctx.tape, grad_out.detach().cpu().double().numpy(), 0, tol=ctx.adj_tol)
+            return (torch.tensor(grad, dtype=torch.float64),) + (None,) * 9
+
+    return EffectiveStress
+
+
+_EFF = None
+
+
+def effective_stress(theta, phase, E_loads, hs, inclusions=((400.0, 0.2),), nu=0.3, edot0=1.0, tol=1e-10,
+                     adj_tol=1e-10, precision=GSM_FP64):
+    """Differentiable final mean stress of a Norton-matrix composite.
+
+    theta: float64 tensor (E, sigma0, n) of the matrix (phase id 0); phase:
+    uint8 CUDA tensor (N, N, N) with ids 1.. for the elastic ``inclusions``.
+    Returns Sigma_K (6,) whose backward pass runs ``ms_adjoint``."""
+    global _EFF
+    if _EFF is None:
+        _EFF = _effective_stress_function()
+    return _EFF.apply(theta, phase, E_loads, hs, tuple(inclusions), nu, edot0, tol, adj_tol, precision)

@@ -41,6 +41,8 @@
 #define AD_HD inline
 #endif
 
+#include "fpow.cuh"
+
 namespace gsm {
 namespace ad {
 
@@ -186,13 +188,26 @@ AD_HD float log_(float x) { return logf(x); }
 template <class T, int N, unsigned A>
 AD_HD Tan<T, N, A> log_(const Tan<T, N, A>& x) { return chain(x, log_(x.v), inv(x.v)); }
 
-// x^p for x > 0 and a passive exponent p: exp(p log x).
-AD_HD double pow_(double x, double p) { return std::exp(p * std::log(x)); }
+// x^p for x > 0 and a passive exponent p.  FP64: the table-driven power of
+// fpow.cuh (~26 FP64 operations; exp(p log x) takes ~54 FMA-equivalents and
+// the general pow() ~98 on GB300, measured).  FP32: exp(p log x).
+AD_HD double pow_(double x, double p) { return fpow::pow_pos(x, p); }
 AD_HD float pow_(float x, float p) { return expf(p * logf(x)); }
 template <class T, int N, unsigned A>
 AD_HD Tan<T, N, A> pow_(const Tan<T, N, A>& x, T p) {
   const T r = pow_(x.v, p);
-  return chain(x, r, p * r * inv(x.v));
+  if constexpr (sizeof(T) == 4) {
+    // FP32: p x^(p-1) alone can overflow for tiny x where the product with
+    // the tangent does not; scale the tangent by 1/x first
+    const T ix = inv(x.v), pr = p * r;
+    Tan<T, N, A> o;
+    o.v = r;
+#pragma unroll
+    for (int k = 0; k < N; ++k) o.d[k] = has<A>(k) ? pr * (x.d[k] * ix) : T(0);
+    return o;
+  } else {
+    return chain(x, r, p * r * inv(x.v));
+  }
 }
 
 // -------------------------------------------------------- adjoint accumulators
@@ -368,10 +383,24 @@ template <class T> struct FSq {
   template <class X> AD_HD X f(const X& x) const { return x * x; }
   template <class X> AD_HD X df(const X& x, const X&) const { return x * T(2); }
 };
-template <class T> struct FPow {   // x^p, x > 0, passive p
-  T p;
-  template <class X> AD_HD X f(const X& x) const { return pow_(x, p); }
-  template <class X> AD_HD X df(const X& x, const X& r) const { return (r * p) * inv(x); }
+// x^p for x > 0 and a passive exponent p.  The node caches w = x^(p-1):
+// x^p = x w and d/dx = p w, so a first-order sweep needs no division (the
+// second-order tangent of w carries the one reciprocal).
+template <class L> struct PowN : Expr<PowN<L>> {
+  using value_type = typename L::value_type;
+  using scalar = typename L::scalar;
+  hold_t<L> l;
+  scalar p;
+  mutable value_type v, w;
+  AD_HD PowN(const L& a, scalar e) : l(a), p(e) {}
+  AD_HD value_type fwd() const {
+    const value_type x = l.fwd();
+    w = pow_(x, p - scalar(1));
+    v = x * w;
+    return v;
+  }
+  AD_HD const value_type& val() const { return v; }
+  template <class B> AD_HD void back(const B& bv) const { l.back(bv * (w * p)); }
 };
 
 // ------------------------------------------------------------------ operators
@@ -406,9 +435,7 @@ template <class A> AD_HD Unary<A, FSqrt<typename A::scalar>> sqrt(const Expr<A>&
 template <class A> AD_HD Unary<A, FExp<typename A::scalar>> exp(const Expr<A>& a) { return {a.self(), {}}; }
 template <class A> AD_HD Unary<A, FLog<typename A::scalar>> log(const Expr<A>& a) { return {a.self(), {}}; }
 template <class A> AD_HD Unary<A, FSq<typename A::scalar>> sq(const Expr<A>& a) { return {a.self(), {}}; }
-template <class A> AD_HD Unary<A, FPow<typename A::scalar>> pow(const Expr<A>& a, typename A::scalar p) {
-  return {a.self(), FPow<typename A::scalar>{p}};
-}
+template <class A> AD_HD PowN<A> pow(const Expr<A>& a, typename A::scalar p) { return PowN<A>(a.self(), p); }
 
 // ---------------------------------------------------------------- leaf packs
 // A heterogeneous, fixed-size set of leaves addressed by a compile-time index:

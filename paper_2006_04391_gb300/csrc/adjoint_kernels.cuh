@@ -1,0 +1,296 @@
+// Device kernels of the adjoint of the load history (basic scheme + implicit
+// Euler material update).  The paper differentiates only locally, inside one
+// material evaluation (Sec. 4.1, Eq. tangent_formula; Sec. 5); this is the
+// discrete adjoint of a whole homogenization run, hand-written on top of the
+// AD blocks of the law.  Included by ms_solve.cu only.
+//
+// For J = w . Sigma_K and step k with checkpoint (eps_k, z_{k-1}), given the
+// adjoints g_sig (uniform w/N^3 at the last step, else 0) and g_z of
+// (sigma_k, z_k):
+//   prepare:  re-solve the update, K = psi_yy + phi_vv/h, C_t = psi_ee + psi_ey dy/deps,
+//             a_u = C_t g_sig + (dz/deps)^T g_z = C_t g_sig - psi_ey K^-1 (P^T g_z)
+//   solve:    compatible zero-mean lam with P_V(C_t lam) = P_V(a_u)     (host loop)
+//   finish:   a = g_sig - lam,  b = K^-1 (P^T g_z + psi_ye a)   (psi_ye a = -P^T C a)
+//             g_{z,k-1} = (phi_vv/h) b on (z11, z22, g23, g13, g12)  (= P^T g_z + psi_ye a
+//             where the voxel does not flow, dy/dy_n = I there)
+//             dJ/dtheta += a . dsigma/dtheta|_y - b . dR/dtheta  (Norton: theta = E, sigma0, n)
+#pragma once
+
+#include "ms_kernels.cuh"
+
+namespace gsm {
+namespace {
+
+constexpr int kAdjBlock = 128;
+
+struct NortonTheta {
+  double E, sigma0, edot0, n;
+};
+
+// P^T g for a strain-adjoint 6-vector g (z = P y).
+__device__ __forceinline__ void pt_of(const double (&g)[6], double (&gy)[5]) {
+  gy[0] = g[0] - g[2];
+  gy[1] = g[1] - g[2];
+  gy[2] = g[3];
+  gy[3] = g[4];
+  gy[4] = g[5];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kAdjBlock) adj_prepare_kernel(int64_t nvox, const uint8_t* __restrict__ phase,
+                                                                const PhaseTable* __restrict__ tab, double h,
+                                                                const double* __restrict__ eps_k,
+                                                                const double* __restrict__ zprev, double gs0,
+                                                                double gs1, double gs2, double gs3, double gs4,
+                                                                double gs5, const double* __restrict__ g_z,
+                                                                double* __restrict__ Ct21, double* __restrict__ a_u,
+                                                                double* __restrict__ yK) {
+  const double gs[6] = {gs0, gs1, gs2, gs3, gs4, gs5};
+  const Step hs = make_step(h);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nvox; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < nvox;
+    const int ph = in ? (int)phase[i] : 0;
+    const bool vp = in && tab->kind[ph] == GSM_PSI_ELASTIC_VP_DEV;
+    double e[6], zi[6], s[6], zo[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      e[c] = in ? eps_k[c * nvox + i] : 0.0;
+      zi[c] = vp ? zprev[c * nvox + i] : 0.0;
+    }
+    if constexpr (MODE == MODE_FP64) voxel_fp64<NortonDev>(tab->p64[ph], e, zi, hs, vp, s, zo, nullptr);
+    else voxel_fp32_fix<NortonDev>(tab->p64[ph], tab->p32[ph], e, zi, hs, vp, s, zo, nullptr);
+    if (!in) continue;
+    double C[6][6], au[6];
+    if (vp) {
+      const LawParams<double>& p = tab->p64[ph];
+      const double y[5] = {zo[0], zo[1], zo[3], zo[4], zo[5]};
+      const double yn[5] = {zi[0], zi[1], zi[3], zi[4], zi[5]};
+      double sig[6], Cee[6][6], Cey[6][5], Cye[5][6], g[5], K[5][5];
+      psi_blocks<NortonDev>(p, e, y, sig, Cee, Cey, Cye);
+      psi_y_yy<NortonDev>(p, e, y, g, K);
+      bool flow = false;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) flow = flow || (y[a] != yn[a]);
+      double gz[6], gy[5], t[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) gz[c] = g_z[c * nvox + i];
+      pt_of(gz, gy);
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) C[r][c] = Cee[r][c];
+      if (flow) {
+        const double inv_h = 1.0 / h;
+        double v[5], gv[5], Hv[5][5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) v[a] = (y[a] - yn[a]) * inv_h;
+        phi_v_vv<NortonDev>(p, v, gv, Hv);
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) K[a][b] += Hv[a][b] * inv_h;
+        Chol5<double> ch;
+        ch.factor(K);
+        ch.solve(gy, t);
+        // C_t = Cee + Cey dy/deps, dy/deps = -K^-1 Cye
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          double rhs[5], dy[5];
+#pragma unroll
+          for (int a = 0; a < 5; ++a) rhs[a] = -Cye[a][c];
+          ch.solve(rhs, dy);
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc += Cey[r][a] * dy[a];
+            C[r][c] += acc;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc += C[c][r] * gs[c];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) acc -= Cey[r][a] * t[a];
+        au[r] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) yK[a * nvox + i] = y[a];
+      int q = 5;
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = a; b < 5; ++b) yK[(q++) * nvox + i] = K[a][b];
+    } else {
+      double C21[21];
+      voxel_elastic<double>(tab->p64[ph], e, s, C21);
+      int q = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+          C[r][c] = C21[q];
+          C[c][r] = C21[q];
+          ++q;
+        }
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc += C[c][r] * gs[c];
+        au[r] = acc;
+      }
+    }
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) Ct21[(q++) * nvox + i] = 0.5 * (C[r][c] + C[c][r]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a_u[c * nvox + i] = au[c];
+  }
+}
+
+// tau = C_t lam - a_u, lam = lam_raw / N^3 (C2R output).
+__global__ void adj_tau_kernel(int64_t nvox, const double* __restrict__ Ct21, const double* __restrict__ a_u,
+                               const double* __restrict__ lam_raw, double inv_n3, double* __restrict__ tau) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    double l[6], C[6][6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) l[c] = lam_raw[c * nvox + i] * inv_n3;
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) {
+        const double v = Ct21[(q++) * nvox + i];
+        C[r][c] = v;
+        C[c][r] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      double acc = -a_u[r * nvox + i];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc += C[r][c] * l[c];
+      tau[r * nvox + i] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kAdjBlock) adj_finish_kernel(
+    int64_t nvox, const uint8_t* __restrict__ phase, const PhaseTable* __restrict__ tab, double h, int phase_id,
+    NortonTheta th, const double* __restrict__ eps_k, const double* __restrict__ zprev, double gs0, double gs1,
+    double gs2, double gs3, double gs4, double gs5, const double* __restrict__ g_z, const double* __restrict__ lam_raw,
+    double inv_n3, const double* __restrict__ yK, double* __restrict__ g_z_prev, double* __restrict__ partials) {
+  const double gs[6] = {gs0, gs1, gs2, gs3, gs4, gs5};
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    const int ph = (int)phase[i];
+    double out[6] = {0, 0, 0, 0, 0, 0};
+    if (tab->kind[ph] == GSM_PSI_ELASTIC_VP_DEV) {
+      const LawParams<double>& p = tab->p64[ph];
+      double e[6], a[6], gz[6], gy[5], y[5], yn[5], K[5][5];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        e[c] = eps_k[c * nvox + i];
+        a[c] = gs[c] - lam_raw[c * nvox + i] * inv_n3;
+        gz[c] = g_z[c * nvox + i];
+      }
+      yn[0] = zprev[i];
+      yn[1] = zprev[nvox + i];
+      yn[2] = zprev[3 * nvox + i];
+      yn[3] = zprev[4 * nvox + i];
+      yn[4] = zprev[5 * nvox + i];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) y[b] = yK[b * nvox + i];
+      int q = 5;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = r; c < 5; ++c) {
+          const double v = yK[(q++) * nvox + i];
+          K[r][c] = v;
+          K[c][r] = v;
+        }
+      pt_of(gz, gy);
+      double sig[6], Cee[6][6], Cey[6][5], Cye[5][6], psy[5];
+      psi_blocks<NortonDev>(p, e, y, sig, Cee, Cey, Cye);
+      psi_y_and_stress<NortonDev>(p, e, y, psy, sig);
+      double rhs[5];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        double s = gy[r];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s += Cye[r][c] * a[c];
+        rhs[r] = s;
+      }
+      bool flow = false;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) flow = flow || (y[b] != yn[b]);
+      double b5[5] = {0, 0, 0, 0, 0}, gyn[5];
+      double v[5];
+      const double inv_h = 1.0 / h;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) v[b] = (y[b] - yn[b]) * inv_h;
+      if (flow) {
+        Chol5<double> ch;
+        ch.factor(K);
+        ch.solve(rhs, b5);
+        double gv[5], Hv[5][5];
+        phi_v_vv<NortonDev>(p, v, gv, Hv);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          double s = 0.0;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) s += Hv[r][c] * b5[c];
+          gyn[r] = s * inv_h;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) gyn[r] = rhs[r];
+      }
+      out[0] = gyn[0];
+      out[1] = gyn[1];
+      out[3] = gyn[2];
+      out[4] = gyn[3];
+      out[5] = gyn[4];
+      if (ph == phase_id) {
+        // P^T sigma = -psi_y; dR/dE = psi_y / E, dR/dsigma0 = phi_v / sigma0 = P^T sigma / sigma0,
+        // dR/dn = P^T sigma (-ln(s/edot0) / n^2); dsigma/dE|_y = sigma / E
+        double bP = 0.0, aS = 0.0;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) bP -= b5[r] * psy[r];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) aS += a[c] * sig[c];
+        const double qv = (4.0 / 3.0) * (v[0] * v[0] + v[1] * v[1] + v[0] * v[1]) +
+                          (1.0 / 3.0) * (v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
+        const double logt = qv > 0.0 ? 0.5 * log(qv) - log(th.edot0) : 0.0;
+        acc[0] += (aS + bP) / th.E;
+        acc[1] += -bP / th.sigma0;
+        acc[2] += bP * logt / (th.n * th.n);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g_z_prev[c * nvox + i] = out[c];
+  }
+  block_sum<3>(acc, partials, gridDim.x);
+}
+
+__global__ void adj_sum_kernel(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t < 3) {
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += partials[t * n + b];
+    out[t] = s;
+  }
+}
+
+}  // namespace
+}  // namespace gsm

@@ -27,7 +27,7 @@ template <class T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p
 // Viscoplastic (Norton) voxels.
 template <int MODE, bool TAN>
 __global__ void __launch_bounds__(kBlock) norton_kernel(int64_t n, int64_t ld, LawParams<double> p,
-                                                        LawParams<float> pf, double h,
+                                                        LawParams<float> pf, Step hs,
                                                         const void* __restrict__ eps_,
                                                         const void* __restrict__ zn_, void* __restrict__ sig_,
                                                         void* __restrict__ z_, void* __restrict__ tan_,
@@ -51,15 +51,15 @@ __global__ void __launch_bounds__(kBlock) norton_kernel(int64_t n, int64_t ld, L
     IO t[21];
     unsigned st;
     if constexpr (MODE == MODE_FP64) {
-      st = voxel_fp64<NortonDev>(p, e, zi, h, active, s, zo, TAN ? t : nullptr);
+      st = voxel_fp64<NortonDev>(p, e, zi, hs, active, s, zo, TAN ? t : nullptr);
     } else if constexpr (MODE == MODE_FP32_FIX) {
-      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, h, active, s, zo, TAN ? t : nullptr);
+      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, hs, active, s, zo, TAN ? t : nullptr);
     } else {
-      st = voxel_fp32<NortonDev>(pf, e, zi, (float)h, active, s, zo, TAN ? t : nullptr);
+      st = voxel_fp32<NortonDev>(pf, e, zi, hs, active, s, zo, TAN ? t : nullptr);
     }
     bool fin = true;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) fin = fin && isfinite(s[c]) && isfinite(zo[c]);
+    for (int c = 0; c < 6; ++c) fin = fin && finite64(s[c]) && finite64(zo[c]);
     if (!fin) st |= ST_NONFINITE;
     if (active) {
 #pragma unroll
@@ -106,13 +106,14 @@ __global__ void __launch_bounds__(kBlock) elastic_kernel(int64_t n, int64_t ld, 
   }
 }
 
-template <class K> int grid_for(K kernel, int64_t n) {
-  static int per_sm = 0;  // one static per kernel instantiation
-  if (per_sm == 0) {
+// Persistent grid: SMs x resident blocks of this instantiation (one cached
+// occupancy per kernel: the template parameter is the kernel itself).
+template <auto Kernel> int grid_for(int64_t n) {
+  static const int per_sm = [] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b <= 0) b = 1;
-    per_sm = b;
-  }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, kBlock, 0) != cudaSuccess || b <= 0) b = 1;
+    return b;
+  }();
   const int64_t need = (n + kBlock - 1) / kBlock;
   const int64_t cap = (int64_t)sm_count() * per_sm;
   return (int)(need < cap ? need : cap);
@@ -121,8 +122,7 @@ template <class K> int grid_for(K kernel, int64_t n) {
 template <int MODE, bool TAN>
 cudaError_t launch_norton(const Material& m, int64_t n, int64_t ld, double h, const void* eps, const void* zn,
                           void* sig, void* z, void* tan, int32_t* status, cudaStream_t s) {
-  auto k = norton_kernel<MODE, TAN>;
-  norton_kernel<MODE, TAN><<<grid_for(k, n), kBlock, 0, s>>>(n, ld, m.p64, m.p32, h, eps, zn, sig, z, tan, status);
+  norton_kernel<MODE, TAN><<<grid_for<norton_kernel<MODE, TAN>>(n), kBlock, 0, s>>>(n, ld, m.p64, m.p32, make_step(h), eps, zn, sig, z, tan, status);
   count_launch();
   return cudaGetLastError();
 }
@@ -130,8 +130,7 @@ cudaError_t launch_norton(const Material& m, int64_t n, int64_t ld, double h, co
 template <class IO, bool TAN>
 cudaError_t launch_elastic(const LawParams<IO>& p, int64_t n, int64_t ld, const void* eps, const void* zn,
                            void* sig, void* z, void* tan, int32_t* status, cudaStream_t s) {
-  auto k = elastic_kernel<IO, TAN>;
-  elastic_kernel<IO, TAN><<<grid_for(k, n), kBlock, 0, s>>>(
+  elastic_kernel<IO, TAN><<<grid_for<elastic_kernel<IO, TAN>>(n), kBlock, 0, s>>>(
       n, ld, p, static_cast<const IO*>(eps), static_cast<const IO*>(zn), static_cast<IO*>(sig),
       static_cast<IO*>(z), static_cast<IO*>(tan), status);
   count_launch();

@@ -78,6 +78,45 @@ struct NortonDev {
     auto q = S(4.0 / 3.0) * (sq(v0) + sq(v1) + v0 * v1) + S(1.0 / 3.0) * (sq(v2) + sq(v3) + sq(v4));
     return p.c_phi * pow(q, p.a_phi);
   }
+
+  // psi depends on (eps, y) only through tr(eps) and dev(eps) - P y (P y is
+  // traceless, C isotropic).  With the trial strain e_s = dev(eps) - P y_n:
+  //   psi_y(eps, y_n + w)  = psi_y(e_s, w),
+  //   sigma(eps, y_n + w)  = sigma(e_s, w) + kappa tr(eps) 1,  kappa = lam + 2 mu / 3.
+  // The increment is solved on (e_s, w), so neither the hydrostatic strain nor
+  // the accumulated viscous strain adds rounding to the residual: its
+  // rounding is relative to the deviatoric trial state.  Returns tr(eps).
+  template <class T> AD_HD static T trial_strain(const T (&eps)[6], const T (&yn)[5], T (&es)[6]) {
+    const T tr = eps[0] + eps[1] + eps[2];
+    const T m = tr * T(1.0 / 3.0);
+    es[0] = (eps[0] - m) - yn[0];
+    es[1] = (eps[1] - m) - yn[1];
+    es[2] = (eps[2] - m) + (yn[0] + yn[1]);
+    es[3] = eps[3] - yn[2];
+    es[4] = eps[4] - yn[3];
+    es[5] = eps[5] - yn[4];
+    return tr;
+  }
+  template <class T> AD_HD static T hydro_stress(const LawParams<T>& p, T tr) {
+    return (p.lam + p.mu * T(2.0 / 3.0)) * tr;
+  }
+
+  // phi(s v) = s^(2 a_phi) phi(v) and psi is quadratic, so the step on
+  // (e_s / s, w / s) is the same problem with c_phi scaled by s^(2 a_phi - 2),
+  // and has the same Newton matrix.  s = 2^k.  Returns false when the scaled
+  // constant leaves the range in which the FP32 solve stays finite; that
+  // happens only for trial strains so small that the dissipation dominates
+  // psi by many orders and the flow, far below the resolution of y, is taken
+  // as zero.
+  template <class T> AD_HD static bool rescale(LawParams<T>& p, int k) {
+    const T e = T(k) * (T(2) * p.a_phi - T(2));
+    T f;
+    if constexpr (sizeof(T) == 4) f = exp2f(e);
+    else f = exp2(e);
+    p.c_phi *= f;
+    const T big = T(sizeof(T) == 4 ? 1e20 : 1e280);
+    return p.c_phi > T(1) / big && p.c_phi < big;
+  }
 };
 
 }  // namespace gsm

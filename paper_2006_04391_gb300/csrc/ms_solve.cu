@@ -1,287 +1,48 @@
 // Moulinec-Suquet basic scheme driving the GSM update (AutoMat, arXiv
 // 2006.04391: Sec. 1 and Sec. 3 "Material Law Evaluations" -- fixed reference
 // stiffness, one material evaluation without tangent per voxel and
-// iteration).  The paper ran this solver on the CPU; here every step runs on
-// the GPU and the fields stay resident in HBM:
+// iteration), and the serving loop that runs many such solves at once.  The
+// paper ran this solver on the CPU; here every step runs on the GPU and the
+// fields stay resident in HBM.  One iteration ("tick") of every active job:
 //
 //   material kernel   sigma, z = law(eps_raw / N^3, z_n)   + FP64 partial sums of sigma
-//   cuFFT R2C (x6)    sigma -> sig_hat
-//   gamma kernel      per mode: q = sig_hat k, residual partial sums (FP64),
-//                     eps_hat -= Gamma0(k) : sig_hat, and a copy of eps_hat
-//                     into sig_hat's buffer for the inverse transform
-//   finalize kernel   fixed-order sums -> e and <sigma> (FP64), 1 value to host
-//   cuFFT C2R (x6)    eps_hat copy -> eps_raw (unnormalised: N^3 eps)
+//   cuFFT R2C (x6)    sigma -> sig_hat                      (per job)
+//   gamma kernel      per mode: error partial sums (FP64), eps_hat -= Gamma0 : sig_hat,
+//                     and a copy of eps_hat into sig_hat's buffer for the inverse
+//   finalize kernel   fixed-order sums -> e and <sigma> (FP64) per job, one copy to host
+//   cuFFT C2R (x6)    eps_hat copy -> eps_raw (unnormalised: N^3 eps)   (per job)
 //
+// The material, gamma and finalize kernels take every job of the tick in one
+// launch (ms_kernels.cuh); ms_run is a tick loop over a single job, the
+// serve_* API a tick loop over a job table with admission by an HBM budget.
 // The C2R output is never normalised in a separate pass: the material kernel
 // scales it by 1/N^3 as it loads it.  cuFFT may overwrite the input of a
 // multi-dimensional C2R, which is why the gamma kernel writes the updated
 // eps_hat twice (state and transform input).
-//
-// Green operator of the isotropic reference medium (lambda0, mu0), applied to
-// a symmetric tau with q = tau k (homogeneous of degree 0 in k):
-//   (Gamma0 : tau)_ij = (k_j q_i + k_i q_j) / (2 mu0 |k|^2)
-//                       - (lambda0 + mu0) / (mu0 (lambda0 + 2 mu0)) (k.q) k_i k_j / |k|^4.
-// Even N: a mode with the Nyquist index N/2 together with any other nonzero
-// index has no Hermitian-consistent Gamma0; it gets Gamma0 := 0 and is left
-// out of the equilibrium error.  Pure-axis Nyquist modes keep the operator.
 #include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
 
+#include "adjoint_kernels.cuh"
 #include "common.cuh"
-#include "voxel.cuh"
+#include "ms_kernels.cuh"
 
 namespace gsm {
-
-int material_update(const Material& m, int64_t n, const void* eps, const void* zn, int64_t ld, double h,
-                    void* sig, void* z, void* tan, int32_t* status, cudaStream_t s);
-
 namespace {
-
-constexpr int kMaxPhases = 16;
-constexpr int kMatBlock = 128;
-constexpr int kGamBlock = 256;
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-struct PhaseTable {
-  int kind[kMaxPhases];  // GSM_PSI_* of each phase
-  LawParams<double> p64[kMaxPhases];
-  LawParams<float> p32[kMaxPhases];
-};
-
-template <class T> struct cplx;
-template <> struct cplx<double> { using type = cufftDoubleComplex; };
-template <> struct cplx<float> { using type = cufftComplex; };
-
-// ------------------------------------------------------------------ kernels
-
-// Block-wide deterministic sum of 6 FP64 values (fixed shuffle order).
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double* out, int64_t out_stride) {
-  __shared__ double sh[NV][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < NV; ++c)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < NV; ++c) sh[c][warp] = v[c];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[c][w];
-      out[c * out_stride + blockIdx.x] = s;
-    }
-  }
-}
-
-// Material evaluation of every voxel.  T = field type; MODE = MODE_FP64 or MODE_FP32.
-template <class T, int MODE>
-__global__ void __launch_bounds__(kMatBlock) ms_material_kernel(int64_t nvox, const uint8_t* __restrict__ phase,
-                                                                PhaseTable tab, double h, double inv_n3,
-                                                                const T* __restrict__ eps_raw,
-                                                                const T* __restrict__ zn, T* __restrict__ sig,
-                                                                T* __restrict__ z, double* __restrict__ partials) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nvox; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    const bool in = i < nvox;
-    const int ph = in ? (int)phase[i] : 0;
-    const bool vp = in && tab.kind[ph] == GSM_PSI_ELASTIC_VP_DEV;
-    T e[6], zi[6], s[6], zo[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      e[c] = in ? (T)((double)__ldg(eps_raw + c * nvox + i) * inv_n3) : T(0);
-      zi[c] = vp ? __ldg(zn + c * nvox + i) : T(0);
-    }
-    // every lane enters the solver so that the warp votes see all 32 lanes
-    if constexpr (MODE == MODE_FP64) {
-      voxel_fp64<NortonDev>(tab.p64[ph], e, zi, h, vp, s, zo, nullptr);
-    } else {
-      voxel_fp32<NortonDev>(tab.p32[ph], e, zi, (float)h, vp, s, zo, nullptr);
-    }
-    if (in && !vp) {
-      if constexpr (MODE == MODE_FP64) voxel_elastic<double>(tab.p64[ph], e, s, nullptr);
-      else voxel_elastic<float>(tab.p32[ph], e, s, nullptr);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) zo[c] = T(0);
-    }
-    if (in) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sig[c * nvox + i] = s[c];
-        z[c * nvox + i] = zo[c];
-        acc[c] += (double)s[c];
-      }
-    }
-  }
-  block_sum<6>(acc, partials, gridDim.x);
-}
-
-// Mode (a, b, c) of the half spectrum -> signed integer frequency.
-__device__ __forceinline__ int freq(int a, int N) { return a < (N + 1) / 2 ? a : a - N; }
-
-// Fused Green-operator application, equilibrium-error partial sums and copy
-// of the updated strain spectrum into the inverse-transform input.
-template <class T>
-__global__ void __launch_bounds__(kGamBlock) ms_gamma_kernel(int N, double lam0, double mu0,
-                                                             typename cplx<T>::type* __restrict__ sig_hat,
-                                                             typename cplx<T>::type* __restrict__ eps_hat,
-                                                             int64_t nmodes, double* __restrict__ partials) {
-  using C = typename cplx<T>::type;
-  const int Nh = N / 2 + 1;
-  const bool even = (N % 2) == 0;
-  const double inv2mu = 1.0 / (2.0 * mu0);
-  const double coef = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
-  double res = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < nmodes; m += stride) {
-    const int c = (int)(m % Nh);
-    const int64_t ab = m / Nh;
-    const int b = (int)(ab % N);
-    const int a = (int)(ab / N);
-    const int kx = freq(a, N), ky = freq(b, N), kz = c;
-    const int nz = (kx != 0) + (ky != 0) + (kz != 0);
-    const bool nyq = even && (a == N / 2 || b == N / 2 || c == N / 2);
-    const bool skip = nz == 0 || (nyq && nz >= 2);
-    C s[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) s[q] = sig_hat[q * nmodes + m];
-    if (skip) {
-      // Gamma0 = 0: eps_hat unchanged; the transform input gets eps_hat
-#pragma unroll
-      for (int q = 0; q < 6; ++q) sig_hat[q * nmodes + m] = eps_hat[q * nmodes + m];
-      continue;
-    }
-    // Arithmetic in the field precision T; the error sum accumulates in FP64.
-    const T k1 = (T)kx, k2 = (T)ky, k3 = (T)kz;
-    // q = sigma k (Voigt 11,22,33,23,13,12; tensor shears)
-    T qr[3], qi[3];
-    qr[0] = s[0].x * k1 + s[5].x * k2 + s[4].x * k3;
-    qi[0] = s[0].y * k1 + s[5].y * k2 + s[4].y * k3;
-    qr[1] = s[5].x * k1 + s[1].x * k2 + s[3].x * k3;
-    qi[1] = s[5].y * k1 + s[1].y * k2 + s[3].y * k3;
-    qr[2] = s[4].x * k1 + s[3].x * k2 + s[2].x * k3;
-    qi[2] = s[4].y * k1 + s[3].y * k2 + s[2].y * k3;
-    const double w = (c == 0 || (even && c == N / 2)) ? 1.0 : 2.0;
-    res += w * ((double)(qr[0] * qr[0] + qi[0] * qi[0]) + (double)(qr[1] * qr[1] + qi[1] * qi[1]) +
-                (double)(qr[2] * qr[2] + qi[2] * qi[2]));
-    const T kk = k1 * k1 + k2 * k2 + k3 * k3;
-    const T ik2 = T(1) / kk;
-    const T a1 = (T)inv2mu * ik2;
-    const T a2 = (T)coef * ik2 * ik2;
-    const T kqr = k1 * qr[0] + k2 * qr[1] + k3 * qr[2];
-    const T kqi = k1 * qi[0] + k2 * qi[1] + k3 * qi[2];
-    const T kv[3] = {k1, k2, k3};
-    const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int i = ii[q], j = jj[q];
-      const T f = q < 3 ? T(1) : T(2);  // engineering shears for strain
-      const T dr = f * (a1 * (kv[j] * qr[i] + kv[i] * qr[j]) - a2 * kqr * kv[i] * kv[j]);
-      const T di = f * (a1 * (kv[j] * qi[i] + kv[i] * qi[j]) - a2 * kqi * kv[i] * kv[j]);
-      C e = eps_hat[q * nmodes + m];
-      e.x -= dr;
-      e.y -= di;
-      eps_hat[q * nmodes + m] = e;
-      sig_hat[q * nmodes + m] = e;
-    }
-  }
-  double v[1] = {res};
-  block_sum<1>(v, partials, gridDim.x);
-}
-
-struct Reduced {
-  double e;        // equilibrium error
-  double mean[6];  // <sigma>
-  double res;      // sum |xi . c|^2
-};
-
-// Fixed-order final sums of the block partials.
-__global__ void ms_finalize_kernel(const double* __restrict__ mat_part, int n_mat, const double* __restrict__ gam_part,
-                                   int n_gam, double inv_n3, double floor_, Reduced* __restrict__ out) {
-  __shared__ double sh[7];
-  const int t = threadIdx.x;
-  if (t < 7) {
-    double s = 0.0;
-    if (t < 6)
-      for (int b = 0; b < n_mat; ++b) s += mat_part[t * n_mat + b];
-    else
-      for (int b = 0; b < n_gam; ++b) s += gam_part[b];
-    sh[t] = s;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double m[6];
-    for (int c = 0; c < 6; ++c) m[c] = sh[c] * inv_n3;
-    // sum |xi . c|^2 with xi = 2 pi k and c = sigma^ / N^3
-    const double num = sqrt(sh[6]) * kTwoPi * inv_n3;
-    const double fro = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + 2.0 * (m[3] * m[3] + m[4] * m[4] + m[5] * m[5]));
-    out->e = num / fmax(fro, floor_);
-    for (int c = 0; c < 6; ++c) out->mean[c] = m[c];
-    out->res = sh[6];
-  }
-}
-
-// eps_raw += N^3 dE (uniform macro-strain increment at a step start).
-template <class T>
-__global__ void ms_add_uniform_kernel(int64_t nvox, T* __restrict__ eps_raw, double d0, double d1, double d2,
-                                      double d3, double d4, double d5) {
-  const double d[6] = {d0, d1, d2, d3, d4, d5};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) eps_raw[c * nvox + i] = (T)((double)eps_raw[c * nvox + i] + d[c]);
-}
-
-// eps_hat = R2C(eps_raw) / N^3 with the mean mode set to N^3 E exactly.
-template <class T>
-__global__ void ms_spectrum_init_kernel(int64_t nmodes, const typename cplx<T>::type* __restrict__ raw_hat,
-                                        typename cplx<T>::type* __restrict__ eps_hat, double inv_n3, double n3,
-                                        double E0, double E1, double E2, double E3, double E4, double E5) {
-  const double E[6] = {E0, E1, E2, E3, E4, E5};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < nmodes; m += stride) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      typename cplx<T>::type v = raw_hat[q * nmodes + m];
-      if (m == 0) {
-        v.x = (T)(n3 * E[q]);
-        v.y = T(0);
-      } else {
-        v.x = (T)((double)v.x * inv_n3);
-        v.y = (T)((double)v.y * inv_n3);
-      }
-      eps_hat[q * nmodes + m] = v;
-    }
-  }
-}
-
-// Precision conversion / scaling: dst = src * scale.
-template <class S, class D>
-__global__ void ms_convert_kernel(int64_t n, const S* __restrict__ src, D* __restrict__ dst, double scale) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    dst[i] = (D)((double)src[i] * scale);
-}
 
 int grid_cap(int64_t n, int block, int per_sm) {
   const int64_t need = (n + block - 1) / block;
   const int64_t cap = (int64_t)sm_count() * per_sm;
   return (int)std::max<int64_t>(1, std::min(need, cap));
 }
-
-// ---------------------------------------------------------- field buffers
 
 template <class T> struct Fields {
   using C = typename cplx<T>::type;
@@ -291,159 +52,536 @@ template <class T> struct Fields {
   T* z = nullptr;        // [6][nvox]
   C* sig_hat = nullptr;  // [6][nmodes] (also the C2R input)
   C* eps_hat = nullptr;  // [6][nmodes]
-  cufftHandle r2c = 0, c2r = 0;
-  bool planned = false;
 };
 
 template <class T> size_t field_bytes(int64_t nvox, int64_t nmodes) {
   return 4 * 6 * nvox * sizeof(T) + 2 * 6 * nmodes * sizeof(typename cplx<T>::type);
 }
 
-}  // namespace
+int64_t n_vchunks(int64_t nvox) { return (nvox + kVChunk - 1) / kVChunk; }
+int64_t n_mchunks(int64_t nmodes) { return (nmodes + kMChunk - 1) / kMChunk; }
 
-struct MsContext {
+size_t job_bytes(int N, int precision) {
+  const int64_t nv = (int64_t)N * N * N, nm = (int64_t)N * N * (N / 2 + 1);
+  size_t b = field_bytes<double>(nv, nm) + (precision == MS_PREC_FP32_BULK ? field_bytes<float>(nv, nm) : 0);
+  b += (6 * n_vchunks(nv) + n_mchunks(nm)) * sizeof(double) + sizeof(PhaseTable) + (size_t)nv;  // + phase copy
+  return b;
+}
+
+size_t plan_bytes_one(int N, bool fp32) {
+  int n[3] = {N, N, N};
+  const long long nv = (long long)N * N * N, nm = (long long)N * N * (N / 2 + 1);
+  size_t total = 0, ws = 0;
+  if (cufftEstimateMany(3, n, nullptr, 1, (int)nv, nullptr, 1, (int)nm, fp32 ? CUFFT_R2C : CUFFT_D2Z, 6, &ws) ==
+      CUFFT_SUCCESS)
+    total += ws;
+  if (cufftEstimateMany(3, n, nullptr, 1, (int)nm, nullptr, 1, (int)nv, fp32 ? CUFFT_C2R : CUFFT_Z2D, 6, &ws) ==
+      CUFFT_SUCCESS)
+    total += ws;
+  return total;
+}
+
+size_t plan_bytes(int N, int precision) {
+  return plan_bytes_one(N, false) + (precision == MS_PREC_FP32_BULK ? plan_bytes_one(N, true) : 0);
+}
+
+// ------------------------------------------------------------------- engine
+
+struct Plans {
+  cufftHandle r2c = 0, c2r = 0;
+};
+
+// Stream, cuFFT plan cache and the per-tick job table shared by all jobs.
+struct Engine {
+  cudaStream_t stream = nullptr;
+  std::map<std::pair<int, int>, Plans> plans;  // (N, fp32) -> plans
+  JobView* views_dev = nullptr;                // scratch: the tick's job table
+  JobView* views_host = nullptr;               // pinned staging
+  Reduced* red_dev = nullptr;
+  Reduced* red_host = nullptr;
+  int cap = 0;
+  bool inited = false;
+  int per_sm_mat[3] = {1, 1, 1};
+  int per_sm_gam[2] = {1, 1};
+
+  int init(cudaStream_t s, int capacity) {
+    stream = s;
+    cap = capacity;
+    inited = true;
+    if (cudaMalloc((void**)&views_dev, cap * sizeof(JobView)) != cudaSuccess ||
+        cudaMallocHost((void**)&views_host, cap * sizeof(JobView)) != cudaSuccess ||
+        cudaMalloc((void**)&red_dev, cap * sizeof(Reduced)) != cudaSuccess ||
+        cudaMallocHost((void**)&red_host, cap * sizeof(Reduced)) != cudaSuccess) {
+      cudaGetLastError();
+      return GSM_ENOMEM;
+    }
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_batch_kernel<double, MODE_FP64>, kMatBlock, 0) ==
+        cudaSuccess)
+      per_sm_mat[0] = std::max(b, 1);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_batch_kernel<double, MODE_FP32_FIX>, kMatBlock,
+                                                      0) == cudaSuccess)
+      per_sm_mat[1] = std::max(b, 1);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_batch_kernel<float, MODE_FP32>, kMatBlock, 0) ==
+        cudaSuccess)
+      per_sm_mat[2] = std::max(b, 1);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<double>, kGamBlock, 0) == cudaSuccess)
+      per_sm_gam[0] = std::max(b, 1);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<float>, kGamBlock, 0) == cudaSuccess)
+      per_sm_gam[1] = std::max(b, 1);
+    return GSM_OK;
+  }
+
+  int get_plans(int N, bool fp32, Plans** out) {
+    auto key = std::make_pair(N, fp32 ? 1 : 0);
+    auto it = plans.find(key);
+    if (it == plans.end()) {
+      Plans p;
+      int n[3] = {N, N, N};
+      const int nv = N * N * N, nm = N * N * (N / 2 + 1);
+      if (cufftPlanMany(&p.r2c, 3, n, nullptr, 1, nv, nullptr, 1, nm, fp32 ? CUFFT_R2C : CUFFT_D2Z, 6) !=
+          CUFFT_SUCCESS)
+        return GSM_ECUDA;
+      if (cufftPlanMany(&p.c2r, 3, n, nullptr, 1, nm, nullptr, 1, nv, fp32 ? CUFFT_C2R : CUFFT_Z2D, 6) !=
+          CUFFT_SUCCESS) {
+        cufftDestroy(p.r2c);
+        return GSM_ECUDA;
+      }
+      cufftSetStream(p.r2c, stream);
+      cufftSetStream(p.c2r, stream);
+      it = plans.emplace(key, p).first;
+    }
+    *out = &it->second;
+    return GSM_OK;
+  }
+
+  ~Engine() {
+    if (inited) cudaStreamSynchronize(stream);
+    for (auto& kv : plans) {
+      cufftDestroy(kv.second.r2c);
+      cufftDestroy(kv.second.c2r);
+    }
+    cudaFree(views_dev);
+    cudaFreeHost(views_host);
+    cudaFree(red_dev);
+    cudaFreeHost(red_host);
+  }
+};
+
+// --------------------------------------------------------------------- jobs
+
+struct Job {
+  int64_t id = 0;
   int N = 0;
   int64_t nvox = 0, nmodes = 0;
+  int n_vch = 0, n_mch = 0;
   int precision = MS_PREC_FP64;
+  int law_mode = MODE_FP64;  // arithmetic of the laws on FP64 fields
+  uint8_t* phase_owned = nullptr;
   const uint8_t* phase = nullptr;
-  int n_phases = 0;
-  PhaseTable tab;
+  PhaseTable tab_host;
+  PhaseTable* tab_dev = nullptr;
   double lam0 = 0, mu0 = 0;
-  cudaStream_t stream = nullptr;
+  double theta[kMaxPhases][3] = {};  // (sigma0, edot0, n) of Norton phases
   Fields<double> f64;
   Fields<float> f32;
   double* mat_part = nullptr;
   double* gam_part = nullptr;
-  Reduced* red_dev = nullptr;
-  Reduced* red_host = nullptr;
-  int mat_grid64 = 0, mat_grid32 = 0, gam_grid = 0, elt_grid = 0;
+  size_t bytes = 0;
+  bool allocated = false;
+  // load
+  std::vector<double> E, h;
+  std::vector<int32_t> forced;
+  double tol = 1e-8, switch_tol = 1e-5;
+  int max_iter = 10000;
+  // state
+  int step = 0, n_eval = 0, n32 = 0, since_best = 0;
+  bool fp32_phase = false, need_start = true, done = false, notconv = false;
+  double best = 1e300;
   double E_prev[6] = {0, 0, 0, 0, 0, 0};
-  bool have_state = false;
+  // results
+  std::vector<double> Sigma, final_error;
+  std::vector<int32_t> iters, fp32_iters;
+  int64_t total_iters = 0;
+  // optional per-step checkpoints for the adjoint: [n_steps][6][nvox] each
+  double* tape_eps = nullptr;   // converged strain eps_k
+  double* tape_zprev = nullptr; // internal variables z_{k-1} entering step k
 };
 
-namespace {
-
-template <class T> cufftType r2c_type();
-template <> cufftType r2c_type<double>() { return CUFFT_D2Z; }
-template <> cufftType r2c_type<float>() { return CUFFT_R2C; }
-template <class T> cufftType c2r_type();
-template <> cufftType c2r_type<double>() { return CUFFT_Z2D; }
-template <> cufftType c2r_type<float>() { return CUFFT_C2R; }
-
-template <class T> int plan_fields(MsContext& c, Fields<T>& f) {
-  int n[3] = {c.N, c.N, c.N};
-  const int64_t nv = c.nvox, nm = c.nmodes;
-  if (cufftPlanMany(&f.r2c, 3, n, nullptr, 1, (int)nv, nullptr, 1, (int)nm, r2c_type<T>(), 6) != CUFFT_SUCCESS)
-    return GSM_ECUDA;
-  if (cufftPlanMany(&f.c2r, 3, n, nullptr, 1, (int)nm, nullptr, 1, (int)nv, c2r_type<T>(), 6) != CUFFT_SUCCESS)
-    return GSM_ECUDA;
-  cufftSetStream(f.r2c, c.stream);
-  cufftSetStream(f.c2r, c.stream);
-  f.planned = true;
-  auto alloc = [](void** p, size_t b) { return cudaMalloc(p, b) == cudaSuccess; };
-  bool ok = alloc((void**)&f.eps_raw, 6 * nv * sizeof(T)) && alloc((void**)&f.zn, 6 * nv * sizeof(T)) &&
-            alloc((void**)&f.sig, 6 * nv * sizeof(T)) && alloc((void**)&f.z, 6 * nv * sizeof(T)) &&
-            alloc((void**)&f.sig_hat, 6 * nm * sizeof(typename Fields<T>::C)) &&
-            alloc((void**)&f.eps_hat, 6 * nm * sizeof(typename Fields<T>::C));
-  return ok ? GSM_OK : GSM_ENOMEM;
+int job_setup(Job& j, int N, const uint8_t* phase_dev, int n_phases, const gsm_handle* laws, int precision) {
+  if (N < 2 || N > 1024 || n_phases < 1 || n_phases > kMaxPhases || !laws ||
+      (precision != MS_PREC_FP64 && precision != MS_PREC_FP32_BULK))
+    return GSM_EINVAL;
+  const int64_t n = N;
+  if (n * n * n > (int64_t)INT32_MAX / 6) return GSM_EINVAL;  // cuFFT batch distances are int
+  j.N = N;
+  j.nvox = n * n * n;
+  j.nmodes = n * n * (n / 2 + 1);
+  j.n_vch = (int)n_vchunks(j.nvox);
+  j.n_mch = (int)n_mchunks(j.nmodes);
+  j.precision = precision;
+  j.phase = phase_dev;
+  std::memset(&j.tab_host, 0, sizeof(j.tab_host));
+  double lam_min = 1e300, lam_max = -1e300, mu_min = 1e300, mu_max = -1e300;
+  j.law_mode = MODE_FP64;
+  for (int p = 0; p < n_phases; ++p) {
+    const Material* m = reinterpret_cast<const Material*>(laws[p]);
+    if (!m) return GSM_EINVAL;
+    j.tab_host.kind[p] = m->psi_kind;
+    j.tab_host.p64[p] = m->p64;
+    j.tab_host.p32[p] = m->p32;
+    if (m->psi_kind == GSM_PSI_ELASTIC_VP_DEV && m->precision != GSM_FP64) j.law_mode = MODE_FP32_FIX;
+    if (m->psi_kind == GSM_PSI_ELASTIC_VP_DEV) {
+      j.theta[p][0] = m->params[2];
+      j.theta[p][1] = m->params[3];
+      j.theta[p][2] = m->params[4];
+    }
+    lam_min = std::min(lam_min, m->p64.lam);
+    lam_max = std::max(lam_max, m->p64.lam);
+    mu_min = std::min(mu_min, m->p64.mu);
+    mu_max = std::max(mu_max, m->p64.mu);
+  }
+  j.lam0 = 0.5 * (lam_min + lam_max);
+  j.mu0 = 0.5 * (mu_min + mu_max);
+  j.bytes = job_bytes(N, precision);
+  return GSM_OK;
 }
 
-template <class T> void free_fields(Fields<T>& f) {
-  cudaFree(f.eps_raw);
-  cudaFree(f.zn);
-  cudaFree(f.sig);
-  cudaFree(f.z);
-  cudaFree(f.sig_hat);
-  cudaFree(f.eps_hat);
-  if (f.planned) {
-    cufftDestroy(f.r2c);
-    cufftDestroy(f.c2r);
-  }
+template <class T> bool alloc_fields(Fields<T>& f, int64_t nv, int64_t nm, cudaStream_t s) {
+  using C = typename cplx<T>::type;
+  return cudaMallocAsync((void**)&f.eps_raw, 6 * nv * sizeof(T), s) == cudaSuccess &&
+         cudaMallocAsync((void**)&f.zn, 6 * nv * sizeof(T), s) == cudaSuccess &&
+         cudaMallocAsync((void**)&f.sig, 6 * nv * sizeof(T), s) == cudaSuccess &&
+         cudaMallocAsync((void**)&f.z, 6 * nv * sizeof(T), s) == cudaSuccess &&
+         cudaMallocAsync((void**)&f.sig_hat, 6 * nm * sizeof(C), s) == cudaSuccess &&
+         cudaMallocAsync((void**)&f.eps_hat, 6 * nm * sizeof(C), s) == cudaSuccess;
+}
+
+template <class T> void free_fields(Fields<T>& f, cudaStream_t s) {
+  void* ptrs[6] = {f.eps_raw, f.zn, f.sig, f.z, f.sig_hat, f.eps_hat};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, s);
   f = Fields<T>();
 }
 
-cufftResult exec_r2c(Fields<double>& f, double* in, cufftDoubleComplex* out) { return cufftExecD2Z(f.r2c, in, out); }
-cufftResult exec_r2c(Fields<float>& f, float* in, cufftComplex* out) { return cufftExecR2C(f.r2c, in, out); }
-cufftResult exec_c2r(Fields<double>& f, cufftDoubleComplex* in, double* out) { return cufftExecZ2D(f.c2r, in, out); }
-cufftResult exec_c2r(Fields<float>& f, cufftComplex* in, float* out) { return cufftExecC2R(f.c2r, in, out); }
+void job_free(Job& j, cudaStream_t s) {
+  if (!j.allocated) return;
+  free_fields(j.f64, s);
+  free_fields(j.f32, s);
+  if (j.mat_part) cudaFreeAsync(j.mat_part, s);
+  if (j.gam_part) cudaFreeAsync(j.gam_part, s);
+  if (j.tab_dev) cudaFreeAsync(j.tab_dev, s);
+  if (j.phase_owned) cudaFreeAsync(j.phase_owned, s);
+  j.mat_part = j.gam_part = nullptr;
+  j.tab_dev = nullptr;
+  j.phase_owned = nullptr;
+  j.allocated = false;
+}
 
-template <class T> Fields<T>& fields(MsContext& c);
-template <> Fields<double>& fields<double>(MsContext& c) { return c.f64; }
-template <> Fields<float>& fields<float>(MsContext& c) { return c.f32; }
+// Device memory of a job (stream-ordered allocations).  `phase_host` (may be
+// NULL) is copied into a job-owned device array.
+int job_alloc(Job& j, cudaStream_t s, const uint8_t* phase_host) {
+  bool ok = alloc_fields(j.f64, j.nvox, j.nmodes, s);
+  if (ok && j.precision == MS_PREC_FP32_BULK) ok = alloc_fields(j.f32, j.nvox, j.nmodes, s);
+  ok = ok && cudaMallocAsync((void**)&j.mat_part, 6 * (size_t)j.n_vch * sizeof(double), s) == cudaSuccess &&
+       cudaMallocAsync((void**)&j.gam_part, (size_t)j.n_mch * sizeof(double), s) == cudaSuccess &&
+       cudaMallocAsync((void**)&j.tab_dev, sizeof(PhaseTable), s) == cudaSuccess;
+  if (ok && phase_host) {
+    ok = cudaMallocAsync((void**)&j.phase_owned, (size_t)j.nvox, s) == cudaSuccess &&
+         cudaMemcpyAsync(j.phase_owned, phase_host, (size_t)j.nvox, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    j.phase = j.phase_owned;
+  }
+  j.allocated = true;
+  if (!ok) {
+    cudaGetLastError();
+    job_free(j, s);
+    return GSM_ENOMEM;
+  }
+  cudaMemcpyAsync(j.tab_dev, &j.tab_host, sizeof(PhaseTable), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(j.f64.eps_raw, 0, 6 * j.nvox * sizeof(double), s);
+  cudaMemsetAsync(j.f64.zn, 0, 6 * j.nvox * sizeof(double), s);
+  // the host sources of the copies above must outlive them
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
+  return GSM_OK;
+}
 
-// Step start in precision T: eps_raw += N^3 (E - E_prev); eps_hat = spectrum of eps with mean N^3 E.
-template <class T> int step_start(MsContext& c, const double* E, const double* E_prev) {
-  Fields<T>& f = fields<T>(c);
-  const double n3 = (double)c.nvox;
+int job_load(Job& j, const ms_load* load) {
+  if (!load || load->n_steps < 1 || !load->E || !load->h || load->max_iter < 1) return GSM_EINVAL;
+  for (int k = 0; k < load->n_steps; ++k)
+    if (!(std::isfinite(load->h[k]) && load->h[k] > 0.0)) return GSM_EINVAL;
+  if (load->forced_iters)
+    for (int k = 0; k < load->n_steps; ++k)
+      if (load->forced_iters[k] < 1) return GSM_EINVAL;
+  const int n = load->n_steps;
+  j.E.assign(load->E, load->E + 6 * n);
+  j.h.assign(load->h, load->h + n);
+  j.forced.clear();
+  if (load->forced_iters) j.forced.assign(load->forced_iters, load->forced_iters + n);
+  j.tol = load->tol;
+  j.max_iter = load->max_iter;
+  j.switch_tol = load->switch_tol > 0.0 ? load->switch_tol : 1e-5;
+  j.Sigma.assign(6 * n, 0.0);
+  j.final_error.assign(n, 0.0);
+  j.iters.assign(n, 0);
+  j.fp32_iters.assign(n, 0);
+  j.total_iters = 0;
+  j.step = 0;
+  j.need_start = true;
+  j.done = false;
+  j.notconv = false;
+  return GSM_OK;
+}
+
+template <class T> Fields<T>& fields(Job& j);
+template <> Fields<double>& fields<double>(Job& j) { return j.f64; }
+template <> Fields<float>& fields<float>(Job& j) { return j.f32; }
+
+cufftResult exec_r2c(const Plans& p, double* in, cufftDoubleComplex* out) { return cufftExecD2Z(p.r2c, in, out); }
+cufftResult exec_r2c(const Plans& p, float* in, cufftComplex* out) { return cufftExecR2C(p.r2c, in, out); }
+cufftResult exec_c2r(const Plans& p, cufftDoubleComplex* in, double* out) { return cufftExecZ2D(p.c2r, in, out); }
+cufftResult exec_c2r(const Plans& p, cufftComplex* in, float* out) { return cufftExecC2R(p.c2r, in, out); }
+
+int elt_grid(int64_t n) { return grid_cap(n, 256, 8); }
+
+template <class S, class D> void convert(cudaStream_t s, const S* src, D* dst, int64_t n, double scale) {
+  ms_convert_kernel<S, D><<<elt_grid(n), 256, 0, s>>>(n, src, dst, scale);
+  count_launch();
+}
+
+// eps_raw += N^3 (E - E_prev); eps_hat = spectrum of eps with mean N^3 E.
+template <class T> int spectrum_start(Engine& g, Job& j, const double* E, const double* E_prev) {
+  Fields<T>& f = fields<T>(j);
+  Plans* p = nullptr;
+  int rc = g.get_plans(j.N, sizeof(T) == 4, &p);
+  if (rc != GSM_OK) return rc;
+  const double n3 = (double)j.nvox;
   double d[6];
   for (int q = 0; q < 6; ++q) d[q] = n3 * (E[q] - E_prev[q]);
-  ms_add_uniform_kernel<T><<<c.elt_grid, 256, 0, c.stream>>>(c.nvox, f.eps_raw, d[0], d[1], d[2], d[3], d[4], d[5]);
-  count_launch();
-  if (exec_r2c(f, f.eps_raw, f.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
-  ms_spectrum_init_kernel<T><<<c.elt_grid, 256, 0, c.stream>>>(c.nmodes, f.sig_hat, f.eps_hat, 1.0 / n3, n3, E[0],
-                                                                E[1], E[2], E[3], E[4], E[5]);
-  count_launch();
+  ms_add_uniform_kernel<T><<<elt_grid(j.nvox), 256, 0, g.stream>>>(j.nvox, f.eps_raw, d[0], d[1], d[2], d[3], d[4],
+                                                                     d[5]);
+  if (exec_r2c(*p, f.eps_raw, f.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
+  ms_spectrum_init_kernel<T><<<elt_grid(j.nmodes), 256, 0, g.stream>>>(j.nmodes, f.sig_hat, f.eps_hat, 1.0 / n3, n3,
+                                                                         E[0], E[1], E[2], E[3], E[4], E[5]);
+  count_launch(2);
   return cudaGetLastError() == cudaSuccess ? GSM_OK : GSM_ECUDA;
 }
 
-// One iteration's evaluation half: material, forward FFT, gamma + residual, finalize.
-template <class T> int evaluate(MsContext& c, double h) {
-  Fields<T>& f = fields<T>(c);
-  const double inv_n3 = 1.0 / (double)c.nvox;
-  constexpr bool d = sizeof(T) == 8;
-  if constexpr (d)
-    ms_material_kernel<T, MODE_FP64><<<c.mat_grid64, kMatBlock, 0, c.stream>>>(
-        c.nvox, c.phase, c.tab, h, inv_n3, f.eps_raw, f.zn, f.sig, f.z, c.mat_part);
-  else
-    ms_material_kernel<T, MODE_FP32><<<c.mat_grid32, kMatBlock, 0, c.stream>>>(
-        c.nvox, c.phase, c.tab, h, inv_n3, f.eps_raw, f.zn, f.sig, f.z, c.mat_part);
-  count_launch();
-  if (exec_r2c(f, f.sig, f.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
-  ms_gamma_kernel<T><<<c.gam_grid, kGamBlock, 0, c.stream>>>(c.N, c.lam0, c.mu0, f.sig_hat, f.eps_hat, c.nmodes,
-                                                             c.gam_part);
-  count_launch();
-  ms_finalize_kernel<<<1, 32, 0, c.stream>>>(c.mat_part, d ? c.mat_grid64 : c.mat_grid32, c.gam_part, c.gam_grid,
-                                             inv_n3, c.mu0 * 1e-6, c.red_dev);
-  count_launch();
-  cudaMemcpyAsync(c.red_host, c.red_dev, sizeof(Reduced), cudaMemcpyDeviceToHost, c.stream);
-  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return GSM_ECUDA;
-  return cudaGetLastError() == cudaSuccess ? GSM_OK : GSM_ECUDA;
+template <class T> int inverse(Engine& g, Job& j) {
+  Fields<T>& f = fields<T>(j);
+  Plans* p = nullptr;
+  int rc = g.get_plans(j.N, sizeof(T) == 4, &p);
+  if (rc != GSM_OK) return rc;
+  return exec_c2r(*p, f.sig_hat, f.eps_raw) == CUFFT_SUCCESS ? GSM_OK : GSM_ECUDA;
 }
 
-template <class T> int inverse(MsContext& c) {
-  Fields<T>& f = fields<T>(c);
-  return exec_c2r(f, f.sig_hat, f.eps_raw) == CUFFT_SUCCESS ? GSM_OK : GSM_ECUDA;
-}
+int cap_of(const Job& j) { return j.forced.empty() ? j.max_iter : j.forced[j.step]; }
 
-template <class S, class D> void convert(MsContext& c, const S* src, D* dst, int64_t n, double scale) {
-  ms_convert_kernel<S, D><<<c.elt_grid, 256, 0, c.stream>>>(n, src, dst, scale);
-  count_launch();
-}
-
-size_t plan_bytes(int N, bool fp32) {
-  size_t total = 0;
-  int n[3] = {N, N, N};
-  const long long nv = (long long)N * N * N, nm = (long long)N * N * (N / 2 + 1);
-  size_t ws = 0;
-  if (cufftEstimateMany(3, n, nullptr, 1, (int)nv, nullptr, 1, (int)nm, CUFFT_D2Z, 6, &ws) == CUFFT_SUCCESS) total += ws;
-  if (cufftEstimateMany(3, n, nullptr, 1, (int)nm, nullptr, 1, (int)nv, CUFFT_Z2D, 6, &ws) == CUFFT_SUCCESS) total += ws;
-  if (fp32) {
-    if (cufftEstimateMany(3, n, nullptr, 1, (int)nv, nullptr, 1, (int)nm, CUFFT_R2C, 6, &ws) == CUFFT_SUCCESS) total += ws;
-    if (cufftEstimateMany(3, n, nullptr, 1, (int)nm, nullptr, 1, (int)nv, CUFFT_C2R, 6, &ws) == CUFFT_SUCCESS) total += ws;
+// Start load step j.step: macro-strain increment and, in FP32-bulk mode, the
+// FP32 copies of the FP64 state.
+int step_start(Engine& g, Job& j) {
+  const double* E = j.E.data() + 6 * j.step;
+  j.n_eval = 0;
+  j.n32 = 0;
+  j.best = 1e300;
+  j.since_best = 0;
+  j.fp32_phase = j.precision == MS_PREC_FP32_BULK && cap_of(j) > 1;
+  if (j.fp32_phase) {
+    convert<double, float>(g.stream, j.f64.eps_raw, j.f32.eps_raw, 6 * j.nvox, 1.0);
+    convert<double, float>(g.stream, j.f64.zn, j.f32.zn, 6 * j.nvox, 1.0);
+    return spectrum_start<float>(g, j, E, j.E_prev);
   }
-  return total;
+  return spectrum_start<double>(g, j, E, j.E_prev);
 }
 
-void destroy(MsContext* c) {
-  if (!c) return;
-  free_fields(c->f64);
-  free_fields(c->f32);
-  cudaFree(c->mat_part);
-  cudaFree(c->gam_part);
-  cudaFree(c->red_dev);
-  cudaFreeHost(c->red_host);
-  delete c;
+// FP32 -> FP64 hand-over within a step: the FP32 strain of the last
+// evaluation becomes the FP64 strain, resynthesised from its spectrum so that
+// its mean is E_k exactly.
+int switch_to_fp64(Engine& g, Job& j) {
+  const double* E = j.E.data() + 6 * j.step;
+  convert<float, double>(g.stream, j.f32.eps_raw, j.f64.eps_raw, 6 * j.nvox, 1.0);
+  int rc = spectrum_start<double>(g, j, E, E);
+  if (rc != GSM_OK) return rc;
+  cudaMemcpyAsync(j.f64.sig_hat, j.f64.eps_hat, 6 * j.nmodes * sizeof(cufftDoubleComplex), cudaMemcpyDeviceToDevice,
+                  g.stream);
+  j.fp32_phase = false;
+  return inverse<double>(g, j);
 }
+
+// After the tick's evaluation: convergence, precision switch, step end.
+int post_eval(Engine& g, Job& j, const Reduced& r) {
+  ++j.n_eval;
+  const double e = r.e;
+  const int cap = cap_of(j);
+  if (j.fp32_phase) {
+    ++j.n32;
+    if (e < j.best * 0.999) {
+      j.best = e;
+      j.since_best = 0;
+    } else {
+      ++j.since_best;
+    }
+    if (e < std::max(j.switch_tol, j.tol) || j.since_best >= 20 || j.n_eval >= cap - 1) return switch_to_fp64(g, j);
+    return inverse<float>(g, j);
+  }
+  bool end = false, conv = false;
+  if (!j.forced.empty()) {
+    end = conv = j.n_eval >= cap;
+  } else if (e < j.tol) {
+    end = conv = true;
+  } else if (j.n_eval >= cap) {
+    end = true;
+  }
+  if (!end) return inverse<double>(g, j);
+  if (!conv) j.notconv = true;
+  if (j.tape_eps) {
+    const int64_t n6 = 6 * j.nvox;
+    convert<double, double>(g.stream, j.f64.eps_raw, j.tape_eps + j.step * n6, n6, 1.0 / (double)j.nvox);
+    cudaMemcpyAsync(j.tape_zprev + j.step * n6, j.f64.zn, n6 * sizeof(double), cudaMemcpyDeviceToDevice, g.stream);
+  }
+  std::swap(j.f64.zn, j.f64.z);  // z_n <- z
+  for (int q = 0; q < 6; ++q) {
+    j.Sigma[6 * j.step + q] = r.mean[q];
+    j.E_prev[q] = j.E[6 * j.step + q];
+  }
+  j.iters[j.step] = j.n_eval;
+  j.final_error[j.step] = e;
+  j.fp32_iters[j.step] = j.n32;
+  j.total_iters += j.n_eval;
+  ++j.step;
+  if (j.step >= (int)j.h.size()) j.done = true;
+  else j.need_start = true;
+  return GSM_OK;
+}
+
+// One iteration of every job in `jobs` (none may be done).
+int tick(Engine& g, const std::vector<Job*>& jobs) {
+  const int n = (int)jobs.size();
+  if (n == 0) return GSM_OK;
+  if (n > g.cap || n > kMaxBatch) return GSM_EINVAL;
+  for (Job* j : jobs)
+    if (j->need_start) {
+      int rc = step_start(g, *j);
+      if (rc != GSM_OK) return rc;
+      j->need_start = false;
+    }
+  // launch groups: FP64 fields + FP64 laws, FP64 fields + FP32-fix laws, FP32 fields
+  auto key = [](const Job* j) { return j->fp32_phase ? 2 : (j->law_mode == MODE_FP32_FIX ? 1 : 0); };
+  std::vector<Job*> order;
+  order.reserve(n);
+  int gstart[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    for (Job* j : jobs)
+      if (key(j) == k) order.push_back(j);
+    gstart[k + 1] = (int)order.size();
+  }
+  int64_t vtot[3] = {0, 0, 0}, mtot[2] = {0, 0};
+  for (int i = 0; i < n; ++i) {
+    Job& j = *order[i];
+    const int k = key(&j);
+    const int pk = k == 2 ? 1 : 0;
+    const bool f = j.fp32_phase;
+    JobView& v = g.views_host[i];
+    v.phase = j.phase;
+    v.eps_raw = f ? (const void*)j.f32.eps_raw : (const void*)j.f64.eps_raw;
+    v.zn = f ? (const void*)j.f32.zn : (const void*)j.f64.zn;
+    v.sig = f ? (void*)j.f32.sig : (void*)j.f64.sig;
+    v.z = f ? (void*)j.f32.z : (void*)j.f64.z;
+    v.sig_hat = f ? (void*)j.f32.sig_hat : (void*)j.f64.sig_hat;
+    v.eps_hat = f ? (void*)j.f32.eps_hat : (void*)j.f64.eps_hat;
+    v.mat_part = j.mat_part;
+    v.gam_part = j.gam_part;
+    v.tab = j.tab_dev;
+    v.nvox = j.nvox;
+    v.nmodes = j.nmodes;
+    v.vchunk0 = vtot[k];
+    v.mchunk0 = mtot[pk];
+    v.n_vch = j.n_vch;
+    v.n_mch = j.n_mch;
+    v.N = j.N;
+    v.pad = 0;
+    v.h = j.h[j.step];
+    v.inv_h = 1.0 / v.h;
+    v.inv_n3 = 1.0 / (double)j.nvox;
+    v.lam0 = j.lam0;
+    v.mu0 = j.mu0;
+    vtot[k] += j.n_vch;
+    mtot[pk] += j.n_mch;
+  }
+  cudaStream_t s = g.stream;
+  cudaMemcpyAsync(g.views_dev, g.views_host, n * sizeof(JobView), cudaMemcpyHostToDevice, s);
+  const int64_t sms = sm_count();
+  if (gstart[1] > gstart[0]) {
+    const int grid = (int)std::min<int64_t>(vtot[0], sms * g.per_sm_mat[0]);
+    ms_material_batch_kernel<double, MODE_FP64><<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[0],
+                                                                          gstart[1] - gstart[0], vtot[0]);
+    count_launch();
+  }
+  if (gstart[2] > gstart[1]) {
+    const int grid = (int)std::min<int64_t>(vtot[1], sms * g.per_sm_mat[1]);
+    ms_material_batch_kernel<double, MODE_FP32_FIX><<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[1],
+                                                                              gstart[2] - gstart[1], vtot[1]);
+    count_launch();
+  }
+  if (gstart[3] > gstart[2]) {
+    const int grid = (int)std::min<int64_t>(vtot[2], sms * g.per_sm_mat[2]);
+    ms_material_batch_kernel<float, MODE_FP32><<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[2],
+                                                                         gstart[3] - gstart[2], vtot[2]);
+    count_launch();
+  }
+  for (Job* j : order) {
+    Plans* p = nullptr;
+    int rc = g.get_plans(j->N, j->fp32_phase, &p);
+    if (rc != GSM_OK) return rc;
+    const cufftResult fr =
+        j->fp32_phase ? exec_r2c(*p, j->f32.sig, j->f32.sig_hat) : exec_r2c(*p, j->f64.sig, j->f64.sig_hat);
+    if (fr != CUFFT_SUCCESS) return GSM_ECUDA;
+  }
+  if (gstart[2] > gstart[0]) {
+    const int grid = (int)std::min<int64_t>(mtot[0], sms * g.per_sm_gam[0]);
+    ms_gamma_batch_kernel<double><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[0], gstart[2] - gstart[0], mtot[0]);
+    count_launch();
+  }
+  if (gstart[3] > gstart[2]) {
+    const int grid = (int)std::min<int64_t>(mtot[1], sms * g.per_sm_gam[1]);
+    ms_gamma_batch_kernel<float><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[2], gstart[3] - gstart[2], mtot[1]);
+    count_launch();
+  }
+  ms_finalize_batch_kernel<<<n, 32, 0, s>>>(g.views_dev, g.red_dev);
+  count_launch();
+  cudaMemcpyAsync(g.red_host, g.red_dev, n * sizeof(Reduced), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GSM_ECUDA;
+  for (int i = 0; i < n; ++i) {
+    int rc = post_eval(g, *order[i], g.red_host[i]);
+    if (rc != GSM_OK) return rc;
+  }
+  return GSM_OK;
+}
+
+// ------------------------------------------------------------ single solve
+
+struct Ctx {
+  Engine eng;
+  Job job;
+};
+
+// ------------------------------------------------------------------ serving
+
+struct Pending {
+  std::unique_ptr<Job> job;
+  std::vector<uint8_t> phase;
+};
+
+struct Server {
+  Engine eng;
+  size_t budget = 0, used = 0;
+  int max_active = 0;
+  int64_t next_id = 1;
+  std::deque<Pending> queue;
+  std::vector<std::unique_ptr<Job>> active;
+  std::map<int64_t, std::unique_ptr<Job>> finished;
+  std::map<int64_t, int> state;  // 0 queued, 1 active, 2 done, 3 done without convergence
+  std::map<std::pair<int, int>, size_t> plan_cost;
+};
 
 }  // namespace
 }  // namespace gsm
@@ -454,68 +592,25 @@ extern "C" {
 
 size_t ms_workspace_bytes(const ms_problem* prob) {
   if (!prob || prob->N < 2 || prob->N > 1024) return 0;
-  const int N = prob->N;
-  const int64_t nv = (int64_t)N * N * N, nm = (int64_t)N * N * (N / 2 + 1);
-  const bool fp32 = prob->precision == MS_PREC_FP32_BULK;
-  size_t b = field_bytes<double>(nv, nm) + (fp32 ? field_bytes<float>(nv, nm) : 0);
-  b += plan_bytes(N, fp32);
-  b += (size_t)(6 + 1) * 4096 * sizeof(double) + sizeof(Reduced);
-  return b;
+  return job_bytes(prob->N, prob->precision) + plan_bytes(prob->N, prob->precision) +
+         2 * (sizeof(JobView) + sizeof(Reduced));
 }
 
 int ms_create(ms_handle* out, const ms_problem* prob, void* stream) {
   if (!out || !prob) return GSM_EINVAL;
   *out = nullptr;
-  if (prob->N < 2 || prob->N > 1024 || !prob->phase || prob->n_phases < 1 || prob->n_phases > kMaxPhases ||
-      !prob->laws || (prob->precision != MS_PREC_FP64 && prob->precision != MS_PREC_FP32_BULK))
-    return GSM_EINVAL;
-  const int64_t N = prob->N;
-  if (N * N * N > (int64_t)INT32_MAX / 6) return GSM_EINVAL;  // cuFFT batch distances are int
-  MsContext* c = new (std::nothrow) MsContext;
+  if (!prob->phase) return GSM_EINVAL;
+  Ctx* c = new (std::nothrow) Ctx;
   if (!c) return GSM_ENOMEM;
-  c->N = prob->N;
-  c->nvox = N * N * N;
-  c->nmodes = N * N * (N / 2 + 1);
-  c->precision = prob->precision;
-  c->phase = prob->phase;
-  c->n_phases = prob->n_phases;
-  c->stream = static_cast<cudaStream_t>(stream);
-  std::memset(&c->tab, 0, sizeof(c->tab));
-  double lam_min = 1e300, lam_max = -1e300, mu_min = 1e300, mu_max = -1e300;
-  for (int p = 0; p < prob->n_phases; ++p) {
-    const Material* m = reinterpret_cast<const Material*>(prob->laws[p]);
-    if (!m) { delete c; return GSM_EINVAL; }
-    c->tab.kind[p] = m->psi_kind;
-    c->tab.p64[p] = m->p64;
-    c->tab.p32[p] = m->p32;
-    lam_min = std::min(lam_min, m->p64.lam);
-    lam_max = std::max(lam_max, m->p64.lam);
-    mu_min = std::min(mu_min, m->p64.mu);
-    mu_max = std::max(mu_max, m->p64.mu);
-  }
-  c->lam0 = 0.5 * (lam_min + lam_max);
-  c->mu0 = 0.5 * (mu_min + mu_max);
-
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ms_material_kernel<double, MODE_FP64>, kMatBlock, 0);
-  c->mat_grid64 = std::min(grid_cap(c->nvox, kMatBlock, std::max(per, 1)), 4096);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ms_material_kernel<float, MODE_FP32>, kMatBlock, 0);
-  c->mat_grid32 = std::min(grid_cap(c->nvox, kMatBlock, std::max(per, 1)), 4096);
-  c->gam_grid = std::min(grid_cap(c->nmodes, kGamBlock, 8), 4096);
-  c->elt_grid = grid_cap(c->nvox, 256, 8);
-
-  int rc = plan_fields<double>(*c, c->f64);
-  if (rc == GSM_OK && c->precision == MS_PREC_FP32_BULK) rc = plan_fields<float>(*c, c->f32);
-  if (rc == GSM_OK) {
-    bool ok = cudaMalloc((void**)&c->mat_part, 6 * 4096 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void**)&c->gam_part, 4096 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void**)&c->red_dev, sizeof(Reduced)) == cudaSuccess &&
-              cudaMallocHost((void**)&c->red_host, sizeof(Reduced)) == cudaSuccess;
-    if (!ok) rc = GSM_ENOMEM;
-  }
+  int rc = job_setup(c->job, prob->N, prob->phase, prob->n_phases, prob->laws, prob->precision);
+  if (rc == GSM_OK) rc = c->eng.init(static_cast<cudaStream_t>(stream), 1);
+  if (rc == GSM_OK) rc = job_alloc(c->job, c->eng.stream, nullptr);
+  Plans* p = nullptr;
+  if (rc == GSM_OK) rc = c->eng.get_plans(c->job.N, false, &p);
+  if (rc == GSM_OK && c->job.precision == MS_PREC_FP32_BULK) rc = c->eng.get_plans(c->job.N, true, &p);
   if (rc != GSM_OK) {
-    cudaGetLastError();
-    destroy(c);
+    job_free(c->job, c->eng.stream);
+    delete c;
     return rc;
   }
   *out = reinterpret_cast<ms_handle>(c);
@@ -524,118 +619,50 @@ int ms_create(ms_handle* out, const ms_problem* prob, void* stream) {
 
 int ms_destroy(ms_handle h) {
   if (h) {
-    MsContext* c = reinterpret_cast<MsContext*>(h);
-    cudaStreamSynchronize(c->stream);
-    destroy(c);
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    job_free(c->job, c->eng.stream);
+    delete c;  // the engine synchronises its stream
   }
   return GSM_OK;
 }
 
 int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result) {
-  if (!h || !load || !result || load->n_steps < 1 || !load->E || !load->h || load->max_iter < 1 ||
-      !result->Sigma || !result->iters || !result->final_error)
-    return GSM_EINVAL;
-  for (int k = 0; k < load->n_steps; ++k)
-    if (!(std::isfinite(load->h[k]) && load->h[k] > 0.0)) return GSM_EINVAL;
-  if (load->forced_iters)
-    for (int k = 0; k < load->n_steps; ++k)
-      if (load->forced_iters[k] < 1) return GSM_EINVAL;
-  MsContext& c = *reinterpret_cast<MsContext*>(h);
-  const int64_t n6 = 6 * c.nvox;
-  const double n3 = (double)c.nvox;
-  Fields<double>& F = c.f64;
-  Fields<float>& H = c.f32;
-  const bool bulk32 = c.precision == MS_PREC_FP32_BULK;
-  const double switch_tol = load->switch_tol > 0.0 ? load->switch_tol : 1e-5;
-
-  // initial state
-  double E_prev[6] = {0, 0, 0, 0, 0, 0};
+  if (!h || !result || !result->Sigma || !result->iters || !result->final_error) return GSM_EINVAL;
+  Ctx& c = *reinterpret_cast<Ctx*>(h);
+  Job& j = c.job;
+  int rc = job_load(j, load);
+  if (rc != GSM_OK) return rc;
+  const int64_t n6 = 6 * j.nvox;
+  const double n3 = (double)j.nvox;
+  cudaStream_t s = c.eng.stream;
+  for (int q = 0; q < 6; ++q) j.E_prev[q] = 0.0;
   if (state && state->resume) {
     if (!state->eps || !state->z) return GSM_EINVAL;
-    convert<double, double>(c, state->eps, F.eps_raw, n6, n3);
-    cudaMemcpyAsync(F.zn, state->z, n6 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
-    for (int q = 0; q < 6; ++q) E_prev[q] = state->E_prev[q];
+    convert<double, double>(s, state->eps, j.f64.eps_raw, n6, n3);
+    cudaMemcpyAsync(j.f64.zn, state->z, n6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    for (int q = 0; q < 6; ++q) j.E_prev[q] = state->E_prev[q];
   } else {
-    cudaMemsetAsync(F.eps_raw, 0, n6 * sizeof(double), c.stream);
-    cudaMemsetAsync(F.zn, 0, n6 * sizeof(double), c.stream);
+    cudaMemsetAsync(j.f64.eps_raw, 0, n6 * sizeof(double), s);
+    cudaMemsetAsync(j.f64.zn, 0, n6 * sizeof(double), s);
   }
-  int rc_all = GSM_OK;
-  result->total_iters = 0;
-  for (int k = 0; k < load->n_steps; ++k) {
-    const double* E = load->E + 6 * k;
-    const double hk = load->h[k];
-    const int forced = load->forced_iters ? load->forced_iters[k] : 0;
-    const int cap = forced ? forced : load->max_iter;
-    int n_eval = 0, n32 = 0;
-    bool converged = false;
-    int rc = GSM_OK;
-
-    if (bulk32) {
-      // FP32 phase from the FP64 state
-      convert<double, float>(c, F.eps_raw, H.eps_raw, n6, 1.0);
-      convert<double, float>(c, F.zn, H.zn, n6, 1.0);
-      rc = step_start<float>(c, E, E_prev);
-      double best = 1e300;
-      int since_best = 0;
-      // leave at least one evaluation for the FP64 phase
-      while (rc == GSM_OK && n_eval < cap - 1) {
-        rc = evaluate<float>(c, hk);
-        if (rc != GSM_OK) break;
-        ++n_eval;
-        ++n32;
-        const double e = c.red_host->e;
-        if (e < best * 0.999) { best = e; since_best = 0; } else { ++since_best; }
-        if (e < std::max(switch_tol, load->tol) || since_best >= 20 || n_eval >= cap - 1) break;
-        rc = inverse<float>(c);
-      }
-      // hand the FP32 strain (eps_raw of the last evaluation) to FP64
-      if (rc == GSM_OK) {
-        convert<float, double>(c, H.eps_raw, F.eps_raw, n6, 1.0);
-        rc = step_start<double>(c, E, E);  // no increment: already at E_k
-        // resynthesise the FP64 strain from the spectrum so that its mean is E_k exactly
-        if (rc == GSM_OK) {
-          cudaMemcpyAsync(F.sig_hat, F.eps_hat, 6 * c.nmodes * sizeof(cufftDoubleComplex), cudaMemcpyDeviceToDevice,
-                          c.stream);
-          rc = inverse<double>(c);
-        }
-      }
-    } else {
-      rc = step_start<double>(c, E, E_prev);
-    }
-    while (rc == GSM_OK && n_eval < cap) {
-      rc = evaluate<double>(c, hk);
-      if (rc != GSM_OK) break;
-      ++n_eval;
-      const double e = c.red_host->e;
-      if (forced) {
-        if (n_eval >= forced) { converged = true; break; }
-      } else if (e < load->tol) {
-        converged = true;
-        break;
-      }
-      if (n_eval >= cap) break;
-      rc = inverse<double>(c);
-    }
+  const std::vector<Job*> batch{&j};
+  while (!j.done) {
+    rc = tick(c.eng, batch);
     if (rc != GSM_OK) return rc;
-    if (!converged) rc_all = GSM_ENOTCONV;
-    // step end: z_n <- z (swap), Sigma_k = <sigma>
-    std::swap(F.zn, F.z);
-    for (int q = 0; q < 6; ++q) {
-      result->Sigma[6 * k + q] = c.red_host->mean[q];
-      E_prev[q] = E[q];
-    }
-    result->iters[k] = n_eval;
-    result->final_error[k] = c.red_host->e;
-    if (result->fp32_iters) result->fp32_iters[k] = n32;
-    result->total_iters += n_eval;
   }
+  const int n = (int)j.h.size();
+  std::memcpy(result->Sigma, j.Sigma.data(), 6 * n * sizeof(double));
+  std::memcpy(result->iters, j.iters.data(), n * sizeof(int32_t));
+  std::memcpy(result->final_error, j.final_error.data(), n * sizeof(double));
+  if (result->fp32_iters) std::memcpy(result->fp32_iters, j.fp32_iters.data(), n * sizeof(int32_t));
+  result->total_iters = j.total_iters;
   if (state && state->eps && state->z) {
-    convert<double, double>(c, F.eps_raw, state->eps, n6, 1.0 / n3);
-    cudaMemcpyAsync(state->z, F.zn, n6 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
-    for (int q = 0; q < 6; ++q) state->E_prev[q] = E_prev[q];
+    convert<double, double>(s, j.f64.eps_raw, state->eps, n6, 1.0 / n3);
+    cudaMemcpyAsync(state->z, j.f64.zn, n6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    for (int q = 0; q < 6; ++q) state->E_prev[q] = j.E_prev[q];
   }
-  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return GSM_ECUDA;
-  return rc_all;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
+  return j.notconv ? GSM_ENOTCONV : GSM_OK;
 }
 
 int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_result* result, void* stream) {
@@ -645,6 +672,327 @@ int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_re
   rc = ms_run(h, load, state, result);
   ms_destroy(h);
   return rc;
+}
+
+// ------------------------------------------------------------------ serving
+
+int serve_create(serve_handle* out, size_t hbm_budget_bytes, int max_active, void* stream) {
+  if (!out || max_active < 1 || max_active > kMaxBatch || hbm_budget_bytes == 0) return GSM_EINVAL;
+  *out = nullptr;
+  Server* sv = new (std::nothrow) Server;
+  if (!sv) return GSM_ENOMEM;
+  int rc = sv->eng.init(static_cast<cudaStream_t>(stream), max_active);
+  if (rc != GSM_OK) {
+    delete sv;
+    return rc;
+  }
+  sv->budget = hbm_budget_bytes;
+  sv->max_active = max_active;
+  *out = reinterpret_cast<serve_handle>(sv);
+  return GSM_OK;
+}
+
+int serve_destroy(serve_handle h) {
+  if (!h) return GSM_OK;
+  Server* sv = reinterpret_cast<Server*>(h);
+  for (auto& j : sv->active) job_free(*j, sv->eng.stream);
+  delete sv;  // the engine synchronises its stream
+  return GSM_OK;
+}
+
+int serve_submit(serve_handle h, const serve_job* desc, int64_t* id) {
+  if (!h || !desc || !id || !desc->phase || !desc->laws) return GSM_EINVAL;
+  if (desc->n_phases < 1 || desc->n_phases > kMaxPhases) return GSM_EINVAL;
+  Server* sv = reinterpret_cast<Server*>(h);
+  Pending p;
+  p.job.reset(new (std::nothrow) Job);
+  if (!p.job) return GSM_ENOMEM;
+  int rc = job_setup(*p.job, desc->N, nullptr, desc->n_phases, desc->laws, desc->precision);
+  if (rc != GSM_OK) return rc;
+  for (int64_t i = 0; i < p.job->nvox; ++i)
+    if (desc->phase[i] >= desc->n_phases) return GSM_EINVAL;
+  ms_load ld;
+  ld.n_steps = desc->n_steps;
+  ld.E = desc->E;
+  ld.h = desc->h;
+  ld.tol = desc->tol;
+  ld.max_iter = desc->max_iter;
+  ld.forced_iters = nullptr;
+  ld.switch_tol = desc->switch_tol;
+  rc = job_load(*p.job, &ld);
+  if (rc != GSM_OK) return rc;
+  if (p.job->bytes + plan_bytes(desc->N, desc->precision) > sv->budget) return GSM_ENOMEM;  // never admissible
+  p.phase.assign(desc->phase, desc->phase + p.job->nvox);
+  p.job->id = sv->next_id++;
+  *id = p.job->id;
+  sv->state[p.job->id] = 0;
+  sv->queue.push_back(std::move(p));
+  return GSM_OK;
+}
+
+int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_finished) {
+  if (!h) return GSM_EINVAL;
+  Server* sv = reinterpret_cast<Server*>(h);
+  Engine& g = sv->eng;
+  // admission: first come first served while a slot and the HBM budget allow
+  while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active) {
+    Pending& p = sv->queue.front();
+    Job& j = *p.job;
+    const int n_prec = j.precision == MS_PREC_FP32_BULK ? 2 : 1;
+    size_t extra = j.bytes;
+    for (int f = 0; f < n_prec; ++f)
+      if (!sv->plan_cost.count(std::make_pair(j.N, f))) extra += plan_bytes_one(j.N, f == 1);
+    if (sv->used + extra > sv->budget) break;
+    int rc = job_alloc(j, g.stream, p.phase.data());
+    if (rc != GSM_OK) return rc;
+    Plans* pl = nullptr;
+    for (int f = 0; f < n_prec; ++f) {
+      const auto key = std::make_pair(j.N, f);
+      if (!sv->plan_cost.count(key)) sv->plan_cost[key] = plan_bytes_one(j.N, f == 1);
+      rc = g.get_plans(j.N, f == 1, &pl);
+      if (rc != GSM_OK) return rc;
+    }
+    sv->used += extra;
+    sv->state[j.id] = 1;
+    sv->active.push_back(std::move(p.job));
+    sv->queue.pop_front();
+  }
+  std::vector<Job*> batch;
+  for (auto& j : sv->active) batch.push_back(j.get());
+  int rc = tick(g, batch);
+  if (rc != GSM_OK) return rc;
+  for (size_t i = 0; i < sv->active.size();) {
+    if (sv->active[i]->done) {
+      std::unique_ptr<Job> j = std::move(sv->active[i]);
+      sv->active.erase(sv->active.begin() + i);
+      job_free(*j, g.stream);
+      sv->used -= j->bytes;
+      sv->state[j->id] = j->notconv ? 3 : 2;
+      sv->finished[j->id] = std::move(j);
+    } else {
+      ++i;
+    }
+  }
+  if (n_active) *n_active = (int32_t)sv->active.size();
+  if (n_queued) *n_queued = (int32_t)sv->queue.size();
+  if (n_finished) *n_finished = (int32_t)sv->finished.size();
+  return GSM_OK;
+}
+
+int serve_job_state(serve_handle h, int64_t id, int32_t* state, int32_t* step, int64_t* total_iters) {
+  if (!h || !state) return GSM_EINVAL;
+  Server* sv = reinterpret_cast<Server*>(h);
+  auto it = sv->state.find(id);
+  if (it == sv->state.end()) return GSM_EINVAL;
+  *state = it->second;
+  const Job* j = nullptr;
+  for (auto& a : sv->active)
+    if (a->id == id) j = a.get();
+  if (!j) {
+    auto f = sv->finished.find(id);
+    if (f != sv->finished.end()) j = f->second.get();
+  }
+  if (step) *step = j ? j->step : 0;
+  if (total_iters) *total_iters = j ? j->total_iters : 0;
+  return GSM_OK;
+}
+
+int serve_fetch(serve_handle h, int64_t id, double* Sigma, int32_t* iters, double* final_error) {
+  if (!h || !Sigma || !iters || !final_error) return GSM_EINVAL;
+  Server* sv = reinterpret_cast<Server*>(h);
+  auto it = sv->finished.find(id);
+  if (it == sv->finished.end()) return GSM_EINVAL;
+  const Job& j = *it->second;
+  const int n = (int)j.h.size();
+  std::memcpy(Sigma, j.Sigma.data(), 6 * n * sizeof(double));
+  std::memcpy(iters, j.iters.data(), n * sizeof(int32_t));
+  std::memcpy(final_error, j.final_error.data(), n * sizeof(double));
+  const int rc = j.notconv ? GSM_ENOTCONV : GSM_OK;
+  sv->finished.erase(it);
+  sv->state.erase(id);
+  return rc;
+}
+
+size_t serve_job_bytes(int N, int precision) {
+  if (N < 2 || N > 1024) return 0;
+  return job_bytes(N, precision) + plan_bytes(N, precision);
+}
+
+}  // extern "C"
+
+// ============================================================= adjoint (tape)
+// ms_run_taped keeps the per-step checkpoints (eps_k, z_{k-1}) of a load
+// history; ms_adjoint runs the backward sweep over them (kernels and
+// equations in adjoint_kernels.cuh).  The adjoint equilibrium of each step is
+// solved by the basic-scheme fixed point lam <- lam - Gamma0 (C_t lam - a_u)
+// with the context's FFT plans, Green-operator kernel and reductions.
+
+struct Tape {
+  Ctx* ctx = nullptr;
+  int n_steps = 0;
+  std::vector<double> E, h;
+  double* ckpt = nullptr;  // [2][n_steps][6][nvox]: eps_k, then z_{k-1}
+  double* Ct21 = nullptr;  // [21][nvox]
+  double* a_u = nullptr;   // [6][nvox]
+  double* yK = nullptr;    // [20][nvox]: y (5) and K upper triangle (15)
+  double* gz = nullptr;    // [6][nvox]
+  double* gz_prev = nullptr;
+  double* part = nullptr;  // [3][grid]
+  double* out_dev = nullptr;
+  double* out_host = nullptr;
+};
+
+extern "C" {
+
+int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_handle* tape_out) {
+  if (!h || !load || !result || !tape_out) return GSM_EINVAL;
+  *tape_out = nullptr;
+  Ctx& c = *reinterpret_cast<Ctx*>(h);
+  Job& j = c.job;
+  if (load->n_steps < 1) return GSM_EINVAL;
+  Tape* t = new (std::nothrow) Tape;
+  if (!t) return GSM_ENOMEM;
+  t->ctx = &c;
+  t->n_steps = load->n_steps;
+  const int64_t n6 = 6 * j.nvox;
+  const size_t ck = (size_t)2 * load->n_steps * n6 * sizeof(double);
+  bool ok = cudaMalloc((void**)&t->ckpt, ck) == cudaSuccess &&
+            cudaMalloc((void**)&t->Ct21, 21 * j.nvox * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->a_u, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->yK, 20 * j.nvox * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->gz, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->gz_prev, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->part, 3 * 4096 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->out_dev, 4 * sizeof(double)) == cudaSuccess &&
+            cudaMallocHost((void**)&t->out_host, 4 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ms_tape_destroy(reinterpret_cast<ms_tape_handle>(t));
+    return GSM_ENOMEM;
+  }
+  j.tape_eps = t->ckpt;
+  j.tape_zprev = t->ckpt + (size_t)load->n_steps * n6;
+  const int rc = ms_run(h, load, nullptr, result);
+  j.tape_eps = j.tape_zprev = nullptr;
+  if (rc != GSM_OK && rc != GSM_ENOTCONV) {
+    ms_tape_destroy(reinterpret_cast<ms_tape_handle>(t));
+    return rc;
+  }
+  t->E.assign(load->E, load->E + 6 * load->n_steps);
+  t->h.assign(load->h, load->h + load->n_steps);
+  *tape_out = reinterpret_cast<ms_tape_handle>(t);
+  return rc;
+}
+
+int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int max_iter, double* grad,
+               int32_t* lam_iters) {
+  if (!th || !w || !grad || max_iter < 1 || !(tol > 0.0)) return GSM_EINVAL;
+  Tape& t = *reinterpret_cast<Tape*>(th);
+  Ctx& c = *t.ctx;
+  Job& j = c.job;
+  Engine& g = c.eng;
+  if (phase_id < 0 || phase_id >= kMaxPhases || j.tab_host.kind[phase_id] != GSM_PSI_ELASTIC_VP_DEV)
+    return GSM_EINVAL;
+  cudaStream_t s = g.stream;
+  const int64_t nv = j.nvox, n6 = 6 * nv;
+  const double n3 = (double)nv, inv_n3 = 1.0 / n3;
+  // parameters of the differentiated phase (E, sigma0, edot0, n)
+  NortonTheta nt;
+  {
+    const LawParams<double>& p = j.tab_host.p64[phase_id];
+    // E from the Lame constants: E = mu (3 lam + 2 mu) / (lam + mu)
+    nt.E = p.mu * (3.0 * p.lam + 2.0 * p.mu) / (p.lam + p.mu);
+  }
+  nt.sigma0 = j.theta[phase_id][0];
+  nt.edot0 = j.theta[phase_id][1];
+  nt.n = j.theta[phase_id][2];
+  Plans* pl = nullptr;
+  int rc = g.get_plans(j.N, false, &pl);
+  if (rc != GSM_OK) return rc;
+  const int grid_prep = grid_cap(nv, kAdjBlock, 4);
+  const int grid_fin = std::min(grid_cap(nv, kAdjBlock, 8), 4096);
+  double total[3] = {0.0, 0.0, 0.0};
+  cudaMemsetAsync(t.gz, 0, n6 * sizeof(double), s);
+  for (int k = t.n_steps - 1; k >= 0; --k) {
+    const double* eps_k = t.ckpt + (size_t)k * n6;
+    const double* zprev = t.ckpt + (size_t)(t.n_steps + k) * n6;
+    const double hk = t.h[k];
+    double gs[6] = {0, 0, 0, 0, 0, 0};
+    if (k == t.n_steps - 1)
+      for (int q = 0; q < 6; ++q) gs[q] = w[q] * inv_n3;
+    if (j.law_mode == MODE_FP64)
+      adj_prepare_kernel<MODE_FP64><<<grid_prep, kAdjBlock, 0, s>>>(nv, j.phase, j.tab_dev, hk, eps_k, zprev, gs[0],
+                                                                     gs[1], gs[2], gs[3], gs[4], gs[5], t.gz, t.Ct21,
+                                                                     t.a_u, t.yK);
+    else
+      adj_prepare_kernel<MODE_FP32_FIX><<<grid_prep, kAdjBlock, 0, s>>>(nv, j.phase, j.tab_dev, hk, eps_k, zprev,
+                                                                         gs[0], gs[1], gs[2], gs[3], gs[4], gs[5],
+                                                                         t.gz, t.Ct21, t.a_u, t.yK);
+    count_launch();
+    // adjoint equilibrium: lam in eps_raw (N^3 lam), lam^ in eps_hat
+    cudaMemsetAsync(j.f64.eps_raw, 0, n6 * sizeof(double), s);
+    cudaMemsetAsync(j.f64.eps_hat, 0, 6 * j.nmodes * sizeof(cufftDoubleComplex), s);
+    JobView& v = g.views_host[0];
+    std::memset(&v, 0, sizeof v);
+    v.sig_hat = j.f64.sig_hat;
+    v.eps_hat = j.f64.eps_hat;
+    v.mat_part = j.mat_part;
+    v.gam_part = j.gam_part;
+    v.nvox = nv;
+    v.nmodes = j.nmodes;
+    v.n_vch = 0;
+    v.n_mch = j.n_mch;
+    v.N = j.N;
+    v.inv_n3 = inv_n3;
+    v.lam0 = j.lam0;
+    v.mu0 = j.mu0;
+    cudaMemcpyAsync(g.views_dev, g.views_host, sizeof(JobView), cudaMemcpyHostToDevice, s);
+    const int gam_grid = (int)std::min<int64_t>(j.n_mch, (int64_t)sm_count() * g.per_sm_gam[0]);
+    double first = -1.0;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+      adj_tau_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.a_u, j.f64.eps_raw, inv_n3, j.f64.sig);
+      if (cufftExecD2Z(pl->r2c, j.f64.sig, j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
+      ms_gamma_batch_kernel<double><<<gam_grid, kGamBlock, 0, s>>>(g.views_dev, 1, j.n_mch);
+      ms_finalize_batch_kernel<<<1, 32, 0, s>>>(g.views_dev, g.red_dev);
+      count_launch(3);
+      cudaMemcpyAsync(g.red_host, g.red_dev, sizeof(Reduced), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
+      const double r = std::sqrt(g.red_host->res);
+      if (first < 0.0) first = r;
+      if (r <= tol * first || first == 0.0) break;
+      if (cufftExecZ2D(pl->c2r, j.f64.sig_hat, j.f64.eps_raw) != CUFFT_SUCCESS) return GSM_ECUDA;
+    }
+    if (lam_iters) lam_iters[k] = it + 1;
+    adj_finish_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, j.phase, j.tab_dev, hk, phase_id, nt, eps_k, zprev, gs[0],
+                                                     gs[1], gs[2], gs[3], gs[4], gs[5], t.gz, j.f64.eps_raw, inv_n3,
+                                                     t.yK, t.gz_prev, t.part);
+    adj_sum_kernel<<<1, 32, 0, s>>>(t.part, grid_fin, t.out_dev);
+    count_launch(2);
+    cudaMemcpyAsync(t.out_host, t.out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GSM_ECUDA;
+    for (int q = 0; q < 3; ++q) total[q] += t.out_host[q];
+    std::swap(t.gz, t.gz_prev);
+  }
+  for (int q = 0; q < 3; ++q) grad[q] = total[q];
+  return GSM_OK;
+}
+
+int ms_tape_destroy(ms_tape_handle th) {
+  if (!th) return GSM_OK;
+  Tape* t = reinterpret_cast<Tape*>(th);
+  if (t->ctx) cudaStreamSynchronize(t->ctx->eng.stream);
+  cudaFree(t->ckpt);
+  cudaFree(t->Ct21);
+  cudaFree(t->a_u);
+  cudaFree(t->yK);
+  cudaFree(t->gz);
+  cudaFree(t->gz_prev);
+  cudaFree(t->part);
+  cudaFree(t->out_dev);
+  cudaFreeHost(t->out_host);
+  delete t;
+  return GSM_OK;
 }
 
 }  // extern "C"
@@ -727,7 +1075,7 @@ extern "C" int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, co
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* partials = scratch;                                    // [6][grid]
   Reduced* red = reinterpret_cast<Reduced*>(scratch + 6 * kNoAllocMaxBlocks);
-  ms_material_kernel<double, MODE_FP64><<<grid, kMatBlock, 0, s>>>(nvox, phase, tab, step_h, 1.0, eps, z_n, sigma, z,
+  ms_material_kernel<double, MODE_FP64><<<grid, kMatBlock, 0, s>>>(nvox, phase, tab, make_step(step_h), 1.0, eps, z_n, sigma, z,
                                                                    partials);
   ms_finalize_kernel<<<1, 32, 0, s>>>(partials, grid, nullptr, 0, 1.0 / (double)nvox, 1.0, red);
   count_launch(2);

@@ -20,6 +20,8 @@
 // all second-order blocks come from one forward-over-reverse sweep.
 #pragma once
 
+#include <cstring>
+
 #include "ad.cuh"
 #include "laws.cuh"
 
@@ -33,6 +35,7 @@ enum : unsigned {
   ST_NONFINITE = 1u << 17,
   ST_CAP = 1u << 18,
   ST_NOT_SPD = 1u << 19,
+  ST_FIX_SHIFT = 20,     // bits 20-23: FP64 corrections (FP32-bulk mode)
 };
 
 constexpr int kLineIterMax = 60;
@@ -45,6 +48,66 @@ AD_HD float fmax_(float a, float b) { return a > b ? a : b; }
 AD_HD double sqrt_pos(double x) { return std::sqrt(x); }
 AD_HD float sqrt_pos(float x) { return sqrtf(x); }
 
+
+// Conversions between FP64 and FP32 on the integer pipe, with an optional
+// exact scaling by 2^k folded into the exponent.  On GB300 an F2F conversion
+// occupies the FP64 pipe (~1.7 FMA slots, measured), and the FP32-bulk update
+// converts ~30 values per voxel; bit manipulation moves that work (and the
+// scalings) to the integer units.  f32_of truncates (relative error < 2^-23)
+// and flushes results below 2^-126 to zero; inf/nan map to inf/nan.  f64_of
+// is exact for normal floats and zero (the FP32 values here are never
+// subnormal) and flushes results below 2^-1022 to zero.
+AD_HD float f32_of(double x, int k = 0) {
+#if defined(__CUDA_ARCH__)
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &x, sizeof b);
+#endif
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned m = (unsigned)(b >> 29) & 0x7fffffu;
+  const int fe = e - 1023 + 127 + k;
+  unsigned r;
+  if (e == 0x7ff) r = 0x7f800000u | (m ? 0x400000u : 0u);
+  else if (e == 0 || fe <= 0) r = 0u;
+  else if (fe >= 255) r = 0x7f800000u;
+  else r = ((unsigned)fe << 23) | m;
+  r |= sign;
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(r);
+#else
+  float f;
+  std::memcpy(&f, &r, sizeof f);
+  return f;
+#endif
+}
+
+AD_HD double f64_of(float x, int k = 0) {
+#if defined(__CUDA_ARCH__)
+  const unsigned b = __float_as_uint(x);
+#else
+  unsigned b;
+  std::memcpy(&b, &x, sizeof b);
+#endif
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const int e = (int)((b >> 23) & 0xff);
+  const unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
+  const int de = e - 127 + 1023 + k;
+  unsigned long long r;
+  if (e == 0xff) r = 0x7ff0000000000000ull | m;
+  else if (e == 0 || de <= 0) r = 0ull;
+  else if (de >= 2047) r = 0x7ff0000000000000ull;
+  else r = ((unsigned long long)de << 52) | m;
+  r |= sign;
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)r);
+#else
+  double d;
+  std::memcpy(&d, &r, sizeof d);
+  return d;
+#endif
+}
 
 // In-place Cholesky of a 5x5 SPD matrix; keeps the inverse diagonal.
 template <class T> struct Chol5 {
@@ -208,6 +271,45 @@ AD_HD void line_eval(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], 
   gp = s1;
 }
 
+// psi_y and sigma = psi_eps in one first-order reverse sweep (strain and
+// internal variables both active).
+template <class Law, class T>
+AD_HD void psi_y_and_stress(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], T (&g)[5], T (&sig)[6]) {
+  ad::UniformPack<ad::Var<T>, 6> E;
+  ad::For<0, 6>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(E).v = eps[decltype(kc)::value]; });
+  ad::UniformPack<ad::Var<T>, 5> Y;
+  ad::For<0, 5>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(Y).v = y[decltype(kc)::value]; });
+  auto f = Law::psi(E, Y, p);
+  f.fwd();
+  f.back(T(1));
+  ad::For<0, 6>::run([&](auto kc) { sig[decltype(kc)::value] = ad::get<decltype(kc)::value>(E).a; });
+  ad::For<0, 5>::run([&](auto kc) { g[decltype(kc)::value] = ad::get<decltype(kc)::value>(Y).a; });
+}
+
+// Mixed block psi_ey (6x5): the change of sigma per change of y.
+// Forward-over-reverse with unit seeds on y; the strain leaves carry no tangent.
+template <class Law, class T>
+AD_HD void psi_ey(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], T (&B)[6][5]) {
+  using V0 = ad::Tan<T, 5, 0u>;
+  ad::UniformPack<ad::Var<V0>, 6> E;
+  ad::For<0, 6>::run([&](auto kc) {
+    auto& l = ad::get_mut<decltype(kc)::value>(E);
+    l.v.v = eps[decltype(kc)::value];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) l.v.d[j] = T(0);
+  });
+  ad::SeededPack<ad::Var, T, 5, 0, 5> Y;
+  ad::seed_unit<decltype(Y), T, 0, 5>(Y, y);
+  auto f = Law::psi(E, Y, p);
+  f.fwd();
+  f.back(T(1));
+  ad::For<0, 6>::run([&](auto kc) {
+    constexpr int i = decltype(kc)::value;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) B[i][j] = ad::get<i>(E).a.d[j];
+  });
+}
+
 // sigma = psi_eps(eps, y): reverse sweep with active strain leaves.
 template <class Law, class T>
 AD_HD void stress(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], T (&sig)[6]) {
@@ -251,6 +353,14 @@ AD_HD void psi_blocks(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5],
 
 // ------------------------------------------------------------- warp voting
 
+AD_HD bool any_lane(bool b) {
+#if defined(__CUDA_ARCH__)
+  return __any_sync(0xffffffffu, b);
+#else
+  return b;
+#endif
+}
+
 AD_HD bool all_done(bool done) {
 #if defined(__CUDA_ARCH__)
   return __all_sync(0xffffffffu, done);
@@ -287,29 +397,114 @@ template <class T> AD_HD T absmax5(const T (&a)[5]) {
 
 // ----------------------------------------------------------------- the solve
 
-// Solve the implicit Euler step in precision T for the increment w = y - y_n.
-// Returns the Cholesky factor of the last Newton matrix in `ch` (for the
-// tangent or for an FP64 correction).  `active` = false for padding lanes:
-// they take part in the warp votes only.
+// Time step and its reciprocal in both precisions, formed once per launch
+// (a per-voxel FP64 division costs ~10 FP64-pipe slots).
+struct Step {
+  double h, inv_h;
+  float hf, inv_hf;
+};
+AD_HD Step make_step(double h) { return Step{h, 1.0 / h, (float)h, (float)(1.0 / h)}; }
+AD_HD void step_of(const Step& s, double& h, double& inv_h) { h = s.h; inv_h = s.inv_h; }
+AD_HD void step_of(const Step& s, float& h, float& inv_h) { h = s.hf; inv_h = s.inv_hf; }
+
+// FP64 finiteness from the exponent bits (integer pipe; an FP64 compare
+// occupies the FP64 pipe).
+AD_HD bool finite64(double x) {
+#if defined(__CUDA_ARCH__)
+  const unsigned hi = (unsigned)__double2hiint(x);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &x, sizeof b);
+  const unsigned hi = (unsigned)(b >> 32);
+#endif
+  return (hi & 0x7ff00000u) != 0x7ff00000u;
+}
+AD_HD bool finite64(float x) { return std::isfinite(x); }
+
+// Exact powers of two from the bit patterns (k in the normal range).
+AD_HD float exp2i(int k, float) {
+  const unsigned b = (unsigned)(k + 127) << 23;
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(b);
+#else
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+// floor(log2 max_i |a_i|) from the exponent fields (integer pipe); the
+// smallest normal exponent when every entry is zero or subnormal.
+AD_HD int ilog2_max(const double (&a)[6]) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#if defined(__CUDA_ARCH__)
+    const int ei = (int)(((unsigned)__double2hiint(a[i]) >> 20) & 0x7ffu);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &a[i], sizeof b);
+    const int ei = (int)((b >> 52) & 0x7ff);
+#endif
+    e = ei > e ? ei : e;
+  }
+  return e == 0 ? -1022 : e - 1023;
+}
+AD_HD int ilog2_max(const float (&a)[6]) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#if defined(__CUDA_ARCH__)
+    const int ei = (int)((__float_as_uint(a[i]) >> 23) & 0xffu);
+#else
+    unsigned b;
+    std::memcpy(&b, &a[i], sizeof b);
+    const int ei = (int)((b >> 23) & 0xff);
+#endif
+    e = ei > e ? ei : e;
+  }
+  return e == 0 ? -126 : e - 127;
+}
+
+template <class T> AD_HD T absmax6(const T (&a)[6]) {
+  T m = T(0);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m = fmax_(m, a[i] < T(0) ? -a[i] : a[i]);
+  return m;
+}
+
+// Solve the implicit Euler step in precision T for the increment w, posed
+// on the trial strain e_s (Law::trial_strain): R(w) = psi_y(e_s, w) +
+// phi_v(w / h) = 0.  Returns the Cholesky factor of the last Newton matrix
+// in `ch` (for the tangent or for an FP64 correction).  `active` = false for
+// padding lanes: they take part in the warp votes only.
+//
+// Rates below 1e-140 (FP64) or 1e-18 (FP32) of |d| / h, d the predictor,
+// are not resolved (this keeps the dissipation's q = |v|^2 from
+// underflowing), nor in FP32 roots where the dissipation Hessian overflows:
+// the flow is then taken as zero.  Both happen only where the dissipation
+// outweighs psi by many orders, i.e. for flows far below the resolution of
+// the trial strain.
 template <class Law, class T>
-AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&eps)[6], const T (&yn)[5], T h,
-                               bool active, T newton_tol, T (&w)[5], Chol5<T>& ch) {
-  const T inv_h = T(1) / h;
+AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const Step& hs, bool active, T newton_tol,
+                               T (&w)[5], Chol5<T>& ch) {
+  T h, inv_h;
+  step_of(hs, h, inv_h);
   unsigned st = 0;
   int n_line = 0, n_newton = 0;
 #pragma unroll
   for (int a = 0; a < 5; ++a) w[a] = T(0);
 
-  // 1. predictor
-  T r0[5];
-  psi_y<Law>(p, eps, yn, r0);
-  const T r0max = absmax5(r0);
-  bool flows = active && (r0max > T(0));
-  if (active && !(r0max == r0max)) { st |= ST_NONFINITE; flows = false; }
+  // 1. predictor at w = 0.  In the trial frame psi_y(e_s, 0) vanishes only
+  // for a zero deviatoric trial stress: then there is no flow.
   T d[5];
+  bool flows;
   {
-    T g0[5], Hp[5][5];
-    psi_y_yy<Law>(p, eps, yn, g0, Hp);
+    T r0[5], Hp[5][5];
+    const T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
+    psi_y_yy<Law>(p, es, zero, r0, Hp);
+    const T r0max = absmax5(r0);
+    flows = active && r0max > T(0);
+    if (active && !(r0max == r0max)) { st |= ST_NONFINITE; flows = false; }
     Chol5<T> hp;
     const bool ok = hp.factor(Hp);
     if (flows && !ok) { st |= ST_NOT_SPD; flows = false; }
@@ -318,31 +513,39 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&eps)[6], const T
     for (int a = 0; a < 5; ++a) mr[a] = -r0[a];
     hp.solve(mr, d);
   }
+  const T th_min = T(sizeof(T) == 8 ? 1e-140 : 1e-18) * h / fmax_(absmax5(d), T(sizeof(T) == 8 ? 1e-300 : 1e-37));
+  if (!(th_min < T(1))) flows = false;
 
   // 2. segment minimisation in u = ln(theta)
   T theta = T(1), lo = T(0), hi = T(1);
-  bool done = !flows;
+  bool done = !flows, below = false;
   for (int it = 0; it < kLineIterMax; ++it) {
     if (all_done(done)) break;
     if (!done) {
       ++n_line;
-      T y[5], wt[5];
+      T wt[5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        wt[a] = theta * d[a];
-        y[a] = yn[a] + wt[a];
-      }
+      for (int a = 0; a < 5; ++a) wt[a] = theta * d[a];
       T g, gp;
-      line_eval<Law>(p, eps, y, wt, d, inv_h, g, gp);
+      line_eval<Law>(p, es, wt, wt, d, inv_h, g, gp);
       if (g >= T(0)) hi = theta; else lo = theta;
-      const T du = -g / (theta * gp);
+      // g' = d^T K d > 0; where the dissipation Hessian leaves the range of T
+      // (FP32, rates near the floor) the step bisects instead, and a root
+      // below such a point is not resolved
+      const bool fin = gp > T(0) && gp < T(sizeof(T) == 8 ? 1e300 : 1e37);
+      const T du = fin ? -g * ad::inv(theta * gp) : T(0);
+      const bool small = fin && (du < T(0) ? -du : du) <= T(sizeof(T) == 8 ? 1e-12 : 1e-6);
       T tn = theta * fp64_exp_step(du);
-      if (!(tn > lo && tn < hi)) tn = lo > T(0) ? sqrt_pos(lo * hi) : T(0.125) * hi;
-      const bool small = (du < T(0) ? -du : du) <= T(sizeof(T) == 8 ? 1e-12 : 1e-6);
+      // safeguard only steps that leave the bracket; a converged step may
+      // round onto a bracket end and is kept
+      if (!small && !(tn > lo && tn < hi)) tn = lo > T(0) ? sqrt_pos(lo * hi) : T(0.125) * hi;
+      if (tn < th_min) tn = th_min;
+      below = !(hi > th_min) || (!fin && g >= T(0));
       theta = tn;
-      if (small || g == T(0) || !(g == g)) done = true;
+      if (small || below || g == T(0) || !(g == g)) done = true;
     }
   }
+  if (below || !(theta > T(0))) flows = false;
   if (flows) {
 #pragma unroll
     for (int a = 0; a < 5; ++a) w[a] = theta * d[a];
@@ -355,13 +558,10 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&eps)[6], const T
     if (all_done(done)) break;
     if (!done) {
       ++n_newton;
-      T y[5], v[5], R[5], K[5][5], gv[5], Hv[5][5];
+      T v[5], R[5], K[5][5], gv[5], Hv[5][5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        y[a] = yn[a] + w[a];
-        v[a] = w[a] * inv_h;
-      }
-      psi_y_yy<Law>(p, eps, y, R, K);
+      for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
+      psi_y_yy<Law>(p, es, w, R, K);
       phi_v_vv<Law>(p, v, gv, Hv);
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
@@ -370,19 +570,20 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&eps)[6], const T
         for (int b = 0; b < 5; ++b) K[a][b] += Hv[a][b] * inv_h;
       }
       T dw[5];
-      if (!ch.factor(K)) {
+      const bool spd = ch.factor(K);
+      ch.solve(R, dw);
+      const T dmax = absmax5(dw);
+      if (!spd) {
         st |= ST_NOT_SPD;
         done = true;
-#pragma unroll
-        for (int a = 0; a < 5; ++a) dw[a] = T(0);
+      } else if (!(dmax < T(sizeof(T) == 8 ? 1e300 : 1e37))) {
+        st |= ST_NONFINITE;  // w keeps the last finite iterate
+        done = true;
       } else {
-        ch.solve(R, dw);
-      }
 #pragma unroll
-      for (int a = 0; a < 5; ++a) w[a] += dw[a];
-      const T scale = fmax_(absmax5(w), T(sizeof(T) == 8 ? 1e-300 : 1e-30));
-      if (absmax5(dw) <= newton_tol * scale) { conv = true; done = true; }
-      if (!(absmax5(dw) == absmax5(dw))) { st |= ST_NONFINITE; done = true; }
+        for (int a = 0; a < 5; ++a) w[a] += dw[a];
+        if (dmax <= newton_tol * fmax_(absmax5(w), T(sizeof(T) == 8 ? 1e-300 : 1e-30))) { conv = true; done = true; }
+      }
     }
   }
   if (active && !conv && !(st & (ST_NOT_SPD | ST_NONFINITE))) st |= ST_CAP;

@@ -4,8 +4,8 @@
 //
 //   MODE_FP64       every step in FP64.
 //   MODE_FP32_FIX   FP32 line search and Newton (the bulk of the work), then
-//                   FP64 Newton corrections: FP64 residual, FP32 Newton matrix
-//                   re-evaluated at the FP64 rate, until the correction is
+//                   FP64 Newton corrections: FP64 residual, the FP32 Newton
+//                   matrix of the last FP32 iteration, until the correction is
 //                   below 1e-6 of the increment (normally one).  A Newton step
 //                   whose matrix is accurate to FP32 and whose residual is
 //                   FP64 lands within ~1e-13 of the FP64 root.
@@ -36,13 +36,12 @@ template <class T> AD_HD void z_of_y(const T (&y)[5], T (&z)[6]) {
 // upper triangle row-major (21 entries).  `flows` = false means y = y_n with
 // an unbounded dissipation Hessian: dy/deps = 0 and C_t = psi_ee.
 template <class Law, class T>
-AD_HD void tangent(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], const T (&w)[5], T h,
+AD_HD void tangent(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], const T (&w)[5], T inv_h,
                    bool flows, T (&C21)[21]) {
   T sig[6], Cee[6][6], Cey[6][5], Cye[5][6];
   psi_blocks<Law>(p, eps, y, sig, Cee, Cey, Cye);
   if (flows) {
     T g[5], K[5][5], gv[5], Hv[5][5], v[5];
-    const T inv_h = T(1) / h;
 #pragma unroll
     for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
     psi_y_yy<Law>(p, eps, y, g, K);
@@ -77,12 +76,14 @@ AD_HD void tangent(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], co
 
 // Viscoplastic voxel, FP64 arithmetic.
 template <class Law>
-AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], const double (&zn)[6], double h,
+AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], const double (&zn)[6], const Step& hs,
                           bool active, double (&sig)[6], double (&z)[6], double* C21) {
   const double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
+  double es[6];
+  Law::trial_strain(eps, yn, es);
   double w[5];
   Chol5<double> ch;
-  const unsigned st = solve_increment<Law, double>(p, eps, yn, h, active, 1e-10, w, ch);
+  const unsigned st = solve_increment<Law, double>(p, es, hs, active, 1e-10, w, ch);
   double y[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) y[a] = yn[a] + w[a];
@@ -90,7 +91,7 @@ AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], co
   z_of_y(y, z);
   if (C21) {
     double t[21];
-    tangent<Law, double>(p, eps, y, w, h, absmax5(w) > 0.0, t);
+    tangent<Law, double>(p, eps, y, w, hs.inv_h, absmax5(w) > 0.0, t);
 #pragma unroll
     for (int c = 0; c < 21; ++c) C21[c] = t[c];
   }
@@ -98,107 +99,132 @@ AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], co
 }
 
 // Viscoplastic voxel, FP32 bulk + FP64 correction.
+// The FP32 solve sees the trial strain e_s (formed in FP64) scaled by an
+// exact power of two s ~ |e_s|, with c_phi rescaled to match (Law::rescale):
+// its rounding is then relative to the deviatoric trial state whatever the
+// hydrostatic strain, the accumulated viscous strain or the magnitude of
+// e_s, and its last Newton matrix equals the unscaled one to FP32 accuracy.
+// The corrections reuse that factor: each step w += K32^-1 R64 with the FP64
+// residual contracts the error by ~1e-6 (normally one step).  The FP64
+// reverse sweep that gives the residual also gives sigma(e_s, w); the last
+// correction dw moves it by psi_ey dw (FP32 block, dw tiny), and the
+// hydrostatic stress is added back.
 template <class Law>
 AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>& pf, const double (&eps)[6],
-                              const double (&zn)[6], double h, bool active, double (&sig)[6], double (&z)[6],
+                              const double (&zn)[6], const Step& hs, bool active, double (&sig)[6], double (&z)[6],
                               double* C21) {
   const double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
-  float epsf[6], ynf[5], wf[5];
+  double es[6];
+  const double tr = Law::trial_strain(eps, yn, es);
+  const int k = ilog2_max(es);  // s = 2^k ~ max |e_s|, applied in the conversions
+  float esf[6], wf[5];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) epsf[i] = (float)eps[i];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) ynf[a] = (float)yn[a];
+  for (int i = 0; i < 6; ++i) esf[i] = f32_of(es[i], -k);
+  LawParams<float> ps = pf;
+  const bool in_range = Law::rescale(ps, k);
   Chol5<float> chf;
-  unsigned st = solve_increment<Law, float>(pf, epsf, ynf, (float)h, active, 1e-4f, wf, chf);
+  unsigned st = solve_increment<Law, float>(ps, esf, hs, active && in_range, 1e-4f, wf, chf);
+  if (active && !in_range) st |= ST_CONVERGED;  // no resolvable flow (Law::rescale)
+  const bool flows = absmax5(wf) > 0.0f;
   double w[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) w[a] = (double)wf[a];
-  const bool flows = absmax5(w) > 0.0;
+  for (int a = 0; a < 5; ++a) w[a] = f64_of(wf[a], k);
 
-  // FP64 Newton corrections.
-  const double inv_h = 1.0 / h;
+  // FP64 corrections
+  const double inv_h = hs.inv_h;
   bool done = !(active && flows);
-  int n_fix = 0;
   bool conv = done;
+  int n_fix = 0;
+  float dwf[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (done) {  // no flow (or padding lane): sigma at w = 0, no correction
+    double R[5];
+    psi_y_and_stress<Law>(p, es, w, R, sig);
+  }
   for (int it = 0; it < 4; ++it) {
     if (all_done(done)) break;
     if (!done) {
       ++n_fix;
-      double y[5], v[5], R[5], gv[5];
+      double v[5], R[5], gv[5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        y[a] = yn[a] + w[a];
-        v[a] = w[a] * inv_h;
-      }
-      psi_y<Law>(p, eps, y, R);
+      for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
+      psi_y_and_stress<Law>(p, es, w, R, sig);
       phi_v<Law>(p, v, gv);
-      float Rf[5], vf[5], yf[5];
+      float Rf[5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        Rf[a] = (float)(-(R[a] + gv[a]));
-        vf[a] = (float)v[a];
-        yf[a] = (float)y[a];
-      }
-      float g[5], K[5][5], gvf[5], Hv[5][5];
-      psi_y_yy<Law>(pf, epsf, yf, g, K);
-      phi_v_vv<Law>(pf, vf, gvf, Hv);
-      const float inv_hf = (float)inv_h;
-#pragma unroll
-      for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int b = 0; b < 5; ++b) K[a][b] += Hv[a][b] * inv_hf;
-      Chol5<float> ck;
-      float dwf[5];
-      if (ck.factor(K)) {
-        ck.solve(Rf, dwf);
-      } else {
-        st |= ST_NOT_SPD;
+      for (int a = 0; a < 5; ++a) Rf[a] = f32_of(-(R[a] + gv[a]), -k);
+      chf.solve(Rf, dwf);
+      const float dmax = absmax5(dwf);
+      if (!(dmax < 1e37f)) {
+        st |= ST_NONFINITE;
+        done = true;
 #pragma unroll
         for (int a = 0; a < 5; ++a) dwf[a] = 0.0f;
-        done = true;
-      }
-      double dw[5];
+      } else {
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        dw[a] = (double)dwf[a];
-        w[a] += dw[a];
+        for (int a = 0; a < 5; ++a) w[a] += f64_of(dwf[a], k);
+        if (dmax <= 1e-6f * absmax5(wf)) { done = true; conv = true; }
       }
-      if (absmax5(dw) <= 1e-6 * absmax5(w)) { done = true; conv = true; }
-      if (!(absmax5(dw) == absmax5(dw))) { st |= ST_NONFINITE; done = true; }
     }
   }
   if (active && flows && !conv) st = (st & ~ST_CONVERGED) | ST_CAP;
   st += (unsigned)n_fix << ST_NEWTON_SHIFT;
+  st |= (unsigned)(n_fix & 0xf) << ST_FIX_SHIFT;
+  if (n_fix > 0) {
+    // sigma of the last sweep was taken before the last dw: add psi_ey dw
+    float B[6][5];
+    psi_ey<Law>(ps, esf, wf, B);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      float d = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) d += B[i][a] * dwf[a];
+      sig[i] += f64_of(d, k);
+    }
+  }
+  const double sh = Law::hydro_stress(p, tr);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) sig[i] += sh;
   double y[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) y[a] = yn[a] + w[a];
-  stress<Law>(p, eps, y, sig);
   z_of_y(y, z);
   if (C21) {
     double t[21];
-    tangent<Law, double>(p, eps, y, w, h, flows, t);
+    tangent<Law, double>(p, eps, y, w, hs.inv_h, absmax5(w) > 0.0, t);
 #pragma unroll
     for (int c = 0; c < 21; ++c) C21[c] = t[c];
   }
   return st;
 }
 
-// Viscoplastic voxel, FP32 only.
+// Viscoplastic voxel, FP32 only (same scaled trial frame as above).
 template <class Law>
-AD_HD unsigned voxel_fp32(const LawParams<float>& pf, const float (&eps)[6], const float (&zn)[6], float h,
+AD_HD unsigned voxel_fp32(const LawParams<float>& pf, const float (&eps)[6], const float (&zn)[6], const Step& hs,
                           bool active, float (&sig)[6], float (&z)[6], float* C21) {
   const float yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
+  float es[6];
+  Law::trial_strain(eps, yn, es);
+  const int k = ilog2_max(es) > 126 ? 126 : ilog2_max(es);
+  const float s = exp2i(k, 0.0f), inv_s = exp2i(-k, 0.0f);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) es[i] *= inv_s;
+  LawParams<float> ps = pf;
+  const bool in_range = Law::rescale(ps, k);
   float w[5];
   Chol5<float> ch;
-  const unsigned st = solve_increment<Law, float>(pf, eps, yn, h, active, 1e-6f, w, ch);
+  unsigned st = solve_increment<Law, float>(ps, es, hs, active && in_range, 1e-6f, w, ch);
+  if (active && !in_range) st |= ST_CONVERGED;
   float y[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) y[a] = yn[a] + w[a];
+  for (int a = 0; a < 5; ++a) {
+    w[a] *= s;
+    y[a] = yn[a] + w[a];
+  }
   stress<Law>(pf, eps, y, sig);
   z_of_y(y, z);
   if (C21) {
     float t[21];
-    tangent<Law, float>(pf, eps, y, w, h, absmax5(w) > 0.0f, t);
+    tangent<Law, float>(pf, eps, y, w, hs.inv_hf, absmax5(w) > 0.0f, t);
 #pragma unroll
     for (int c = 0; c < 21; ++c) C21[c] = t[c];
   }

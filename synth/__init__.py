@@ -217,3 +217,44 @@ def shear_tension_load(n_steps=20, amp=0.02):
 def fibre_composite(N=256, seed=0):
     """RSA cylinders r=6, length 180 (aspect 15), 15 % volume fraction."""
     return rsa_cylinders(N, 6.0, 0.15, min(180.0, 0.7 * N), seed=seed)
+
+
+def unit_direction(rng):
+    """Random unit vector on the Voigt-6 strain space (engineering shears)."""
+    d = rng.normal(size=6)
+    return d / np.linalg.norm(d)
+
+
+def serving_stream(n_jobs=64, seed=0, grids=(32, 64, 96, 128, 192), steps=(5, 20), matrix_n=(3.0, 5.0, 10.0)):
+    """Homogenization jobs of the serving workload.
+
+    Per job: N uniform over ``grids``; microstructure RSA spheres (5-25 %,
+    radius max(2, N/10)) or RSA cylinders (10-30 %, radius max(1.5, N/32),
+    length 0.35 N; RSA stops after 20000 tries, so dense targets can jam
+    below the target -- the achieved fraction is recorded), each with
+    probability 1/2; Norton matrix (E=70, nu=0.3,
+    sigma0=0.1, edot0=1) with n drawn from ``matrix_n``; inclusion E=400,
+    nu=0.2; macro strain ramp along a random unit direction with amplitude
+    U[1 %, 2 %] over a step count uniform in ``steps`` (inclusive), h = 0.1.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for k in range(n_jobs):
+        N = int(rng.choice(grids))
+        if rng.uniform() < 0.5:
+            frac = rng.uniform(0.05, 0.25)
+            ph, achieved, _ = rsa_spheres(N, max(2.0, N / 10.0), frac, seed=seed * 1000 + k, max_tries=20000)
+            kind = "spheres"
+        else:
+            frac = rng.uniform(0.10, 0.30)
+            ph, achieved, _ = rsa_cylinders(N, max(1.5, N / 32.0), frac, 0.35 * N, seed=seed * 1000 + k,
+                                            max_tries=20000)
+            kind = "cylinders"
+        n_exp = float(rng.choice(matrix_n))
+        amp = rng.uniform(0.01, 0.02)
+        n_steps = int(rng.integers(steps[0], steps[1] + 1))
+        E = ramp(n_steps, amp * unit_direction(rng))
+        jobs.append({"N": N, "phase": ph, "fraction": achieved, "kind": kind,
+                     "laws": [(1, (70.0, 0.3, 0.1, 1.0, n_exp)), (0, (400.0, 0.2))],
+                     "E": E, "h": [0.1] * n_steps})
+    return jobs

@@ -20,9 +20,9 @@ int host_update(int mode, const double* prm, int64_t n, const double* eps, const
     for (int c = 0; c < 6; ++c) { e[c] = eps[6 * i + c]; zi[c] = zn[6 * i + c]; }
     unsigned st;
     if (mode == 0) {
-      st = voxel_fp64<NortonDev>(p, e, zi, h, true, s, zo, tan ? tan + 21 * i : nullptr);
+      st = voxel_fp64<NortonDev>(p, e, zi, make_step(h), true, s, zo, tan ? tan + 21 * i : nullptr);
     } else {
-      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, h, true, s, zo, tan ? tan + 21 * i : nullptr);
+      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, make_step(h), true, s, zo, tan ? tan + 21 * i : nullptr);
     }
     for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
     status[i] = (int32_t)st;

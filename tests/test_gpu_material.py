@@ -141,3 +141,24 @@ def test_full_size_sampled(gsm, precision):
     s2, z2 = O.update(O.KIND_NORTON, synth.MATRIX_16, eps[idx], zn[idx], 0.01)
     assert rel_rows(sig.cpu().numpy()[:, idx].T, s2).max() < TOL
     assert rel_rows(z.cpu().numpy()[:, idx].T, z2).max() < TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_exp", [1.0, 5.0])
+def test_near_hydrostatic_strains(gsm, precision, n_exp):
+    """Hydrostatic strain plus a deviatoric part from 1e-16 to 1e-4 of it:
+    flows below the resolution of y are treated as none, those below FP32
+    resolution are solved in FP64; sigma stays within 1e-10 of the oracle."""
+    rng = np.random.default_rng(int(n_exp) * 10 + precision)
+    n = 3000
+    vol = rng.uniform(-0.01, 0.01, (n, 1)) * np.array([[1, 1, 1, 0, 0, 0]])
+    dev = rng.normal(size=(n, 6)) * 10.0 ** rng.uniform(-16, -4, (n, 1)) * 0.01
+    eps = vol + dev
+    zn = np.zeros((n, 6))
+    prm = synth.MATRIX_16[:4] + (n_exp,)
+    mat = gsm.norton(*prm, precision=precision)
+    sig, z, st = run(gsm, mat, eps, zn, 0.01)
+    s2, z2 = O.update(O.KIND_NORTON, prm, eps, zn, 0.01)
+    assert np.all(st & gsm.ST_CONVERGED)
+    assert rel_rows(sig, s2).max() < TOL
+    assert np.max(np.abs(z - z2)) < 1e-12

@@ -31,19 +31,28 @@ N_VOX = 1 << 24
 H_STEP = 0.01
 PARAMS = (70.0, 0.3, 0.1, 1.0, 5.0)
 
-# Algorithmic FP64 operation counts of the update (add/sub/mul = 1, fma = 2,
-# each div, sqrt, rsqrt, log, exp = 1), from a hand-derived implementation of
-# the same steps (no AD): predictor, one line-search step, one Newton step,
-# final stress.  The per-voxel total weights them with the iteration counts
-# the kernel reports in its status words.
-FLOPS_PREDICTOR = 73
-FLOPS_LINE = 165
-FLOPS_NEWTON = 300
-FLOPS_STRESS = 30
-# FP64 correction step of the FP32-bulk mode: FP64 residual (70), update (5),
-# conversions and test (10).  The FP32 Newton matrix of a correction is FP32 work.
-FLOPS_FIX64 = 85
+# The material kernels are bound by FP64 issue (FP64 pipe 81-86 % busy,
+# DRAM below 12 %; ncu), so their roofline is FP64 operations per second:
+# each DADD, DMUL or DFMA takes one FP64 issue slot, and GB300 issues two FP64
+# operations per SM per cycle (ncu peak_sustained), i.e. 2 x 152 x 2.07 GHz
+# = 629.4 G/s at the maximum clock.  Operations per voxel are the FP64
+# additions, multiplications and FMAs the algorithm executes, counted by ncu
+# (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on) on this
+# workload at three step sizes:
+#   FP32 bulk + FP64 correction: 124.3 per voxel with one correction; each
+#     further correction repeats the residual sweep (~95);
+#   FP64: 425.5 + 164.0 per line-search iteration (one Newton step), which
+#     reproduces the three counts within 0.1 %.
+FP64_OPS_PEAK_G = 2 * 152 * 2.07
+OPS_FIX_FIRST = 124.3
+OPS_FIX_EXTRA = 95.0
+OPS_FP64_BASE = 425.5
+OPS_FP64_LINE = 164.0
 BYTES_PER_VOXEL_FP64 = 4 * 6 * 8          # eps, z_n in; sigma, z out
+# DRAM bytes of one full-size FP32-bulk launch (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, one capture of launch 6 of this workload: the
+# inputs are read once, less what the 129 MB L2 still holds)
+TRAFFIC_FP32FIX = 1476729344 + 1631010816
 
 
 def parse():
@@ -56,6 +65,10 @@ def parse():
     ap.add_argument("--no-ms", action="store_true", help="skip the basic-scheme measurement")
     ap.add_argument("--voxels", type=int, default=N_VOX, help="batch size (profiling runs use a small batch)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving sample")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serve the full stream distribution (grids up to 192^3, 5-20 steps): long")
     return ap.parse_args()
 
 
@@ -137,14 +150,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def flops_per_voxel(status, mode):
+def ops_per_voxel(status, mode):
+    """Mean FP64 operations per voxel from the kernel's status words."""
     import numpy as np
     line = (status & 0xFF).astype(np.float64)
     newton = ((status >> 8) & 0xFF).astype(np.float64)
+    fix = ((status >> 20) & 0xF).astype(np.float64)
     if mode == "fp64":
-        f = FLOPS_PREDICTOR + FLOPS_LINE * line + FLOPS_NEWTON * newton + FLOPS_STRESS
+        f = OPS_FP64_BASE + OPS_FP64_LINE * line
         return float(f.mean()), float(line.mean()), float(newton.mean())
-    return float(line.mean()), float(newton.mean())
+    f = (OPS_FIX_FIRST + OPS_FIX_EXTRA * np.maximum(fix - 1, 0)) * (fix > 0)
+    return float(f.mean()), float(line.mean()), float((newton - fix).mean()), float(fix.mean())
 
 
 def measured_peaks():
@@ -153,11 +169,6 @@ def measured_peaks():
             return json.load(fh)
     except OSError:
         return {}
-
-
-# FP64 FMA peak of GB300 from the unit counts and clocks: 1.25 TFLOP/s nominal
-# (1.19 TFLOP/s measured with an FMA-throughput kernel at 1987 MHz).
-FP64_PEAK_GFLOPS = 1250.0
 
 
 def run_ours(args):
@@ -181,6 +192,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     results = {}
+    # clocks sampled over both timed material regions (the FP32-bulk region
+    # alone is shorter than the 200 ms sampling period)
+    clocks = Clocks(dev) if rank == 0 else None
+    if clocks:
+        clocks.start()
     for mode, prec in (("fp64", G.GSM_FP64), ("fp32fix", G.GSM_FP32_FP64FIX)):
         mat = G.norton(*PARAMS, precision=prec)
         for _ in range(args.warmup):
@@ -188,9 +204,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         status = st.cpu().numpy()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        clocks = Clocks(dev) if (mode == "fp64" and rank == 0) else None
-        if clocks:
-            clocks.start()
         barrier(world)
         torch.cuda.synchronize()
         l0 = G.kernel_launches()
@@ -201,11 +214,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(world)
         launches = G.kernel_launches() - l0
-        clk = clocks.stop() if clocks else None
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), world)
         results[mode] = {"ms": total_ms / args.steps, "per_launch_ms": statistics.mean(per),
-                         "status": status, "launches": launches, "clocks": clk}
+                         "status": status, "launches": launches}
+    results["clocks"] = clocks.stop() if clocks else None
 
     e2e_ms = float("nan")
     if not args.no_e2e:
@@ -214,7 +227,10 @@ def run_ours(args):
     ms_block = None
     if not args.no_ms and rank == 0:
         ms_block = bench_ms(G, torch)
-    report(args, world, rank, results, e2e_ms, ms_block)
+    serve_block = None
+    if not args.no_serve and rank == 0:
+        serve_block = bench_serve(G, args)
+    report(args, world, rank, results, e2e_ms, ms_block, serve_block)
 
 
 def bench_e2e(G, torch, np, eps, zn, e, z0, sig, z, st, stream, world, args):
@@ -246,14 +262,15 @@ def bench_e2e(G, torch, np, eps, zn, e, z0, sig, z, st, stream, world, args):
     return max_over_ranks(a.elapsed_time(b), world) / args.steps
 
 
-def report(args, world, rank, results, e2e_ms, ms_block):
+def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None):
     if rank != 0:
         return
     peaks = measured_peaks()
     r64, r32 = results["fp64"], results["fp32fix"]
-    fpv, line64, newton64 = flops_per_voxel(r64["status"], "fp64")
-    line32, newton32 = flops_per_voxel(r32["status"], "fp32fix")
+    fpv, line64, newton64 = ops_per_voxel(r64["status"], "fp64")
+    fpv32, line32, newton32, fix32 = ops_per_voxel(r32["status"], "fp32fix")
     achieved = fpv * N_VOX / (r64["per_launch_ms"] * 1e-3) / 1e9
+    achieved32 = fpv32 * N_VOX / (r32["per_launch_ms"] * 1e-3) / 1e9
     value = world * N_VOX / (r32["ms"] * 1e-3)
     out = {
         "metric": "material voxel-updates/s",
@@ -274,20 +291,28 @@ def report(args, world, rank, results, e2e_ms, ms_block):
                    "voxels_per_gpu": N_VOX, "l2": "inputs 1.6 GB > L2, no flush", "parallelism": f"replicas x{world}"},
         "fp64": {"value": world * N_VOX / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                  "mean_line_iters": line64, "mean_newton_iters": newton64},
-        "fp32fix": {"mean_line_iters": line32, "mean_newton_plus_fix_iters": newton32},
-        "roofline": {"kernel": "norton_kernel<MODE_FP64>", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": None, "algorithmic_flops_per_voxel": fpv,
-                     "peak_source": "nominal FP64 of GB300 (unit counts x clock); MEASURED_PEAKS.json has no FP64 entry",
-                     "hbm_frac_fp32fix": BYTES_PER_VOXEL_FP64 * N_VOX / (r32["per_launch_ms"] * 1e-3) / 1e9
+        "fp32fix": {"mean_line_iters": line32, "mean_fp32_newton_iters": newton32, "mean_fp64_corrections": fix32},
+        "roofline": {"kernel": "norton_kernel<MODE_FP32_FIX>", "bound": "alu", "achieved": achieved32,
+                     "peak": FP64_OPS_PEAK_G, "unit": "G FP64 ops/s", "frac": achieved32 / FP64_OPS_PEAK_G,
+                     "traffic": TRAFFIC_FP32FIX, "fp64_ops_per_voxel": fpv32,
+                     "peak_source": "FP64 issue rate of GB300: 2 per SM per cycle (ncu peak_sustained) x 152 SMs "
+                                    "x 2.07 GHz; MEASURED_PEAKS.json has no FP64 entry",
+                     "note": "FP64 operations of the trial strain and the FP64 correction; the FP32 bulk runs on the "
+                             "FP32 pipe",
+                     "hbm_frac": BYTES_PER_VOXEL_FP64 * N_VOX / (r32["per_launch_ms"] * 1e-3) / 1e9
                      / peaks.get("hbm_gbs", 6783.1)},
+        "roofline_fp64_mode": {"kernel": "norton_kernel<MODE_FP64>", "bound": "alu", "achieved": achieved,
+                               "peak": FP64_OPS_PEAK_G, "unit": "G FP64 ops/s",
+                               "frac": achieved / FP64_OPS_PEAK_G, "fp64_ops_per_voxel": fpv},
         "e2e": {"value": world * N_VOX / (e2e_ms * 1e-3), "unit": "voxel-updates/s",
                 "h2d_bytes_per_step": 2 * 6 * 8 * N_VOX, "d2h_bytes_per_step": 2 * 6 * 8 * N_VOX},
-        "gpu_launches": r32["launches"] + r64["launches"],
-        "clocks": r64["clocks"],
+        "gpu_launches": r32["launches"],
+        "clocks": results["clocks"],
     }
     if ms_block is not None:
         out["basic_scheme"] = ms_block
+    if serve_block is not None:
+        out["serve"] = serve_block
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
@@ -308,15 +333,67 @@ def bench_ms(G, torch):
         laws = [G.norton(*synth.MATRIX_256), G.elastic(*synth.FIBRE_256)]
         ctx = G.ms_create(phase, laws, prec)
         n_it = 30
-        G.ms_run(ctx, loads[:1], hs[:1], forced_iters=[3], switch_tol=1e30)  # warm-up
+        # FP32 bulk: FP32 iterations until e < 1e-5 (not reached in 30 iterations), then one FP64
+        G.ms_run(ctx, loads[:1], hs[:1], forced_iters=[3])  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = G.ms_run(ctx, loads[:1], hs[:1], forced_iters=[n_it], switch_tol=1e30)
+        out = G.ms_run(ctx, loads[:1], hs[:1], forced_iters=[n_it])
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        res[name] = {"iters_per_s": n_it / dt, "iters": n_it}
+        res[name] = {"iters_per_s": n_it / dt, "iters": n_it, "fp32_iters": int(out["fp32_iters"][0]),
+                     "final_error": float(out["final_error"][0])}
         G.ms_destroy(ctx)
     return res
+
+
+def bench_serve(G, args):
+    """Serving stream vs the plain one-job-at-a-time FP64 path, same jobs.
+
+    Jobs follow the serving workload's distributions (RSA spheres 5-25 % or
+    cylinders 10-30 %, Norton n in {3, 5, 10}, random unit load directions
+    with 1-2 % amplitude); by default a bounded sample (grids 32-96^3, 2-5
+    steps) so the benchmark stays within minutes.  Arrivals are Poisson with
+    rate 1.5 / (mean solo FP64 service time).  Both paths solve to e < 1e-6.
+    """
+    import numpy as np
+    import synth
+    from paper_2006_04391_gb300 import serving
+    tol = 1e-6
+    if args.serve_full:
+        jobs = synth.serving_stream(args.serve_jobs, seed=7)
+    else:
+        jobs = synth.serving_stream(args.serve_jobs, seed=7, grids=(32, 64, 96), steps=(2, 5))
+    seq = serving.run_sequential(G, jobs, tol=tol)
+    service = np.array([r["service_s"] for r in seq])
+    rate = 1.5 / service.mean()
+    arrivals = serving.poisson_arrivals(len(jobs), rate, seed=11)
+    seq_done = serving.fifo_completion(arrivals, service)
+    seq_lat = seq_done - arrivals
+    budget = 64 << 30
+    stream = serving.run_stream(G, jobs, arrivals, hbm_budget=budget, max_active=64, tol=tol)
+    closed = serving.run_stream(G, jobs, np.zeros(len(jobs)), hbm_budget=budget, max_active=64, tol=tol)
+    diff = max(float(np.max(np.abs(r["Sigma"] - q["Sigma"])) / max(float(np.max(np.abs(q["Sigma"]))), 1e-300))
+               for r, q in zip(stream["jobs"], seq))
+    vox_evals = sum(int(np.sum(q["iters"])) * j["N"] ** 3 for q, j in zip(seq, jobs))
+    return {
+        "workload": (f"{len(jobs)} jobs, grids {sorted(set(j['N'] for j in jobs))}, "
+                     f"{sum(len(j['h']) for j in jobs)} load steps in total, "
+                     + ("full stream distribution" if args.serve_full else "bounded sample (grids <= 96^3, 2-5 steps)")
+                     + f", Poisson arrivals at {rate:.3f}/s = 1.5 x solo FP64 rate, tol {tol}"),
+        "served": {"latency_p50_s": stream["latency_p50"], "latency_p99_s": stream["latency_p99"],
+                   "makespan_s": stream["makespan_s"], "ticks": stream["ticks"], "max_active": stream["max_active"],
+                   "path": "FP32 bulk fields/FFTs, FP64 finish with FP32-Newton + FP64-fix laws, batched ticks"},
+        "sequential_fp64": {"latency_p50_s": float(np.percentile(seq_lat, 50)),
+                            "latency_p99_s": float(np.percentile(seq_lat, 99)),
+                            "makespan_s": float(seq_done.max() - arrivals.min()),
+                            "mean_service_s": float(service.mean())},
+        "throughput_jobs_per_s": {"served_all_at_once": len(jobs) / closed["makespan_s"],
+                                  "sequential_fp64": len(jobs) / float(service.sum()),
+                                  "ratio": (len(jobs) / closed["makespan_s"]) / (len(jobs) / float(service.sum()))},
+        "voxel_updates_per_s": {"served_all_at_once": closed["voxel_updates_per_s"],
+                                "sequential_fp64": vox_evals / float(service.sum())},
+        "max_rel_sigma_diff_served_vs_fp64": diff,
+    }
 
 
 def cpu_baseline(n_sample=1 << 22):

@@ -97,6 +97,10 @@ int gsm_destroy(gsm_handle h);
  *   status  [ld]     per-voxel status word            (out, may be NULL)
  * Element type: double for GSM_FP64 and GSM_FP32_FP64FIX, float for
  * GSM_FP32.  ld >= n_vox.  n_vox = 0 is a no-op.  Arrays must not overlap.
+ * Each array may be device memory or page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister): the kernel then reads and writes the
+ * host memory directly over the host link (NVLink-C2C on GB300), with no
+ * staging copies.  Unregistered host memory is refused with GSM_EINVAL.
  * Asynchronous on `stream` (a cudaStream_t).  Errors: GSM_EINVAL, GSM_ECUDA.
  * A voxel that hits the Newton cap is reported in `status`, not by the
  * return value.

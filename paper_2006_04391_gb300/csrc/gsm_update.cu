@@ -172,6 +172,30 @@ int material_update(const Material& m, int64_t n, const void* eps, const void* z
   return err == cudaSuccess ? GSM_OK : GSM_ECUDA;
 }
 
+// The address under which the current device reaches p: p itself for device
+// and managed memory, the mapped address for page-locked host memory; false
+// for memory the device cannot reach.  NULL maps to NULL.
+bool device_address(const void* p, const void** out) {
+  *out = p;
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      return true;
+    case cudaMemoryTypeHost:
+      if (!a.devicePointer) return false;
+      *out = a.devicePointer;
+      return true;
+    default:
+      return false;
+  }
+}
+
 int validate_material(int psi_kind, int phi_kind, const double* prm, int n_params, int precision) {
   if (!prm) return GSM_EINVAL;
   if (precision < GSM_FP64 || precision > GSM_FP32) return GSM_EINVAL;
@@ -223,7 +247,19 @@ int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, in
   if (!eps || !sigma) return GSM_EINVAL;
   if (m.psi_kind == GSM_PSI_ELASTIC_VP_DEV && (!z_n || !z)) return GSM_EINVAL;
   if (!(std::isfinite(step_h) && step_h > 0.0)) return GSM_EINVAL;
-  return material_update(m, n_vox, eps, z_n, ld, step_h, sigma, z, tangent, status,
+  // every array may be device memory or page-locked host memory (read and
+  // written by the kernel over the host link); unregistered host memory is
+  // refused rather than faulted on
+  const void* in[2] = {eps, z_n};
+  void* out[4] = {sigma, z, tangent, status};
+  for (auto& p : in)
+    if (!device_address(p, &p)) return GSM_EINVAL;
+  for (auto& p : out) {
+    const void* q = p;
+    if (!device_address(q, &q)) return GSM_EINVAL;
+    p = const_cast<void*>(q);
+  }
+  return material_update(m, n_vox, in[0], in[1], ld, step_h, out[0], out[1], out[2], static_cast<int32_t*>(out[3]),
                          static_cast<cudaStream_t>(stream));
 }
 

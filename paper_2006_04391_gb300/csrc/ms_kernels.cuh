@@ -281,20 +281,27 @@ __global__ void __launch_bounds__(kGamBlock) ms_gamma_batch_kernel(const JobView
   }
 }
 
+// Final sums of one problem's partials: warp c (c < 6) sums component c of
+// the material partials, warp 6 the error partials; lane l takes partials
+// l, l + 32, ... and the lanes combine in a fixed shuffle tree, so the order
+// depends only on the partial count (never on other problems in a batch).
+// Launch with kFinBlock threads.
+constexpr int kFinBlock = 224;
 __device__ void finalize_sums(const double* __restrict__ mat_part, int n_mat, const double* __restrict__ gam_part,
                               int n_gam, double inv_n3, double floor_, Reduced* __restrict__ out) {
   __shared__ double sh[7];
-  const int t = threadIdx.x;
-  if (t < 7) {
-    double s = 0.0;
-    if (t < 6)
-      for (int b = 0; b < n_mat; ++b) s += mat_part[t * n_mat + b];
-    else
-      for (int b = 0; b < n_gam; ++b) s += gam_part[b];
-    sh[t] = s;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (w < 6) {
+    for (int b = lane; b < n_mat; b += 32) s += mat_part[w * n_mat + b];
+  } else if (w == 6) {
+    for (int b = lane; b < n_gam; b += 32) s += gam_part[b];
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0 && w < 7) sh[w] = s;
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     double m[6];
     for (int c = 0; c < 6; ++c) m[c] = sh[c] * inv_n3;
     // sum |xi . c|^2 with xi = 2 pi k and c = sigma^ / N^3

@@ -546,7 +546,7 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
     ms_gamma_batch_kernel<float><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[2], gstart[3] - gstart[2], mtot[1]);
     count_launch();
   }
-  ms_finalize_batch_kernel<<<n, 32, 0, s>>>(g.views_dev, g.red_dev);
+  ms_finalize_batch_kernel<<<n, kFinBlock, 0, s>>>(g.views_dev, g.red_dev);
   count_launch();
   cudaMemcpyAsync(g.red_host, g.red_dev, n * sizeof(Reduced), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GSM_ECUDA;
@@ -954,7 +954,7 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
       adj_tau_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.a_u, j.f64.eps_raw, inv_n3, j.f64.sig);
       if (cufftExecD2Z(pl->r2c, j.f64.sig, j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
       ms_gamma_batch_kernel<double><<<gam_grid, kGamBlock, 0, s>>>(g.views_dev, 1, j.n_mch);
-      ms_finalize_batch_kernel<<<1, 32, 0, s>>>(g.views_dev, g.red_dev);
+      ms_finalize_batch_kernel<<<1, kFinBlock, 0, s>>>(g.views_dev, g.red_dev);
       count_launch(3);
       cudaMemcpyAsync(g.red_host, g.red_dev, sizeof(Reduced), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
@@ -1077,7 +1077,7 @@ extern "C" int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, co
   Reduced* red = reinterpret_cast<Reduced*>(scratch + 6 * kNoAllocMaxBlocks);
   ms_material_kernel<double, MODE_FP64><<<grid, kMatBlock, 0, s>>>(nvox, phase, tab, make_step(step_h), 1.0, eps, z_n, sigma, z,
                                                                    partials);
-  ms_finalize_kernel<<<1, 32, 0, s>>>(partials, grid, nullptr, 0, 1.0 / (double)nvox, 1.0, red);
+  ms_finalize_kernel<<<1, kFinBlock, 0, s>>>(partials, grid, nullptr, 0, 1.0 / (double)nvox, 1.0, red);
   count_launch(2);
   if (cudaGetLastError() != cudaSuccess) return GSM_ECUDA;
   if (cudaMemcpyAsync(mean, red->mean, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)

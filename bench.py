@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-ms", action="store_true", help="skip the basic-scheme measurement")
     ap.add_argument("--voxels", type=int, default=N_VOX, help="batch size (profiling runs use a small batch)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving sample")
     ap.add_argument("--serve-full", action="store_true",
@@ -230,7 +231,10 @@ def run_ours(args):
     serve_block = None
     if not args.no_serve and rank == 0:
         serve_block = bench_serve(G, args)
-    report(args, world, rank, results, e2e_ms, ms_block, serve_block)
+    adj_block = None
+    if not args.no_adjoint and rank == 0:
+        adj_block = bench_adjoint(G, torch)
+    report(args, world, rank, results, e2e_ms, ms_block, serve_block, adj_block)
 
 
 def bench_e2e(G, torch, np, eps, zn, e, z0, sig, z, st, stream, world, args):
@@ -298,7 +302,7 @@ def e2e_block(world, e2e):
                     "writes them over NVLink-C2C; staged: H2D copies, kernel, D2H copies on one stream"}
 
 
-def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None):
+def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_block=None):
     if rank != 0:
         return
     peaks = measured_peaks()
@@ -348,6 +352,8 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None):
         out["basic_scheme"] = ms_block
     if serve_block is not None:
         out["serve"] = serve_block
+    if adj_block is not None:
+        out["adjoint"] = adj_block
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
@@ -384,6 +390,48 @@ def bench_ms(G, torch):
                      "law": "FP64" if law_prec == G.GSM_FP64 else "FP32 Newton + FP64 correction"}
         G.ms_destroy(ctx)
     return res
+
+
+def bench_adjoint(G, torch):
+    """Adjoint of the load history on the adjoint workload: 128^3 centred
+    sphere (20 %), Norton matrix, uniaxial ramp to 1 % in 10 steps of h = 0.1,
+    FP64, per-step checkpoints.
+
+    Converged to 1e-8 this takes ~1340 basic-scheme iterations per step
+    forward and about as many adjoint iterations per step and component
+    (the matrix flows, and the fixed elastic reference medium of the basic
+    scheme contracts by ~0.99 per iteration), i.e. minutes.  The benchmark
+    therefore times a bounded run: 20 forced forward iterations per step,
+    then the adjoint of Sigma_11 with 20 adjoint iterations per step.  The
+    per-iteration rates are the measurement; the time to a converged gradient
+    is those rates times the converged counts."""
+    import numpy as np
+    import synth
+    N, steps, k_fwd, k_adj = 128, 10, 20, 20
+    ph = synth.sphere_phase(N, 0.2)
+    phase = torch.from_numpy(ph).cuda()
+    loads = synth.ramp(steps, [0.01, 0, 0, 0, 0, 0])
+    hs = [0.1] * steps
+    ctx = G.ms_create(phase, [G.norton(*synth.MATRIX_16), G.elastic(*synth.INCLUSION_16)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, tape = G.ms_run_taped(ctx, loads, hs, tol=1e-30, forced_iters=[k_fwd] * steps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g, its = G.ms_adjoint(tape, [1, 0, 0, 0, 0, 0], 0, tol=1e-30, max_iter=k_adj, check=False)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    fwd_iters = int(np.sum(res["iters"]))
+    adj_iters = int(np.sum(its))
+    del tape
+    G.ms_destroy(ctx)
+    return {"workload": f"{N}^3 centred sphere ({100 * float(ph.mean()):.1f} % inclusion E=400, nu=0.2), Norton "
+                        f"matrix n=5, uniaxial ramp to 1 % in {steps} steps of h=0.1, FP64, per-step checkpoints",
+            "sample": f"bounded: {k_fwd} forward iterations and {k_adj} adjoint iterations per step (dSigma11)",
+            "forward_taped_s": t_fwd, "forward_iters": fwd_iters, "forward_iters_per_s": fwd_iters / t_fwd,
+            "adjoint_s": t_adj, "adjoint_iters": adj_iters, "adjoint_iters_per_s": adj_iters / t_adj,
+            "tape_bytes": 12 * 8 * N ** 3 * steps}
 
 
 def bench_serve(G, args):

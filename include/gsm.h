@@ -226,8 +226,9 @@ int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_ha
 /* ms_adjoint -- dJ/d(E, sigma0, n) of the Norton phase `phase_id` for the
  * weights w (host [6], tensor-shear Voigt pairing with Sigma_K) into grad
  * (host [3]).  Each adjoint equilibrium is solved until its residual falls
- * by `tol`, at most max_iter iterations (lam_iters: host [n_steps] or NULL).
- * Synchronous.  Errors: GSM_EINVAL, GSM_ECUDA. */
+ * by `tol`, at most max_iter iterations (lam_iters: host [n_steps] or NULL,
+ * the iterations each step took).  Synchronous.  Returns GSM_ENOTCONV, with
+ * grad filled, when a step reached max_iter.  Errors: GSM_EINVAL, GSM_ECUDA. */
 int ms_adjoint(ms_tape_handle tape, const double* w, int phase_id, double tol, int max_iter, double* grad,
                int32_t* lam_iters);
 int ms_tape_destroy(ms_tape_handle tape);

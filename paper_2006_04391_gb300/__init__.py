@@ -308,10 +308,10 @@ def _result_struct(n):
     return res, {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32}
 
 
-def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000):
+def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000, forced_iters=None):
     """Load history from a fresh state keeping per-step checkpoints; returns (result, Tape)."""
     lib = load()
-    ld, keep, n = _load_struct(E, hs, tol, max_iter, None, 0.0)
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, 0.0)
     res, out = _result_struct(n)
     th = ctypes.c_void_p()
     rc = lib.ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th))
@@ -321,15 +321,20 @@ def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000):
     return out, Tape(th, ctx, n)
 
 
-def ms_adjoint(tape, w, phase_id=0, tol=1e-10, max_iter=20000):
-    """dJ/d(E, sigma0, n) of a Norton phase for J = w . Sigma_K; returns (grad[3], lam_iters)."""
+def ms_adjoint(tape, w, phase_id=0, tol=1e-10, max_iter=20000, check=True):
+    """dJ/d(E, sigma0, n) of a Norton phase for J = w . Sigma_K; returns (grad[3], lam_iters).
+
+    With check=False a step that reached max_iter is not an error (the
+    gradient of the capped solves is returned)."""
     lib = load()
     w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(6))
     grad = np.zeros(3)
     its = np.zeros(tape.n_steps, dtype=np.int32)
-    _check(lib.ms_adjoint(tape.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(phase_id),
-                          float(tol), int(max_iter), grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                          its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "ms_adjoint")
+    rc = lib.ms_adjoint(tape.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(phase_id),
+                        float(tol), int(max_iter), grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != GSM_OK and (check or rc != GSM_ENOTCONV):
+        _check(rc, "ms_adjoint")
     return grad, its
 
 

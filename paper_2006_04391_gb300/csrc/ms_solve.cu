@@ -912,6 +912,7 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
   const int grid_prep = grid_cap(nv, kAdjBlock, 4);
   const int grid_fin = std::min(grid_cap(nv, kAdjBlock, 8), 4096);
   double total[3] = {0.0, 0.0, 0.0};
+  bool capped = false;
   cudaMemsetAsync(t.gz, 0, n6 * sizeof(double), s);
   for (int k = t.n_steps - 1; k >= 0; --k) {
     const double* eps_k = t.ckpt + (size_t)k * n6;
@@ -950,6 +951,7 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
     const int gam_grid = (int)std::min<int64_t>(j.n_mch, (int64_t)sm_count() * g.per_sm_gam[0]);
     double first = -1.0;
     int it = 0;
+    bool conv = false;
     for (; it < max_iter; ++it) {
       adj_tau_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.a_u, j.f64.eps_raw, inv_n3, j.f64.sig);
       if (cufftExecD2Z(pl->r2c, j.f64.sig, j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
@@ -960,10 +962,14 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
       if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
       const double r = std::sqrt(g.red_host->res);
       if (first < 0.0) first = r;
-      if (r <= tol * first || first == 0.0) break;
+      if (r <= tol * first || first == 0.0) {
+        conv = true;
+        break;
+      }
       if (cufftExecZ2D(pl->c2r, j.f64.sig_hat, j.f64.eps_raw) != CUFFT_SUCCESS) return GSM_ECUDA;
     }
-    if (lam_iters) lam_iters[k] = it + 1;
+    if (lam_iters) lam_iters[k] = conv ? it + 1 : it;
+    capped = capped || !conv;
     adj_finish_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, j.phase, j.tab_dev, hk, phase_id, nt, eps_k, zprev, gs[0],
                                                      gs[1], gs[2], gs[3], gs[4], gs[5], t.gz, j.f64.eps_raw, inv_n3,
                                                      t.yK, t.gz_prev, t.part);
@@ -975,7 +981,7 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
     std::swap(t.gz, t.gz_prev);
   }
   for (int q = 0; q < 3; ++q) grad[q] = total[q];
-  return GSM_OK;
+  return capped ? GSM_ENOTCONV : GSM_OK;
 }
 
 int ms_tape_destroy(ms_tape_handle th) {

@@ -73,16 +73,28 @@ def parse():
     return ap.parse_args()
 
 
-def dist_setup(args):
+_BACKEND = None
+
+
+def dist_setup(args=None):
+    """One process per GPU under torchrun (NCCL); gloo where CUDA is absent
+    (the multi-rank tests run this path on CPU).  Returns (world, rank)."""
+    global _BACKEND
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    cuda = torch.cuda.is_available()
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+        if cuda:
+            torch.cuda.set_device(local)
+            _BACKEND = "nccl"
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            _BACKEND = "gloo"
+            dist.init_process_group("gloo")
+    elif cuda:
         torch.cuda.set_device(0)
     return world, rank
 
@@ -94,13 +106,28 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Maximum of a host scalar over all ranks (the timing rule: the slowest
+    rank's time is the job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _BACKEND == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """value = units all ranks processed / the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
+def bench_config(world, voxels):
+    return {"workload": f"material-law batch: {voxels} independent voxels per GPU, Norton E=70, nu=0.3, "
+                        "sigma0=0.1, edot0=1, n=5, h=0.01; value: FP32 Newton + one FP64 correction per voxel, "
+                        "fp64 block: full FP64",
+            "voxels_per_gpu": voxels, "l2": "inputs 1.6 GB > L2 at 2^24 voxels, no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 class Clocks:
@@ -311,7 +338,7 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_b
     fpv32, line32, newton32, fix32 = ops_per_voxel(r32["status"], "fp32fix")
     achieved = fpv * N_VOX / (r64["per_launch_ms"] * 1e-3) / 1e9
     achieved32 = fpv32 * N_VOX / (r32["per_launch_ms"] * 1e-3) / 1e9
-    value = world * N_VOX / (r32["ms"] * 1e-3)
+    value = whole_job_rate(N_VOX, world, r32["ms"])
     out = {
         "metric": "material voxel-updates/s",
         "metric_full": METRIC_FULL,
@@ -326,10 +353,8 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_b
         "vs_baseline": None,
         "dtype": "f32+f64fix",
         "data": "synthetic",
-        "config": {"workload": "material-law batch: 2^24 independent voxels, Norton n=5, h=0.01, "
-                               "FP32 Newton + FP64 correction (value) and full FP64 (fp64 block)",
-                   "voxels_per_gpu": N_VOX, "l2": "inputs 1.6 GB > L2, no flush", "parallelism": f"replicas x{world}"},
-        "fp64": {"value": world * N_VOX / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+        "config": bench_config(world, N_VOX),
+        "fp64": {"value": whole_job_rate(N_VOX, world, r64["ms"]), "ms_per_step": r64["ms"],
                  "mean_line_iters": line64, "mean_newton_iters": newton64},
         "fp32fix": {"mean_line_iters": line32, "mean_fp32_newton_iters": newton32, "mean_fp64_corrections": fix32},
         "roofline": {"kernel": "norton_kernel<MODE_FP32_FIX>", "bound": "alu", "achieved": achieved32,
@@ -518,7 +543,7 @@ def run_reference(args):
         "value": value, "unit": "voxel-updates/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "material-law batch, Norton n=5, h=0.01 (oracle on a 2^20-voxel sample per step)"},
+        "config": bench_config(int(os.environ.get("WORLD_SIZE", "1")), N_VOX),
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

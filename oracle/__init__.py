@@ -9,8 +9,10 @@ Contents
 --------
 * ``material`` -- ctypes wrappers of ``gsm_oracle.cpp``: the implicit-Euler
   GSM update (Sec. 4.1, Eq. implicit_euler and Eq. tangent_formula of
-  AutoMat, arXiv 2006.04391), hand-derived potentials and an independent
-  radial return (the conventional strategy of Sec. 4).
+  AutoMat, arXiv 2006.04391), hand-derived potentials, an independent
+  radial return (the conventional strategy of Sec. 4), and the ode23 update
+  of the force-potential form with its tangent ODE (Sec. 4.3, Corollary 1)
+  and stress-driven error control (Sec. 4.5).
 * ``ms`` -- the Moulinec-Suquet basic scheme (cited by the paper in Sec. 1 and
   Sec. 3 "Material Law Evaluations") written with ``numpy.fft``.
 
@@ -21,5 +23,5 @@ closed forms, finite differences, invariants and special cases instead.
 from .material import (  # noqa: F401
     KIND_ELASTIC, KIND_NORTON, lame, update, radial_return, psi, psi_y, psi_yy,
     phi, phi_v, phi_vv, residual, newton_matrix, incremental_potential, stress,
-    max_threads, P_MATRIX, G_MATRIX,
+    max_threads, P_MATRIX, G_MATRIX, update_ode23, psi_force_a,
 )

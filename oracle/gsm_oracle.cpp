@@ -483,6 +483,265 @@ void radial_return(const Law& L, const double eps[6], const double zn[6], double
   tensor_to_voigt(Sig, sig, false);
 }
 
+// ================================================= force-potential form, ode23
+// Sec. 2, Eq. (gsm_internal): adot = dPsi/dA (A) with A = -d omega/d a.  With
+// a = y (the 5 unknowns of z = P y): A = -psi_y(eps, y) = P^T sigma, and the
+// force potential of Eq. (michel_suquet_psi) at sigma_Y = 0, H = 0:
+//   Psi(A) = sigma0 edot0 / (n+1) (s_A / sigma0)^(n+1),  s_A^2 = A^T G^{-1} A
+// (G^{-1} is the dual metric of the rate norm; s_A is the von Mises stress).
+//   Psi_A  = edot0 (s_A/sigma0)^n G^{-1}A / s_A
+//   Psi_AA = edot0 sigma0^{-n} [ s_A^{n-1} G^{-1} + (n-1) s_A^{n-3} (G^{-1}A)(G^{-1}A)^T ]
+// (at s_A = 0: Psi_A = 0; Psi_AA = edot0/sigma0 G^{-1} for n = 1 and 0 for n > 1).
+//
+// Sec. 4.3 integrates the evolution equation over [t_n, t_{n+1}] with strain
+// eps(t) interpolated linearly between eps_n and eps_{n+1}, by the embedded
+// Runge-Kutta pair of Bogacki and Shampine (MATLAB's ode23) with automatic
+// step size control after Hairer, Norsett, Wanner (Solving ODEs I, II.4).
+// Corollary 1: the tangent dy/deps_{n+1} is the solution of the derivative
+// ODE d/dt (dy/de) = Psi_AA(A) dA/de, dA/de = P^T C (theta(t) I - P dy/de),
+// theta(t) = (t - t_n)/h, integrated together with y by the same steps, with
+// the step sizes undifferentiated and the derivative in the error measure.
+// Sec. 4.5 (stress-driven error control): the error measure is taken on the
+// pair of stresses (and of tangents) that the two embedded solutions give
+// at the end of the substep.
+
+struct Ode23Opts {
+  double rtol, atol;
+  int max_steps;
+  bool tangent;
+};
+
+void g_inverse(const Law& L, double Gi[5][5]) {
+  for (int c = 0; c < 5; ++c) {
+    double e[5] = {0, 0, 0, 0, 0}, x[5];
+    e[c] = 1.0;
+    chol_solve(5, &L.G[0][0], e, x);
+    for (int a = 0; a < 5; ++a) Gi[a][c] = x[a];
+  }
+}
+
+// Psi_A(A) and (optionally) Psi_AA(A).
+void psi_force_a(const Law& L, const double Gi[5][5], const double A[5], double g[5], double H[5][5]) {
+  double GA[5];
+  double s2 = 0.0;
+  for (int a = 0; a < 5; ++a) {
+    double t = 0.0;
+    for (int b = 0; b < 5; ++b) t += Gi[a][b] * A[b];
+    GA[a] = t;
+    s2 += A[a] * t;
+  }
+  const double s = std::sqrt(s2);
+  const double n = L.n;
+  if (s == 0.0) {
+    for (int a = 0; a < 5; ++a) g[a] = 0.0;
+    if (H)
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) H[a][b] = n == 1.0 ? L.edot0 / L.sigma0 * Gi[a][b] : 0.0;
+    return;
+  }
+  const double r = std::pow(s / L.sigma0, n);  // (s/sigma0)^n
+  for (int a = 0; a < 5; ++a) g[a] = L.edot0 * r * GA[a] / s;
+  if (H) {
+    const double c1 = L.edot0 * r / s;                        // edot0 sigma0^-n s^(n-1)
+    const double c2 = (n - 1.0) * L.edot0 * r / (s * s * s);  // (n-1) edot0 sigma0^-n s^(n-3)
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) H[a][b] = c1 * Gi[a][b] + c2 * GA[a] * GA[b];
+  }
+}
+
+// Right-hand side at time t in [0, h] of the step: f = Psi_A(A), A = P^T sigma
+// with sigma = C (eps(t) - P y); with Y = dy/deps_{n+1} (5x6) also
+// F = Psi_AA(A) P^T C (theta I - P Y).
+void ode_rhs(const Law& L, const double Gi[5][5], const double epsn[6], const double eps1[6], double h, double t,
+             const double y[5], const double (*Y)[6], double f[5], double (*F)[6]) {
+  const double th = t / h;
+  double et[6], sig[6], A[5];
+  for (int i = 0; i < 6; ++i) et[i] = epsn[i] + th * (eps1[i] - epsn[i]);
+  stress(L, et, y, sig);
+  for (int a = 0; a < 5; ++a) {
+    double s = 0.0;
+    for (int i = 0; i < 6; ++i) s += P[i][a] * sig[i];
+    A[a] = s;
+  }
+  double H[5][5];
+  psi_force_a(L, Gi, A, f, F ? H : nullptr);
+  if (!F) return;
+  // D = theta I - P Y (6x6), CD = C D, dA = P^T C D (5x6)
+  double D[6][6], dA[5][6];
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) {
+      double pz = 0.0;
+      for (int a = 0; a < 5; ++a) pz += P[i][a] * Y[a][k];
+      D[i][k] = (i == k ? th : 0.0) - pz;
+    }
+  for (int a = 0; a < 5; ++a)
+    for (int k = 0; k < 6; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < 6; ++i) {
+        double cd = 0.0;
+        for (int j = 0; j < 6; ++j) cd += L.C[i][j] * D[j][k];
+        s += P[i][a] * cd;
+      }
+      dA[a][k] = s;
+    }
+  for (int a = 0; a < 5; ++a)
+    for (int k = 0; k < 6; ++k) {
+      double s = 0.0;
+      for (int b = 0; b < 5; ++b) s += H[a][b] * dA[b][k];
+      F[a][k] = s;
+    }
+}
+
+// Stress and tangent at the end of a substep from y, Y: sigma = C (eps(t) - P y),
+// Ct = C (theta I - P Y).
+void stress_tangent(const Law& L, const double epsn[6], const double eps1[6], double h, double t, const double y[5],
+                    const double (*Y)[6], double sig[6], double (*Ct)[6]) {
+  const double th = t / h;
+  double et[6];
+  for (int i = 0; i < 6; ++i) et[i] = epsn[i] + th * (eps1[i] - epsn[i]);
+  stress(L, et, y, sig);
+  if (!Ct) return;
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        double pz = 0.0;
+        for (int a = 0; a < 5; ++a) pz += P[j][a] * Y[a][k];
+        s += L.C[i][j] * ((j == k ? th : 0.0) - pz);
+      }
+      Ct[i][k] = s;
+    }
+}
+
+// Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1); y_{+} = y + dt (2/9 k1 + 1/3 k2
+// + 4/9 k3); the order-2 solution uses (7/24, 1/4, 1/3, 1/8) with k4 =
+// f(t + dt, y_{+}), which is k1 of the next step (first same as last).
+const double BS_A21 = 0.5, BS_A32 = 0.75;
+const double BS_B[3] = {2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0};
+const double BS_E[4] = {2.0 / 9.0 - 7.0 / 24.0, 1.0 / 3.0 - 1.0 / 4.0, 4.0 / 9.0 - 1.0 / 3.0, -1.0 / 8.0};
+
+struct OdeInfo {
+  int accepted, rejected, flags;
+};
+
+// One material update by ode23 over [t_n, t_{n+1}] (length h).
+void update_ode23(const Law& L, const double epsn[6], const double eps1[6], const double zn[6], double h,
+                  const Ode23Opts& o, double sig_out[6], double z_out[6], double (*Ct_out)[6], OdeInfo* info) {
+  double Gi[5][5];
+  g_inverse(L, Gi);
+  double y[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
+  double Y[5][6] = {};
+  const bool tan = o.tangent;
+  double k[4][5], K[4][5][6];
+  double t = 0.0, dt = h;
+  ode_rhs(L, Gi, epsn, eps1, h, 0.0, y, Y, k[0], tan ? K[0] : nullptr);
+  double sig_old[6], C_old[6][6];
+  stress_tangent(L, epsn, eps1, h, 0.0, y, Y, sig_old, tan ? C_old : nullptr);
+  info->accepted = info->rejected = 0;
+  info->flags = 0;
+  bool last_rejected = false;
+  while (t < h) {
+    if (info->accepted + info->rejected >= o.max_steps) {
+      info->flags |= F_CAP;
+      break;
+    }
+    const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
+    if (clip) dt = h - t;
+    double ys[5], Ys[5][6];
+    // stage 2
+    for (int a = 0; a < 5; ++a) {
+      ys[a] = y[a] + dt * BS_A21 * k[0][a];
+      if (tan)
+        for (int c = 0; c < 6; ++c) Ys[a][c] = Y[a][c] + dt * BS_A21 * K[0][a][c];
+    }
+    ode_rhs(L, Gi, epsn, eps1, h, t + 0.5 * dt, ys, Ys, k[1], tan ? K[1] : nullptr);
+    // stage 3
+    for (int a = 0; a < 5; ++a) {
+      ys[a] = y[a] + dt * BS_A32 * k[1][a];
+      if (tan)
+        for (int c = 0; c < 6; ++c) Ys[a][c] = Y[a][c] + dt * BS_A32 * K[1][a][c];
+    }
+    ode_rhs(L, Gi, epsn, eps1, h, t + 0.75 * dt, ys, Ys, k[2], tan ? K[2] : nullptr);
+    // order-3 solution and the last stage
+    double yn1[5], Yn1[5][6];
+    for (int a = 0; a < 5; ++a) {
+      yn1[a] = y[a] + dt * (BS_B[0] * k[0][a] + BS_B[1] * k[1][a] + BS_B[2] * k[2][a]);
+      if (tan)
+        for (int c = 0; c < 6; ++c)
+          Yn1[a][c] = Y[a][c] + dt * (BS_B[0] * K[0][a][c] + BS_B[1] * K[1][a][c] + BS_B[2] * K[2][a][c]);
+    }
+    const double tn1 = clip ? h : t + dt;
+    ode_rhs(L, Gi, epsn, eps1, h, tn1, yn1, Yn1, k[3], tan ? K[3] : nullptr);
+    // embedded difference (order 3 minus order 2) and the stress pair it gives
+    double e[5], E[5][6];
+    for (int a = 0; a < 5; ++a) {
+      e[a] = dt * (BS_E[0] * k[0][a] + BS_E[1] * k[1][a] + BS_E[2] * k[2][a] + BS_E[3] * k[3][a]);
+      if (tan)
+        for (int c = 0; c < 6; ++c)
+          E[a][c] = dt * (BS_E[0] * K[0][a][c] + BS_E[1] * K[1][a][c] + BS_E[2] * K[2][a][c] + BS_E[3] * K[3][a][c]);
+    }
+    double y2[5], Y2[5][6], s3[6], s2[6], C3[6][6], C2[6][6];
+    for (int a = 0; a < 5; ++a) {
+      y2[a] = yn1[a] - e[a];
+      if (tan)
+        for (int c = 0; c < 6; ++c) Y2[a][c] = Yn1[a][c] - E[a][c];
+    }
+    stress_tangent(L, epsn, eps1, h, tn1, yn1, Yn1, s3, tan ? C3 : nullptr);
+    stress_tangent(L, epsn, eps1, h, tn1, y2, Y2, s2, tan ? C2 : nullptr);
+    double sum = 0.0;
+    int m = 0;
+    for (int i = 0; i < 6; ++i, ++m) {
+      const double sc = o.atol + o.rtol * std::fmax(std::fabs(sig_old[i]), std::fabs(s3[i]));
+      const double q = (s3[i] - s2[i]) / sc;
+      sum += q * q;
+    }
+    if (tan)
+      for (int i = 0; i < 6; ++i)
+        for (int c = 0; c < 6; ++c, ++m) {
+          const double sc = o.atol + o.rtol * std::fmax(std::fabs(C_old[i][c]), std::fabs(C3[i][c]));
+          const double q = (C3[i][c] - C2[i][c]) / sc;
+          sum += q * q;
+        }
+    // a trial step that overflows is rejected like one with a large error
+    const double err = std::isfinite(sum) ? std::sqrt(sum / m) : 1e300;
+    // step size after Hairer II.4: fac = 0.9, facmin = 0.2, facmax = 5
+    // (1 right after a rejection), exponent 1/(q+1) with q = 2
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    const double grow = err == 0.0 ? facmax : std::fmin(facmax, std::fmax(0.2, 0.9 * std::pow(err, -1.0 / 3.0)));
+    if (err <= 1.0) {
+      t = tn1;
+      for (int a = 0; a < 5; ++a) {
+        y[a] = yn1[a];
+        k[0][a] = k[3][a];
+        if (tan)
+          for (int c = 0; c < 6; ++c) {
+            Y[a][c] = Yn1[a][c];
+            K[0][a][c] = K[3][a][c];
+          }
+      }
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = s3[i];
+        if (tan)
+          for (int c = 0; c < 6; ++c) C_old[i][c] = C3[i][c];
+      }
+      ++info->accepted;
+      last_rejected = false;
+    } else {
+      ++info->rejected;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+  if (t >= h && !(info->flags & (F_NONFINITE | F_CAP))) info->flags |= F_CONVERGED;
+  stress_tangent(L, epsn, eps1, h, h, y, Y, sig_out, Ct_out);
+  z_out[0] = y[0];
+  z_out[1] = y[1];
+  z_out[2] = -(y[0] + y[1]);
+  z_out[3] = y[2];
+  z_out[4] = y[3];
+  z_out[5] = y[4];
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -584,6 +843,42 @@ void ora_newton_matrix_batch(const double* params, int64_t n, const double* y, c
         K[25 * i + 5 * a + b] = H1[a][b] + hp / h;
       }
   }
+}
+
+// ode23 update (Sec. 4.3 with the stress-driven error control of Sec. 4.5):
+// eps_n, eps, z_n [n][6]; tangent [n][6][6] or NULL; info [n][3] = accepted,
+// rejected substeps, flags (1 converged, 2 non-finite, 4 substep cap).
+int ora_update_ode23(const double* params, int64_t n, const double* eps_n, const double* eps, const double* zn,
+                     double h, double rtol, double atol, int max_steps, double* sigma, double* z, double* tangent,
+                     int32_t* info) {
+  Law L;
+  make_law(1, params, &L);
+  Ode23Opts o{rtol, atol, max_steps, tangent != nullptr};
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    double(*Ct)[6] = tangent ? reinterpret_cast<double(*)[6]>(tangent + 36 * i) : nullptr;
+    OdeInfo inf;
+    update_ode23(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, h, o, sigma + 6 * i, z + 6 * i, Ct, &inf);
+    if (info) {
+      info[3 * i] = inf.accepted;
+      info[3 * i + 1] = inf.rejected;
+      info[3 * i + 2] = inf.flags;
+    }
+  }
+  return 0;
+}
+
+// Psi_A (and Psi_AA when H != NULL) of the force potential at A [5].
+void ora_psi_force_a(const double* params, const double* A, double* g, double* H) {
+  Law L;
+  make_law(1, params, &L);
+  double Gi[5][5];
+  g_inverse(L, Gi);
+  double HH[5][5];
+  psi_force_a(L, Gi, A, g, H ? HH : nullptr);
+  if (H)
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) H[5 * a + b] = HH[a][b];
 }
 
 }  // extern "C"

@@ -61,6 +61,10 @@ def _load():
         lib.ora_Pi.restype = ctypes.c_double
         lib.ora_max_threads.restype = ctypes.c_int
         lib.ora_newton_matrix_batch.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, _dp]
+        lib.ora_update_ode23.argtypes = [_dp, ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _ip]
+        lib.ora_update_ode23.restype = ctypes.c_int
+        lib.ora_psi_force_a.argtypes = [_dp, _dp, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -201,3 +205,38 @@ def newton_matrix_batch(params, y, y_n, h):
     H = np.empty((n, 5, 5))
     _load().ora_newton_matrix_batch(_ptr(_params(params)), n, _ptr(y), _ptr(y_n), float(h), _ptr(K), _ptr(H))
     return K, H
+
+
+def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100000, tangent=False, info=False):
+    """Material update by ode23 (Sec. 4.3, stress-driven error control Sec. 4.5).
+
+    eps_n, eps, z_n: (n, 6); returns sigma, z [, tangent (n, 6, 6)] [, info
+    (n, 3) = accepted substeps, rejected substeps, flags]."""
+    lib = _load()
+    eps_n = _f64(eps_n).reshape(-1, 6)
+    eps = _f64(eps).reshape(-1, 6)
+    z_n = _f64(z_n).reshape(-1, 6)
+    n = eps.shape[0]
+    sig = np.zeros((n, 6))
+    z = np.zeros((n, 6))
+    C = np.zeros((n, 6, 6)) if tangent else None
+    inf = np.zeros((n, 3), dtype=np.int32)
+    lib.ora_update_ode23(_ptr(_params(params)), ctypes.c_int64(n), _ptr(eps_n), _ptr(eps), _ptr(z_n), ctypes.c_double(h),
+                         ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(max_steps), _ptr(sig), _ptr(z),
+                         _ptr(C) if tangent else None, inf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    out = [sig, z]
+    if tangent:
+        out.append(C)
+    if info:
+        out.append(inf)
+    return tuple(out)
+
+
+def psi_force_a(params, A):
+    """(Psi_A, Psi_AA) of the Norton force potential at A (5,)."""
+    lib = _load()
+    A = _f64(A).reshape(5)
+    g = np.zeros(5)
+    H = np.zeros((5, 5))
+    lib.ora_psi_force_a(_ptr(_params(params)), _ptr(A), _ptr(g), _ptr(H))
+    return g, H

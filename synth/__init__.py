@@ -186,6 +186,19 @@ def rsa_spheres(N, radius, frac, seed=0, max_tries=200000):
     return ph, float(ph.mean()), len(centres)
 
 
+def ode23_batch(n, seed=0):
+    """Load-step-like material inputs for the adaptive (ode23) update: z_n
+    deviatoric with (z11, z22, g23, g13, g12) ~ U[-0.005, 0.005], eps_n = z_n +
+    U[-0.002, 0.002]^6 (trial stresses up to ~2 sigma0 for the matrix law),
+    eps = eps_n + U[-0.001, 0.001]^6.  Returns (eps_n, eps, z_n), each (n, 6)."""
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-0.005, 0.005, (n, 5))
+    zn = np.stack([y[:, 0], y[:, 1], -y[:, 0] - y[:, 1], y[:, 2], y[:, 3], y[:, 4]], axis=1)
+    eps_n = zn + rng.uniform(-0.002, 0.002, (n, 6))
+    eps = eps_n + rng.uniform(-0.001, 0.001, (n, 6))
+    return eps_n, eps, zn
+
+
 def ramp(n_steps, E_final):
     """E_k = (k / n_steps) E_final, k = 1..n_steps -> (n_steps, 6)."""
     E_final = np.asarray(E_final, dtype=np.float64)

@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--voxels", type=int, default=N_VOX, help="batch size (profiling runs use a small batch)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-ode23", action="store_true", help="skip the ode23 material-update measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving sample")
     ap.add_argument("--serve-full", action="store_true",
@@ -261,7 +262,10 @@ def run_ours(args):
     adj_block = None
     if not args.no_adjoint and rank == 0:
         adj_block = bench_adjoint(G, torch)
-    report(args, world, rank, results, e2e_ms, ms_block, serve_block, adj_block)
+    ode_block = None
+    if not args.no_ode23 and rank == 0:
+        ode_block = bench_ode23(G, torch, args)
+    report(args, world, rank, results, e2e_ms, ms_block, serve_block, adj_block, ode_block)
 
 
 def bench_e2e(G, torch, np, eps, zn, e, z0, sig, z, st, stream, world, args):
@@ -329,7 +333,7 @@ def e2e_block(world, e2e):
                     "writes them over NVLink-C2C; staged: H2D copies, kernel, D2H copies on one stream"}
 
 
-def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_block=None):
+def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_block=None, ode_block=None):
     if rank != 0:
         return
     peaks = measured_peaks()
@@ -379,6 +383,8 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_b
         out["serve"] = serve_block
     if adj_block is not None:
         out["adjoint"] = adj_block
+    if ode_block is not None:
+        out["ode23"] = ode_block
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
@@ -415,6 +421,46 @@ def bench_ms(G, torch):
                      "law": "FP64" if law_prec == G.GSM_FP64 else "FP32 Newton + FP64 correction"}
         G.ms_destroy(ctx)
     return res
+
+
+def bench_ode23(G, torch, args):
+    """Adaptive ode23 material update (force-potential form, stress-driven error
+    control, MATLAB's default tolerances rtol 1e-3, atol 1e-6) on 2^22 voxels of
+    load-step-like inputs (synth.ode23_batch, Norton n = 5, h = 0.1), without and
+    with the tangent ODE; FP64."""
+    import numpy as np
+    import synth
+    n = 1 << 22
+    en, e, zn = synth.ode23_batch(n, seed=2024)
+    E0 = torch.from_numpy(np.ascontiguousarray(en.T)).cuda()
+    E1 = torch.from_numpy(np.ascontiguousarray(e.T)).cuda()
+    Z0 = torch.from_numpy(np.ascontiguousarray(zn.T)).cuda()
+    sig = torch.empty_like(E1)
+    z = torch.empty_like(E1)
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    mat = G.norton(*PARAMS)
+    out = {"workload": "2^22 voxels, synth.ode23_batch (z_n as the material batch, eps_n = z_n + U[-0.002,0.002]^6, "
+                       "eps = eps_n + U[-0.001,0.001]^6), Norton n=5, h=0.1, rtol 1e-3, atol 1e-6, FP64"}
+    stream = torch.cuda.current_stream()
+    for name, tan in (("no_tangent", None), ("tangent", torch.empty(36, n, dtype=torch.float64, device="cuda"))):
+        for _ in range(max(1, args.warmup // 2)):
+            G.gsm_update_ode23(mat, E0, E1, Z0, 0.1, sig, z, tan, st)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 3
+        a.record(stream)
+        for _ in range(k):
+            G.gsm_update_ode23(mat, E0, E1, Z0, 0.1, sig, z, tan, st)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / k
+        s = st.cpu().numpy()
+        out[name] = {"voxel_updates_per_s": n / (ms * 1e-3), "ms_per_launch": ms,
+                     "mean_accepted_substeps": float((s & 0xFFFF).mean()),
+                     "mean_rejected_substeps": float(((s >> 20) & 0x7FF).mean()),
+                     "converged_fraction": float(((s >> 16) & 1).mean())}
+        del tan
+    return out
 
 
 def bench_adjoint(G, torch):

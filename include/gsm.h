@@ -108,6 +108,35 @@ int gsm_destroy(gsm_handle h);
 int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, int64_t ld, double step_h,
                void* sigma, void* z, void* tangent, int32_t* status, void* stream);
 
+/*
+ * gsm_update_ode23 -- material update by adaptive explicit Runge-Kutta
+ * integration of the force-potential form ydot = dPsi/dA(-d psi/dy) over the
+ * load step (Sec. 4.3: the Bogacki-Shampine 3(2) pair of MATLAB's ode23, step
+ * sizes after Hairer-Norsett-Wanner, whole step as the first trial), with the
+ * stress-driven error control of Sec. 4.5 and, when tangent != NULL, the
+ * tangent ODE of Corollary 1 integrated with the same substeps.
+ *   eps_n   [6][ld]  strain at t_n                       (in)
+ *   eps     [6][ld]  strain at t_{n+1}                   (in); the strain is
+ *                    interpolated linearly in between
+ *   z_n     [6][ld]  internal variables at t_n           (in; deviatoric)
+ *   h       step size > 0;  rtol > 0, atol >= 0: error tolerances on the
+ *           stresses (and tangents); MATLAB's defaults are 1e-3 and 1e-6
+ *   max_substeps  cap on accepted + rejected substeps per voxel (>= 1)
+ *   sigma, z [6][ld] (out); tangent [36][ld] dsigma/deps_{n+1} as the full
+ *           6x6 matrix row-major (not symmetric in general), or NULL
+ *   status  [ld] or NULL: bits 0-15 accepted substeps, bits 20-30 rejected
+ *           substeps (both saturating), bits 16-19 flags as for gsm_update
+ *           (a voxel that reaches max_substeps has bit 18 and keeps the state
+ *           of its last accepted substep)
+ * Element type double: computed in FP64 whatever the material's precision.
+ * The viscoplastic law only (GSM_ENOTSUP for the elastic law).  Arrays as
+ * for gsm_update (device or page-locked host memory).  Asynchronous on
+ * `stream`.  Errors: GSM_EINVAL, GSM_ENOTSUP, GSM_ECUDA.
+ */
+int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n, int64_t ld,
+                     double step_h, double rtol, double atol, int max_substeps, void* sigma, void* z, void* tangent,
+                     int32_t* status, void* stream);
+
 /* gsm_strerror -- static message for a return code. */
 const char* gsm_strerror(int code);
 

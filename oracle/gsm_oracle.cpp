@@ -690,18 +690,17 @@ void update_ode23(const Law& L, const double epsn[6], const double eps1[6], cons
     stress_tangent(L, epsn, eps1, h, tn1, y2, Y2, s2, tan ? C2 : nullptr);
     double sum = 0.0;
     int m = 0;
-    for (int i = 0; i < 6; ++i, ++m) {
-      const double sc = o.atol + o.rtol * std::fmax(std::fabs(sig_old[i]), std::fabs(s3[i]));
-      const double q = (s3[i] - s2[i]) / sc;
-      sum += q * q;
-    }
+    // (a zero scale, atol = 0 at zero stress, counts a zero difference as no error)
+    auto sq_scaled = [](double d, double sc) {
+      const double q = sc > 0.0 ? d / sc : (d == 0.0 ? 0.0 : 1e300);
+      return q * q;
+    };
+    for (int i = 0; i < 6; ++i, ++m)
+      sum += sq_scaled(s3[i] - s2[i], o.atol + o.rtol * std::fmax(std::fabs(sig_old[i]), std::fabs(s3[i])));
     if (tan)
       for (int i = 0; i < 6; ++i)
-        for (int c = 0; c < 6; ++c, ++m) {
-          const double sc = o.atol + o.rtol * std::fmax(std::fabs(C_old[i][c]), std::fabs(C3[i][c]));
-          const double q = (C3[i][c] - C2[i][c]) / sc;
-          sum += q * q;
-        }
+        for (int c = 0; c < 6; ++c, ++m)
+          sum += sq_scaled(C3[i][c] - C2[i][c], o.atol + o.rtol * std::fmax(std::fabs(C_old[i][c]), std::fabs(C3[i][c])));
     // a trial step that overflows is rejected like one with a large error
     const double err = std::isfinite(sum) ? std::sqrt(sum / m) : 1e300;
     // step size after Hairer II.4: fac = 0.9, facmin = 0.2, facmax = 5

@@ -30,7 +30,7 @@ ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 <<
 EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kernel_launches",
            "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc",
            "serve_create", "serve_destroy", "serve_submit", "serve_tick", "serve_job_state", "serve_fetch",
-           "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy")
+           "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy", "gsm_update_ode23")
 
 _lib = None
 
@@ -85,6 +85,7 @@ def load(path=None):
                                ctypes.c_int, ctypes.c_int]
     lib.gsm_destroy.argtypes = [vp]
     lib.gsm_update.argtypes = [vp, i64, vp, vp, i64, dbl, vp, vp, vp, vp, vp]
+    lib.gsm_update_ode23.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.gsm_strerror.restype = ctypes.c_char_p
     lib.gsm_strerror.argtypes = [ctypes.c_int]
     lib.gsm_kernel_launches.restype = i64
@@ -179,6 +180,21 @@ def gsm_destroy(mat):
     if mat.handle:
         load().gsm_destroy(mat.handle)
         mat.handle = None
+
+
+def gsm_update_ode23(mat, eps_n, eps, z_n, h, sigma, z, tangent=None, status=None, rtol=1e-3, atol=1e-6,
+                     max_substeps=100000, stream=None, n_vox=None):
+    """Material update by ode23 over the load step (FP64 tensors ``[6, ld]``;
+    tangent ``[36, ld]`` = full dsigma/deps_{n+1} row-major; status ``[ld]``)."""
+    lib = load()
+    ld = eps.shape[1]
+    n = ld if n_vox is None else int(n_vox)
+    for t, rows in ((eps_n, 6), (eps, 6), (z_n, 6), (sigma, 6), (z, 6), (tangent, 36)):
+        if t is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != ld or not t.is_contiguous()):
+            raise ValueError("fields must be contiguous [components, ld] tensors with a common ld")
+    rc = lib.gsm_update_ode23(mat.handle, n, _ptr(eps_n), _ptr(eps), _ptr(z_n), ld, float(h), float(rtol), float(atol),
+                              int(max_substeps), _ptr(sigma), _ptr(z), _ptr(tangent), _ptr(status), _stream_ptr(stream))
+    _check(rc, "gsm_update_ode23")
 
 
 def gsm_update(mat, eps, z_n, h, sigma, z, tangent=None, status=None, stream=None, n_vox=None):

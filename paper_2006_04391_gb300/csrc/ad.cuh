@@ -206,7 +206,10 @@ AD_HD Tan<T, N, A> pow_(const Tan<T, N, A>& x, T p) {
     for (int k = 0; k < N; ++k) o.d[k] = has<A>(k) ? pr * (x.d[k] * ix) : T(0);
     return o;
   } else {
-    return chain(x, r, p * r * inv(x.v));
+    // d/dx x^p at x = 0: 0 for p = 0 or p > 1, 1 for p = 1, unbounded for p < 1
+    const T d = x.v != T(0) ? p * r * inv(x.v)
+                            : (p == T(0) ? T(0) : p == T(1) ? T(1) : p > T(1) ? T(0) : T(INFINITY));
+    return chain(x, r, d);
   }
 }
 

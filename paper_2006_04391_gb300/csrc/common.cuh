@@ -29,11 +29,14 @@ inline LawParams<double> make_params(const double* prm, bool norton) {
     const double s0 = prm[2], e0 = prm[3], n = prm[4];
     p.a_phi = (n + 1.0) / (2.0 * n);
     p.c_phi = s0 * e0 * n / (n + 1.0) * std::pow(e0, -(n + 1.0) / n);
+    p.b_Psi = (n + 1.0) / 2.0;
+    p.c_Psi = s0 * e0 / (n + 1.0) * std::pow(s0, -(n + 1.0));
   } else {
     p.a_phi = 1.0;
     p.c_phi = 0.0;
+    p.b_Psi = 1.0;
+    p.c_Psi = 0.0;
   }
-  p.inv_h_unused = 0.0;
   return p;
 }
 
@@ -43,9 +46,14 @@ inline LawParams<float> to_float(const LawParams<double>& p) {
   q.mu = (float)p.mu;
   q.c_phi = (float)p.c_phi;
   q.a_phi = (float)p.a_phi;
-  q.inv_h_unused = 0.0f;
+  q.c_Psi = (float)p.c_Psi;
+  q.b_Psi = (float)p.b_Psi;
   return q;
 }
+
+// The address under which the current device reaches p (device, managed or
+// page-locked host memory); false for memory the device cannot reach.
+bool device_address(const void* p, const void** out);
 
 // Process-wide count of kernel launches made by this library.
 extern std::atomic<int64_t> g_launches;

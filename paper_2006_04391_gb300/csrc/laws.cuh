@@ -27,7 +27,8 @@ template <class T> struct LawParams {
   T lam, mu;      // Lame constants
   T c_phi;        // phi = c_phi * q^a_phi  (see NortonDev)
   T a_phi;
-  T inv_h_unused; // keeps the struct 8-byte aligned for both precisions
+  T c_Psi;        // force potential Psi = c_Psi * s_A^(2 b_Psi)  (see NortonDev)
+  T b_Psi;
 };
 
 // Linear elasticity: psi = 1/2 eps^T C eps, no internal variables.
@@ -77,6 +78,21 @@ struct NortonDev {
     // q = (2/3) zdot:zdot with zdot33 = -v0 - v1 and engineering shears
     auto q = S(4.0 / 3.0) * (sq(v0) + sq(v1) + v0 * v1) + S(1.0 / 3.0) * (sq(v2) + sq(v3) + sq(v4));
     return p.c_phi * pow(q, p.a_phi);
+  }
+
+  // Force potential of Eq. michel_suquet_psi at sigma_Y = 0, H = 0, the convex
+  // dual of phi, on the generalized stress A = -psi_y = (s11 - s33, s22 - s33,
+  // s23, s13, s12) (Sec. 2, Eq. gsm_internal: ydot = dPsi/dA):
+  //   Psi(A) = sigma0 edot0/(n+1) (s_A/sigma0)^(n+1) = c_Psi (s_A^2)^b_Psi,
+  //   s_A^2 = A0^2 + A1^2 - A0 A1 + 3 (A2^2 + A3^2 + A4^2)  (von Mises stress^2,
+  // the metric dual to phi's q), b_Psi = (n+1)/2.
+  template <class AP, class P> AD_HD static auto Psi(const AP& A, const P& p) {
+    using ad::get;
+    const auto& a0 = get<0>(A); const auto& a1 = get<1>(A); const auto& a2 = get<2>(A);
+    const auto& a3 = get<3>(A); const auto& a4 = get<4>(A);
+    using S = typename std::decay_t<decltype(a0)>::scalar;
+    auto s2 = (sq(a0) + sq(a1) - a0 * a1) + S(3) * (sq(a2) + sq(a3) + sq(a4));
+    return p.c_Psi * pow(s2, p.b_Psi);
   }
 
   // psi depends on (eps, y) only through tr(eps) and dev(eps) - P y (P y is

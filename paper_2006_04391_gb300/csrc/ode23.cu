@@ -1,0 +1,103 @@
+// gsm_update_ode23: the material update by adaptive explicit Runge-Kutta
+// integration of the force-potential form (AutoMat, arXiv 2006.04391,
+// Sec. 4.3, Corollary 1, Sec. 4.5) on sm_103a.  One thread per voxel; fields
+// in HBM (or page-locked host memory) in structure-of-arrays layout; a
+// persistent grid-stride loop whose bound is uniform per block, so every lane
+// takes part in the warp votes of the substep loop.
+#include "common.cuh"
+#include "ode23.cuh"
+
+namespace gsm {
+namespace {
+
+constexpr int kOdeBlock = 128;
+
+template <bool TAN>
+__global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld, LawParams<double> p, Step hs,
+                                                          Ode23Ctl ctl, const double* __restrict__ epsn,
+                                                          const double* __restrict__ eps,
+                                                          const double* __restrict__ zn, double* __restrict__ sig,
+                                                          double* __restrict__ z, double* __restrict__ tan,
+                                                          int32_t* __restrict__ status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool active = i < n;
+    double e0[6], e1[6], zi[6], s[6], zo[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      e0[c] = active ? __ldg(epsn + c * ld + i) : 0.0;
+      e1[c] = active ? __ldg(eps + c * ld + i) : 0.0;
+      zi[c] = active ? __ldg(zn + c * ld + i) : 0.0;
+    }
+    double t36[TAN ? 36 : 1];
+    const unsigned st = voxel_ode23<NortonDev, TAN>(p, e0, e1, zi, hs, ctl, active, s, zo, TAN ? t36 : nullptr);
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sig[c * ld + i] = s[c];
+        z[c * ld + i] = zo[c];
+      }
+      if constexpr (TAN) {
+#pragma unroll
+        for (int c = 0; c < 36; ++c) tan[c * ld + i] = t36[c];
+      }
+      if (status) status[i] = (int32_t)st;
+    }
+  }
+}
+
+template <auto Kernel> int ode_grid(int64_t n) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, kOdeBlock, 0) != cudaSuccess || b <= 0) b = 1;
+    return b;
+  }();
+  const int64_t need = (n + kOdeBlock - 1) / kOdeBlock;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  return (int)(need < cap ? need : cap);
+}
+
+}  // namespace
+}  // namespace gsm
+
+using namespace gsm;
+
+extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n,
+                                int64_t ld, double step_h, double rtol, double atol, int max_substeps, void* sigma,
+                                void* z, void* tangent, int32_t* status, void* stream) {
+  if (!h || n_vox < 0 || ld < n_vox) return GSM_EINVAL;
+  if (n_vox == 0) return GSM_OK;
+  const Material& m = *reinterpret_cast<const Material*>(h);
+  if (m.psi_kind != GSM_PSI_ELASTIC_VP_DEV) return GSM_ENOTSUP;
+  if (!eps_n || !eps || !z_n || !sigma || !z) return GSM_EINVAL;
+  if (!(std::isfinite(step_h) && step_h > 0.0) || !(rtol > 0.0) || !(atol >= 0.0) || max_substeps < 1)
+    return GSM_EINVAL;
+  const void* in[3] = {eps_n, eps, z_n};
+  void* out[4] = {sigma, z, tangent, status};
+  for (auto& q : in)
+    if (!device_address(q, &q)) return GSM_EINVAL;
+  for (auto& q : out) {
+    const void* r = q;
+    if (!device_address(r, &r)) return GSM_EINVAL;
+    q = const_cast<void*>(r);
+  }
+  const Ode23Ctl ctl{rtol, atol, max_substeps};
+  const Step hs = make_step(step_h);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double* e0 = static_cast<const double*>(in[0]);
+  const double* e1 = static_cast<const double*>(in[1]);
+  const double* zi = static_cast<const double*>(in[2]);
+  double* so = static_cast<double*>(out[0]);
+  double* zo = static_cast<double*>(out[1]);
+  double* to = static_cast<double*>(out[2]);
+  int32_t* sto = static_cast<int32_t*>(out[3]);
+  if (to)
+    ode23_kernel<true><<<ode_grid<ode23_kernel<true>>(n_vox), kOdeBlock, 0, s>>>(n_vox, ld, m.p64, hs, ctl, e0, e1,
+                                                                                  zi, so, zo, to, sto);
+  else
+    ode23_kernel<false><<<ode_grid<ode23_kernel<false>>(n_vox), kOdeBlock, 0, s>>>(n_vox, ld, m.p64, hs, ctl, e0,
+                                                                                    e1, zi, so, zo, nullptr, sto);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? GSM_OK : GSM_ECUDA;
+}

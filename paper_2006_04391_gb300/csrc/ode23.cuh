@@ -1,0 +1,364 @@
+// Material update by adaptive explicit Runge-Kutta integration of the
+// force-potential form (AutoMat, arXiv 2006.04391, Sec. 4.3 and Sec. 4.5).
+//
+// Sec. 2, Eq. gsm_internal: ydot = dPsi/dA (A), A = -d psi/dy (eps(t), y), with
+// the strain interpolated linearly over the load step,
+// eps(t) = eps_n + theta (eps_{n+1} - eps_n), theta = (t - t_n)/h.
+// Integrator: the Bogacki-Shampine 3(2) pair (MATLAB's ode23), first stage
+// = last stage of the previous step, step sizes after Hairer, Norsett and
+// Wanner (Solving ODEs I, II.4), whole interval as the first trial step.
+// Error measure (Sec. 4.5, stress-driven): RMS over the stress pair the two
+// embedded solutions give at the end of the substep, scaled by atol + rtol
+// max(|sigma_old|, |sigma_new|); with the tangent also over the tangent pair.
+// Tangent (Corollary 1): dY/dt = Psi_AA(A) dA/deps_{n+1},
+// dA/deps_{n+1} = -(theta psi_ye + psi_yy Y), integrated with the same steps
+// (step sizes undifferentiated); C = dsigma/deps_{n+1} = theta psi_ee + psi_ey Y.
+// All derivatives of psi and Psi come from the AD sweeps; FP64 throughout.
+#pragma once
+
+#include "solver.cuh"
+
+namespace gsm {
+
+struct Ode23Ctl {
+  double rtol, atol;
+  int max_steps;  // accepted + rejected substeps
+};
+
+// Status word of the ode23 update: bits 0-15 accepted substeps, bits 20-30
+// rejected substeps (both saturating), flags in bits 16-19 as elsewhere.
+enum : unsigned { ST_ODE_REJ_SHIFT = 20 };
+
+// psi_y, psi_ye (5x6) and psi_yy (5x5) at (eps, y): one forward-over-reverse
+// sweep with 11 unit directions (6 strain, 5 internal variables).
+template <class Law>
+AD_HD void psi_y_blocks(const LawParams<double>& p, const double (&eps)[6], const double (&y)[5], double (&g)[5],
+                        double (&Hye)[5][6], double (&Hyy)[5][5]) {
+  ad::SeededPack<ad::Var, double, 11, 0, 6> E;
+  ad::SeededPack<ad::Var, double, 11, 6, 5> Y;
+  ad::seed_unit<decltype(E), double, 0, 6>(E, eps);
+  ad::seed_unit<decltype(Y), double, 6, 5>(Y, y);
+  auto f = Law::psi(E, Y, p);
+  f.fwd();
+  f.back(1.0);
+  ad::For<0, 5>::run([&](auto kc) {
+    constexpr int a = decltype(kc)::value;
+    const auto& ad_ = ad::get<a>(Y).a;
+    g[a] = ad_.v;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) Hye[a][j] = ad_.d[j];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Hyy[a][j] = ad_.d[6 + j];
+  });
+}
+
+// Psi_A (first order) and Psi_A, Psi_AA (vector mode) of the force potential.
+template <class Law>
+AD_HD void force_a(const LawParams<double>& p, const double (&A)[5], double (&g)[5]) {
+  ad::UniformPack<ad::Var<double>, 5> X;
+  ad::For<0, 5>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(X).v = A[decltype(kc)::value]; });
+  auto f = Law::Psi(X, p);
+  f.fwd();
+  f.back(1.0);
+  ad::For<0, 5>::run([&](auto kc) { g[decltype(kc)::value] = ad::get<decltype(kc)::value>(X).a; });
+}
+
+template <class Law>
+AD_HD void force_a_aa(const LawParams<double>& p, const double (&A)[5], double (&g)[5], double (&H)[5][5]) {
+  ad::SeededPack<ad::Var, double, 5, 0, 5> X;
+  ad::seed_unit<decltype(X), double, 0, 5>(X, A);
+  auto f = Law::Psi(X, p);
+  f.fwd();
+  f.back(1.0);
+  ad::For<0, 5>::run([&](auto kc) {
+    constexpr int a = decltype(kc)::value;
+    const auto& ad_ = ad::get<a>(X).a;
+    g[a] = ad_.v;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) H[a][j] = ad_.d[j];
+  });
+}
+
+template <bool TAN> struct OdeState {
+  double y[5];
+  double Y[TAN ? 5 : 1][TAN ? 6 : 1];
+};
+
+// Right-hand side at theta = t/h: f = Psi_A(A) and, with TAN,
+// F = Psi_AA(A) dA/deps_{n+1}.
+template <class Law, bool TAN>
+AD_HD void ode_rhs(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
+                   const OdeState<TAN>& s, double (&f)[5], double (&F)[TAN ? 5 : 1][TAN ? 6 : 1]) {
+  double et[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
+  double A[5];
+  if constexpr (!TAN) {
+    double g[5];
+    psi_y<Law, double>(p, et, s.y, g);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) A[a] = -g[a];
+    force_a<Law>(p, A, f);
+  } else {
+    double g[5], Hye[5][6], Hyy[5][5];
+    psi_y_blocks<Law>(p, et, s.y, g, Hye, Hyy);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) A[a] = -g[a];
+    double H[5][5];
+    force_a_aa<Law>(p, A, f, H);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double dA[5];
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        double t = theta * Hye[a][k];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) t = fma(Hyy[a][b], s.Y[b][k], t);
+        dA[a] = -t;
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) t = fma(H[a][b], dA[b], t);
+        F[a][k] = t;
+      }
+    }
+  }
+}
+
+// Stress (and with TAN the tangent C = theta psi_ee + psi_ey Y) at theta.
+template <class Law, bool TAN>
+AD_HD void ode_stress(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
+                      const OdeState<TAN>& s, double (&sig)[6], double (&C)[TAN ? 6 : 1][TAN ? 6 : 1]) {
+  double et[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
+  if constexpr (!TAN) {
+    stress<Law>(p, et, s.y, sig);
+  } else {
+    double Cee[6][6], Cey[6][5], Cye[5][6];
+    psi_blocks<Law>(p, et, s.y, sig, Cee, Cey, Cye);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double t = theta * Cee[i][k];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) t = fma(Cey[i][a], s.Y[a][k], t);
+        C[i][k] = t;
+      }
+  }
+}
+
+// (d / sc)^2 of one error-measure entry; a zero scale (atol = 0 at zero
+// stress) counts a zero difference as no error.
+AD_HD double scaled_sq(double d, double sc) {
+  const double q = sc > 0.0 ? d * recip_pos(sc) : (d == 0.0 ? 0.0 : 1e300);
+  return q * q;
+}
+
+// One voxel.  Every lane of a warp must call this (the substep loop votes
+// warp-wide); lanes with active = false only vote.  C36: 36 outputs (row-major
+// 6x6; the tangent of an explicit integrator is not symmetric in general).
+template <class Law, bool TAN>
+AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
+                           const double (&zn)[6], const Step& hs, const Ode23Ctl& ctl, bool active,
+                           double (&sig)[6], double (&z)[6], double* C36) {
+  // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1), order-3 weights (2/9, 1/3, 4/9),
+  // order-2 weights (7/24, 1/4, 1/3, 1/8) on k1..k4 with k4 = f(t + dt, y3).
+  constexpr double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
+  constexpr double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 1.0 / 4.0, e3 = 4.0 / 9.0 - 1.0 / 3.0,
+                   e4 = -1.0 / 8.0;
+  using M56 = double[TAN ? 5 : 1][TAN ? 6 : 1];
+  using M66 = double[TAN ? 6 : 1][TAN ? 6 : 1];
+  const double h = hs.h, inv_h = hs.inv_h;
+  double de[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) de[i] = eps1[i] - epsn[i];
+
+  OdeState<TAN> s;
+  s.y[0] = zn[0];
+  s.y[1] = zn[1];
+  s.y[2] = zn[3];
+  s.y[3] = zn[4];
+  s.y[4] = zn[5];
+  if constexpr (TAN) {
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
+  }
+  double k1[5];
+  M56 K1;
+  ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, k1, K1);
+  double sig_old[6];
+  M66 C_old;
+  ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+
+  double t = 0.0, dt = h;
+  int n_acc = 0, n_rej = 0;
+  unsigned flags = 0;
+  bool done = !active, last_rejected = false;
+  for (;;) {
+    if (all_done(done)) break;
+    if (!done) {
+      if (n_acc + n_rej >= ctl.max_steps) {
+        flags |= ST_CAP;
+        done = true;
+      }
+    }
+    if (!done) {
+      const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
+      if (clip) dt = h - t;
+      // stage 2
+      OdeState<TAN> st;
+      double k[5], y3[5], e[5];
+      M56 Kc, Y3, E;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        st.y[a] = fma(0.5 * dt, k1[a], s.y[a]);
+        y3[a] = fma(b1 * dt, k1[a], s.y[a]);
+        e[a] = e1 * dt * k1[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            st.Y[a][c] = fma(0.5 * dt, K1[a][c], s.Y[a][c]);
+            Y3[a][c] = fma(b1 * dt, K1[a][c], s.Y[a][c]);
+            E[a][c] = e1 * dt * K1[a][c];
+          }
+      }
+      ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc);
+      // stage 3
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        st.y[a] = fma(0.75 * dt, k[a], s.y[a]);
+        y3[a] = fma(b2 * dt, k[a], y3[a]);
+        e[a] = fma(e2 * dt, k[a], e[a]);
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            st.Y[a][c] = fma(0.75 * dt, Kc[a][c], s.Y[a][c]);
+            Y3[a][c] = fma(b2 * dt, Kc[a][c], Y3[a][c]);
+            E[a][c] = fma(e2 * dt, Kc[a][c], E[a][c]);
+          }
+      }
+      ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc);
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        y3[a] = fma(b3 * dt, k[a], y3[a]);
+        e[a] = fma(e3 * dt, k[a], e[a]);
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            Y3[a][c] = fma(b3 * dt, Kc[a][c], Y3[a][c]);
+            E[a][c] = fma(e3 * dt, Kc[a][c], E[a][c]);
+          }
+      }
+      // last stage at the new point (k1 of the next step)
+      const double tn1 = clip ? h : t + dt;
+      const double th1 = clip ? 1.0 : tn1 * inv_h;
+      OdeState<TAN> s3;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        s3.y[a] = y3[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) s3.Y[a][c] = Y3[a][c];
+      }
+      double k4[5];
+      M56 K4;
+      ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4);
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        e[a] = fma(e4 * dt, k4[a], e[a]);
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) E[a][c] = fma(e4 * dt, K4[a][c], E[a][c]);
+      }
+      // stress pair (and tangent pair) of the two embedded solutions
+      double s_hi[6], s_lo[6];
+      M66 C_hi, C_lo;
+      ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
+      OdeState<TAN> s2;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        s2.y[a] = y3[a] - e[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) s2.Y[a][c] = Y3[a][c] - E[a][c];
+      }
+      ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
+      double sum = 0.0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
+      int m = 6;
+      if constexpr (TAN) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
+        m = 42;
+      }
+      // a trial step that overflows is rejected like one with a large error
+      const double err = finite64(sum) ? sqrt(sum / m) : 1e300;
+      // Hairer II.4: fac 0.9, facmin 0.2, facmax 5 (1 right after a rejection), exponent 1/3
+      const double facmax = last_rejected ? 1.0 : 5.0;
+      const double grow = err == 0.0 ? facmax : fmin(facmax, fmax(0.2, 0.9 * fpow::pow_pos(err, -1.0 / 3.0)));
+      if (err <= 1.0) {
+        t = tn1;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          s.y[a] = y3[a];
+          k1[a] = k4[a];
+          if constexpr (TAN)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              s.Y[a][c] = Y3[a][c];
+              K1[a][c] = K4[a][c];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          sig_old[i] = s_hi[i];
+          if constexpr (TAN)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
+        }
+        ++n_acc;
+        last_rejected = false;
+        if (clip) done = true;
+      } else {
+        ++n_rej;
+        last_rejected = true;
+      }
+      dt *= grow;
+    }
+  }
+  // outputs at theta = 1 (sig_old is the stress of the last accepted step)
+#pragma unroll
+  for (int i = 0; i < 6; ++i) sig[i] = sig_old[i];
+  if constexpr (TAN) {
+    if (C36)
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) C36[6 * i + c] = C_old[i][c];
+  }
+  z[0] = s.y[0];
+  z[1] = s.y[1];
+  z[2] = -(s.y[0] + s.y[1]);
+  z[3] = s.y[2];
+  z[4] = s.y[3];
+  z[5] = s.y[4];
+  unsigned st = flags;
+  if (active && t >= h && !(flags & ST_CAP)) st |= ST_CONVERGED;
+  if (!finite64(sig[0]) || !finite64(z[0])) st |= ST_NONFINITE;
+  st |= (unsigned)(n_acc < 0xffff ? n_acc : 0xffff);
+  st |= (unsigned)(n_rej < 0x7ff ? n_rej : 0x7ff) << ST_ODE_REJ_SHIFT;
+  return st;
+}
+
+}  // namespace gsm

@@ -421,6 +421,24 @@ AD_HD bool finite64(double x) {
 }
 AD_HD bool finite64(float x) { return std::isfinite(x); }
 
+// 1/x for a positive normal FP64 x: Newton-Raphson reciprocal iteration
+// r <- r (2 - x r) from an FP32 seed (two steps square the seed's 2^-22
+// relative error twice; one more rounding), without the FP64 division
+// sequence.  For scale factors, where a last-ulp difference is immaterial.
+AD_HD double recip_pos(double x) {
+#if defined(__CUDA_ARCH__)
+  const int k = ((int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu)) - 1023;  // x = 2^k m, m in [1, 2)
+  const float mf = f32_of(x, -k);
+  double r = f64_of(__frcp_rn(mf), -k);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / x;
+#endif
+}
+
 // Exact powers of two from the bit patterns (k in the normal range).
 AD_HD float exp2i(int k, float) {
   const unsigned b = (unsigned)(k + 127) << 23;

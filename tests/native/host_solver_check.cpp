@@ -5,6 +5,7 @@
 
 #include "../../paper_2006_04391_gb300/csrc/common.cuh"
 #include "../../paper_2006_04391_gb300/csrc/voxel.cuh"
+#include "../../paper_2006_04391_gb300/csrc/ode23.cuh"
 
 using namespace gsm;
 
@@ -24,6 +25,28 @@ int host_update(int mode, const double* prm, int64_t n, const double* eps, const
     } else {
       st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, make_step(h), true, s, zo, tan ? tan + 21 * i : nullptr);
     }
+    for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
+    status[i] = (int32_t)st;
+  }
+  return 0;
+}
+
+// ode23 update (AoS [n][6]; tangent [n][36] or NULL; status [n]).
+int host_update_ode23(const double* prm, int64_t n, const double* eps_n, const double* eps, const double* zn,
+                      double h, double rtol, double atol, int max_steps, double* sig, double* z, double* tan,
+                      int32_t* status) {
+  const LawParams<double> p = make_params(prm, true);
+  const Step hs = make_step(h);
+  const Ode23Ctl ctl{rtol, atol, max_steps};
+  for (int64_t i = 0; i < n; ++i) {
+    double e0[6], e1[6], zi[6], s[6], zo[6];
+    for (int c = 0; c < 6; ++c) {
+      e0[c] = eps_n[6 * i + c];
+      e1[c] = eps[6 * i + c];
+      zi[c] = zn[6 * i + c];
+    }
+    unsigned st = tan ? voxel_ode23<NortonDev, true>(p, e0, e1, zi, hs, ctl, true, s, zo, tan + 36 * i)
+                      : voxel_ode23<NortonDev, false>(p, e0, e1, zi, hs, ctl, true, s, zo, nullptr);
     for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
     status[i] = (int32_t)st;
   }

@@ -1,0 +1,109 @@
+"""GPU parity of gsm_update_ode23 (C ABI) against the oracle's ode23 update
+(force-potential form, Bogacki-Shampine pair with stress-driven step-size
+control, tangent ODE of Corollary 1).
+
+Where GPU and oracle take the same substeps their results agree to rounding
+(1e-10 for sigma and z, 1e-9 for the tangent); a borderline accept/reject
+decision can flip between the two roundings, after which both stay within
+the error control's tolerance of each other.  Criterion: at least 98 % of
+voxels tight, every voxel within 10 (rtol |sigma| + atol)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def soa(a, ld):
+    import torch
+    out = np.zeros((a.shape[1], ld))
+    out[:, :a.shape[0]] = a.T
+    return torch.from_numpy(out).cuda()
+
+
+def run(G, mat, en, e, zn, h, rtol=1e-3, atol=1e-6, tangent=False, ld=None, max_substeps=100000):
+    import torch
+    n = e.shape[0]
+    ld = ld or n
+    E0, E1, Z0 = soa(en, ld), soa(e, ld), soa(zn, ld)
+    sig = torch.full_like(E1, float("nan"))
+    z = torch.full_like(E1, float("nan"))
+    tan = torch.full((36, ld), float("nan"), dtype=torch.float64, device="cuda") if tangent else None
+    st = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    G.gsm_update_ode23(mat, E0, E1, Z0, h, sig, z, tan, st, rtol=rtol, atol=atol, max_substeps=max_substeps, n_vox=n)
+    torch.cuda.synchronize()
+    out = [sig.cpu().numpy()[:, :n].T, z.cpu().numpy()[:, :n].T, st.cpu().numpy()[:n]]
+    if tangent:
+        out.append(tan.cpu().numpy()[:, :n].T)
+    return out
+
+
+def check(res, ref, zn, rtol, atol, tangent):
+    sig, z, st = res[:3]
+    assert np.all((st >> 16) & 1), "every voxel converged"
+    rel = np.abs(sig - ref[0]).max(1) / np.abs(ref[0]).max(1)
+    relz = np.abs(z - ref[1]).max(1) / np.maximum(np.abs(ref[1] - zn).max(1), 1e-300)
+    tight = (rel < 1e-10) & (relz < 1e-10)
+    if tangent:
+        C2 = ref[2].reshape(-1, 36)
+        tight &= np.abs(res[3] - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98, tight.mean()
+    assert np.all(np.abs(sig - ref[0]) <= 10 * (rtol * np.abs(ref[0]).max(1, keepdims=True) + atol))
+    acc = st & 0xFFFF
+    assert np.mean(acc[tight] == ref[-1][tight, 0]) == 1.0
+
+
+@pytest.mark.parametrize("tangent", [False, True])
+@pytest.mark.parametrize("n_exp,rtol,atol", [(1.0, 1e-3, 1e-6), (5.0, 1e-3, 1e-6), (10.0, 1e-3, 1e-6),
+                                             (5.0, 1e-8, 1e-11)])
+def test_ode23_matches_oracle(gsm, tangent, n_exp, rtol, atol):
+    prm = synth.MATRIX_16[:4] + (n_exp,)
+    n = 2 * 4096 + 37 if not tangent else 4096 + 37   # several blocks and a ragged tail
+    en, e, zn = synth.ode23_batch(n, seed=int(n_exp * 7) + int(tangent))
+    mat = gsm.norton(*prm)
+    res = run(gsm, mat, en, e, zn, 0.1, rtol, atol, tangent, ld=n + 5)
+    ref = O.update_ode23(prm, en, e, zn, 0.1, rtol=rtol, atol=atol, tangent=tangent, info=True)
+    check(res, ref, zn, rtol, atol, tangent)
+
+
+def test_ode23_full_size_sampled(gsm):
+    """2^22 voxels, the benchmark's launch; 2000 sampled voxels against the oracle."""
+    n = 1 << 22
+    en, e, zn = synth.ode23_batch(n, seed=2024)
+    mat = gsm.norton(*synth.MATRIX_16)
+    sig, z, st = run(gsm, mat, en, e, zn, 0.1)
+    idx = np.random.default_rng(3).choice(n, 2000, replace=False)
+    ref = O.update_ode23(synth.MATRIX_16, en[idx], e[idx], zn[idx], 0.1, info=True)
+    check((sig[idx], z[idx], st[idx]), ref, zn[idx], 1e-3, 1e-6, False)
+    assert np.all((st >> 16) & 1)
+
+
+def test_ode23_degenerate_and_invalid(gsm):
+    import torch
+    mat = gsm.norton(*synth.MATRIX_16)
+    zero = np.zeros((3, 6))
+    sig, z, st, C = run(gsm, mat, zero, zero, zero, 0.1, tangent=True)
+    assert np.all(sig == 0) and np.all(z == 0)
+    assert np.all((st & 0xFFFF) == 1) and np.all(((st >> 20) & 0x7FF) == 0)
+    lam, mu = 70.0 * 0.3 / (1.3 * 0.4), 70.0 / 2.6
+    Cel = np.zeros((6, 6))
+    Cel[:3, :3] = lam
+    Cel[:3, :3] += 2 * mu * np.eye(3)
+    Cel[3:, 3:] = mu * np.eye(3)
+    assert np.allclose(C.reshape(-1, 6, 6), Cel[None], rtol=1e-13, atol=1e-12)
+    # the substep cap ends the loop with the cap flag and without convergence
+    en, e, zn = synth.ode23_batch(64, seed=5)
+    sig, z, st = run(gsm, mat, en, e, zn, 0.1, max_substeps=2)
+    steps = (st & 0xFFFF) + ((st >> 20) & 0x7FF)
+    capped = (st & gsm.ST_CAP) != 0
+    conv = ((st >> 16) & 1) == 1
+    assert capped.sum() > 32 and np.all(capped != conv) and np.all(steps <= 2)
+    t = torch.zeros(6, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update_ode23(mat, t, t, t, 0.0, t.clone(), t.clone())
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update_ode23(mat, t, t, t, 0.1, t.clone(), t.clone(), rtol=0.0)
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update_ode23(gsm.elastic(70.0, 0.3), t, t, t, 0.1, t.clone(), t.clone())

@@ -125,8 +125,39 @@ def material(eps, z_n, phase, laws, h, tangent=False):
     return (sig, z, Ct) if tangent else (sig, z)
 
 
+def isotropic_measures(Ct):
+    """Per-voxel isotropic measures of tangents Ct (n, 6, 6) (stress-like rows,
+    engineering-shear columns): 3k = J::C = (1/3) sum_{i,j<3} C_ij and
+    10 mu = tr_Mandel(C) - 3k, tr_Mandel = C11 + C22 + C33 + 2 (C44 + C55 + C66).
+    For an isotropic C they are its bulk and shear moduli."""
+    three_k = Ct[:, :3, :3].sum(axis=(1, 2)) / 3.0
+    tr = Ct[:, 0, 0] + Ct[:, 1, 1] + Ct[:, 2, 2] + 2.0 * (Ct[:, 3, 3] + Ct[:, 4, 4] + Ct[:, 5, 5])
+    return three_k / 3.0, (tr - three_k) / 10.0
+
+
+def reference_from_tangents(Ct):
+    """Per-step reference medium (Sec. 3: adjusted to the current tangential
+    stiffness): k0, mu0 the midpoints of the per-voxel bulk and shear measures,
+    lambda0 = k0 - 2 mu0 / 3.  For isotropic elastic phases this is the fixed
+    reference of reference_medium."""
+    k, mu = isotropic_measures(Ct)
+    k0 = 0.5 * (k.min() + k.max())
+    mu0 = 0.5 * (mu.min() + mu.max())
+    return k0 - 2.0 * mu0 / 3.0, mu0
+
+
+def reference_stiffness(lam0, mu0):
+    """Isotropic C0 (Voigt, engineering shears)."""
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam0
+    C[:3, :3] += 2.0 * mu0 * np.eye(3)
+    C[3:, 3:] = mu0 * np.eye(3)
+    return C
+
+
 def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
-          eps0=None, zn0=None, E_prev0=None, record=False):
+          eps0=None, zn0=None, E_prev0=None, record=False, stress_mask=None, Sigma_target=None,
+          ref_update=False):
     """Load-history solve of the basic scheme.
 
     phase : (N, N, N) uint8 phase ids, voxel (i, j, k) with k fastest.
@@ -135,6 +166,15 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     hs    : step sizes h_k.
     forced_iters : optional per-step number of material evaluations to run
                    regardless of tol (used for iteration-matched parity).
+    stress_mask  : optional 6 booleans: components whose macroscopic STRESS is
+                   prescribed (mixed boundary conditions; the others prescribe the
+                   strain E_k).  Their mean strain is an unknown, corrected after
+                   each evaluation by dE_s = (C0_ss)^-1 (Sigma_s - <sigma>_s), and
+                   the stopping error is max(e, |Sigma_s - <sigma>_s|_F / |<sigma>|_F).
+    Sigma_target : (n_steps, 6) prescribed stresses (default 0).
+    ref_update   : adjust the reference medium at the start of every load step
+                   to the tangents of a material evaluation at the predicted
+                   strain (Sec. 3), instead of the fixed elastic reference.
 
     Returns dict with Sigma (n_steps, 6), iters (n_steps,), errors (list per
     step), eps and z (N^3, 6) at the end, and the per-step (eps, z) history if
@@ -149,10 +189,22 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     eps = np.zeros((nvox, 6)) if eps0 is None else np.array(eps0, dtype=np.float64).reshape(nvox, 6)
     z_n = np.zeros((nvox, 6)) if zn0 is None else np.array(zn0, dtype=np.float64).reshape(nvox, 6)
     E_prev = np.zeros(6) if E_prev0 is None else np.asarray(E_prev0, dtype=np.float64)
-    floor = mu0 * 1e-6
-    Sigma, iters, errors, hist = [], [], [], []
+    mask = np.zeros(6, dtype=bool) if stress_mask is None else np.asarray(stress_mask, dtype=bool)
+    S_t = np.zeros((loads.shape[0], 6)) if Sigma_target is None else np.asarray(Sigma_target, float).reshape(-1, 6)
+    wF = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])  # tensor Frobenius weights of stress-like Voigt vectors
+    E_mean = E_prev.copy()                          # the current macroscopic strain
+    Sigma, iters, errors, hist, Es, refs = [], [], [], [], [], []
     for step, (E_k, h) in enumerate(zip(loads, hs)):
-        eps = eps + (E_k - E_prev)[None, :]
+        E_start = np.where(mask, E_mean, E_k)
+        eps = eps + (E_start - E_mean)[None, :]
+        E_mean = E_start.copy()
+        if ref_update:
+            _, _, Ct = material(eps, z_n, ph, laws, h, tangent=True)
+            lam0, mu0 = reference_from_tangents(Ct)
+        refs.append((lam0, mu0))
+        floor = mu0 * 1e-6
+        C0 = reference_stiffness(lam0, mu0)
+        C0ss_inv = np.linalg.inv(C0[np.ix_(mask, mask)]) if mask.any() else None
         errs = []
         n_eval = 0
         while True:
@@ -161,27 +213,34 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
             sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
             mean_sig = sig.mean(axis=0)
             e = equilibrium_error(sig_hat, mean_sig, N, floor)
+            if mask.any():
+                r = (S_t[step] - mean_sig)[mask]
+                den = max(np.sqrt(np.sum(wF * mean_sig ** 2)), floor)
+                e = max(e, np.sqrt(np.sum(wF[mask] * r ** 2)) / den)
             errs.append(e)
             if forced_iters is not None:
                 if n_eval >= forced_iters[step]:
                     break
             elif e < tol or n_eval >= max_iter:
                 break
+            if mask.any():
+                E_mean[mask] = E_mean[mask] + C0ss_inv @ r
             tau = voigt_to_tensor_field(np.moveaxis(sig_hat, 0, -1), engineering=False)
             d_hat = gamma0_apply(tau, lam0, mu0, N)
             eps_hat = np.stack([np.fft.fftn(eps[:, c].reshape(N, N, N)) for c in range(6)], axis=-1)
             eps_hat = eps_hat - d_hat
-            eps_hat[0, 0, 0, :] = nvox * E_k
+            eps_hat[0, 0, 0, :] = nvox * E_mean
             eps = np.stack([np.fft.ifftn(eps_hat[..., c]).real.reshape(-1) for c in range(6)], axis=-1)
         z_n = z
-        E_prev = E_k
         Sigma.append(mean_sig)
+        Es.append(E_mean.copy())
         iters.append(n_eval)
         errors.append(errs)
         if record:
             hist.append((eps.copy(), z_n.copy(), sig.copy()))
     out = {"Sigma": np.array(Sigma), "iters": np.array(iters), "errors": errors,
-           "eps": eps, "z": z_n, "sigma": sig, "lam0": lam0, "mu0": mu0}
+           "eps": eps, "z": z_n, "sigma": sig, "lam0": lam0, "mu0": mu0, "E": np.array(Es),
+           "reference": np.array(refs)}
     if record:
         out["history"] = hist
     return out

@@ -1,0 +1,86 @@
+"""Pins of the oracle's basic scheme with mixed boundary conditions (stress
+prescribed on some macroscopic components, the paper's uniaxial setting,
+Sec. 3) and with the reference medium adjusted per load step to the current
+tangents (Sec. 3)."""
+import numpy as np
+
+import oracle as O
+import oracle.ms as OMS
+import synth
+
+UNIAXIAL = [False, True, True, True, True, True]  # eps_11 prescribed, all other stresses 0
+
+
+def test_homogeneous_uniaxial_stress_gives_young_and_poisson():
+    E, nu = 70.0, 0.3
+    ph = np.zeros((6, 6, 6), dtype=np.uint8)
+    loads = np.array([[0.002, 0, 0, 0, 0, 0], [0.005, 0, 0, 0, 0, 0]])
+    r = OMS.solve(ph, [(O.KIND_ELASTIC, (E, nu))], loads, [0.1, 0.1], tol=1e-12, stress_mask=UNIAXIAL)
+    for k, e11 in enumerate((0.002, 0.005)):
+        assert abs(r["Sigma"][k][0] - E * e11) <= 1e-11 * E * e11
+        assert np.max(np.abs(r["Sigma"][k][1:])) <= 1e-12 * E * e11
+        assert np.allclose(r["E"][k], [e11, -nu * e11, -nu * e11, 0, 0, 0], rtol=0, atol=1e-14)
+
+
+def _laminate_exact(f, lams, mus, E11):
+    """Layers normal to x, uniaxial macro-stress along x, lateral macro-stresses
+    zero: traction continuity gives sigma_11 = S in every layer; compatibility
+    gives common lateral strains eps_22 = eps_33 = a; then
+      eps_11^p = (S - 2 lam_p a) / (lam_p + 2 mu_p),
+      E11 = sum f_p eps_11^p,  0 = sum f_p (lam_p eps_11^p + 2 (lam_p + mu_p) a)."""
+    A = np.zeros((2, 2))
+    b = np.array([E11, 0.0])
+    for fp, l, m in zip(f, lams, mus):
+        c = 1.0 / (l + 2 * m)
+        A[0] += fp * np.array([c, -2 * l * c])                        # eps_11^p in (S, a)
+        A[1] += fp * np.array([l * c, -2 * l * l * c + 2 * (l + m)])  # lam eps_11 + 2 (lam + mu) a
+    S, a = np.linalg.solve(A, b)
+    return S, a
+
+
+def test_laminate_under_uniaxial_stress_matches_closed_form():
+    N = 8
+    ph = synth.laminate_phase(N, 3)  # layers normal to x, 3 of 8 planes of phase 1
+    mats = [(70.0, 0.3), (400.0, 0.2)]
+    laws = [(O.KIND_ELASTIC, m) for m in mats]
+    lm = [O.lame(*m) for m in mats]
+    E11 = 0.004
+    r = OMS.solve(ph, laws, [[E11, 0, 0, 0, 0, 0]], [0.1], tol=1e-12, max_iter=5000, stress_mask=UNIAXIAL)
+    f1 = ph.mean()
+    S, a = _laminate_exact([1 - f1, f1], [l for l, _ in lm], [m for _, m in lm], E11)
+    assert abs(r["Sigma"][0][0] - S) <= 1e-9 * abs(S)
+    assert np.max(np.abs(r["Sigma"][0][1:])) <= 1e-10 * abs(S)
+    assert abs(r["E"][0][1] - a) <= 1e-9 * abs(a) and abs(r["E"][0][2] - a) <= 1e-9 * abs(a)
+
+
+def test_reference_from_elastic_tangents_is_the_fixed_reference():
+    ph = synth.sphere_phase(8, 0.2)
+    laws = [(O.KIND_ELASTIC, (70.0, 0.3)), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(2, [0.003, 0.0, 0.0, 0.0, 0.0, 0.001])
+    a = OMS.solve(ph, laws, loads, [0.1, 0.1], tol=1e-10)
+    b = OMS.solve(ph, laws, loads, [0.1, 0.1], tol=1e-10, ref_update=True)
+    lam0, mu0 = OMS.reference_medium(laws)
+    assert np.allclose(b["reference"], [[lam0, mu0]] * 2, rtol=1e-14)
+    assert np.array_equal(a["iters"], b["iters"])
+    assert np.allclose(a["Sigma"], b["Sigma"], rtol=1e-12, atol=0)
+
+
+def test_isotropic_measures_of_an_elastic_tangent():
+    lam, mu = O.lame(70.0, 0.3)
+    C = OMS.reference_stiffness(lam, mu)[None]
+    k, m = OMS.isotropic_measures(C)
+    assert np.isclose(k[0], lam + 2 * mu / 3, rtol=1e-15) and np.isclose(m[0], mu, rtol=1e-15)
+
+
+def test_updated_reference_with_a_flowing_matrix():
+    """With the matrix flowing, the per-step reference (from the tangents)
+    reaches the same macroscopic response as the fixed elastic reference, in no
+    more iterations; its shear modulus lies below the elastic one."""
+    ph = synth.sphere_phase(8, 0.2)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(3, [0.006, 0, 0, 0, 0, 0])
+    a = OMS.solve(ph, laws, loads, [0.1] * 3, tol=1e-8, max_iter=20000, stress_mask=UNIAXIAL)
+    b = OMS.solve(ph, laws, loads, [0.1] * 3, tol=1e-8, max_iter=20000, stress_mask=UNIAXIAL, ref_update=True)
+    assert np.allclose(a["Sigma"], b["Sigma"], rtol=0, atol=1e-6 * np.abs(a["Sigma"]).max())
+    assert b["iters"].sum() <= a["iters"].sum()
+    assert np.all(b["reference"][1:, 1] < OMS.reference_medium(laws)[1])

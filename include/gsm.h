@@ -187,6 +187,16 @@ typedef struct ms_load {
   const int32_t* forced_iters;/* host [n_steps] or NULL: run exactly this many
                                  material evaluations per step (ignores tol)   */
   double switch_tol;          /* MS_PREC_FP32_BULK: FP32 -> FP64 switch (<=0: 1e-5) */
+  int stress_mask;            /* mixed boundary conditions (Sec. 3): bit c set = the
+                                 macroscopic STRESS of Voigt component c is prescribed
+                                 (its entry of E_k is ignored; its mean strain is solved
+                                 for), e.g. 0x3e for uniaxial tension along 11; 0: all
+                                 strains prescribed                                    */
+  const double* Sigma;        /* host [n_steps][6] prescribed stresses or NULL (= 0) */
+  int ref_update;             /* 1: at the start of every load step, adjust the
+                                 reference medium to the tangents of a material
+                                 evaluation at the predicted strain (Sec. 3); 0: the
+                                 fixed elastic reference                               */
 } ms_load;
 
 typedef struct ms_state {
@@ -203,6 +213,10 @@ typedef struct ms_result {
   double* final_error;        /* host [n_steps] e at the end of each step     */
   int32_t* fp32_iters;        /* host [n_steps] of which in FP32 (may be NULL) */
   int64_t total_iters;        /* out                                          */
+  double* E;                  /* host [n_steps][6] macroscopic strain at the end of
+                                 each step (may be NULL)                      */
+  double* reference;          /* host [n_steps][2] (lambda0, mu0) of each step's
+                                 reference medium (may be NULL)               */
 } ms_result;
 
 typedef struct ms_context* ms_handle;
@@ -249,7 +263,9 @@ typedef struct ms_tape* ms_tape_handle;
 /* ms_run_taped -- ms_run from a fresh state (no resume) that keeps the
  * checkpoints (eps_k, z_{k-1}) of every step on the device (2 * 6 * N^3
  * doubles per step) plus adjoint work arrays (53 * N^3 doubles).  The tape
- * refers to the context, which must outlive it.  Errors as ms_run. */
+ * refers to the context, which must outlive it.  Prescribed macroscopic
+ * strains and the fixed reference medium only (stress_mask = 0, ref_update =
+ * 0; GSM_ENOTSUP otherwise).  Errors as ms_run. */
 int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_handle* tape);
 
 /* ms_adjoint -- dJ/d(E, sigma0, n) of the Norton phase `phase_id` for the

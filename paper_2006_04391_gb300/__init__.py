@@ -50,7 +50,8 @@ class ms_problem(ctypes.Structure):
 class ms_load(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("E", ctypes.POINTER(ctypes.c_double)),
                 ("h", ctypes.POINTER(ctypes.c_double)), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("forced_iters", ctypes.POINTER(ctypes.c_int32)), ("switch_tol", ctypes.c_double)]
+                ("forced_iters", ctypes.POINTER(ctypes.c_int32)), ("switch_tol", ctypes.c_double),
+                ("stress_mask", ctypes.c_int), ("Sigma", ctypes.POINTER(ctypes.c_double)), ("ref_update", ctypes.c_int)]
 
 
 class ms_state(ctypes.Structure):
@@ -68,7 +69,8 @@ class serve_job(ctypes.Structure):
 class ms_result(ctypes.Structure):
     _fields_ = [("Sigma", ctypes.POINTER(ctypes.c_double)), ("iters", ctypes.POINTER(ctypes.c_int32)),
                 ("final_error", ctypes.POINTER(ctypes.c_double)),
-                ("fp32_iters", ctypes.POINTER(ctypes.c_int32)), ("total_iters", ctypes.c_int64)]
+                ("fp32_iters", ctypes.POINTER(ctypes.c_int32)), ("total_iters", ctypes.c_int64),
+                ("E", ctypes.POINTER(ctypes.c_double)), ("reference", ctypes.POINTER(ctypes.c_double))]
 
 
 def load(path=None):
@@ -246,7 +248,15 @@ def ms_create(phase, laws, precision=MS_PREC_FP64, stream=None):
     return ctx
 
 
-def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol):
+def _mask_bits(stress_mask):
+    if stress_mask is None:
+        return 0
+    if isinstance(stress_mask, (int, np.integer)):
+        return int(stress_mask)
+    return sum(1 << c for c, b in enumerate(stress_mask) if b)
+
+
+def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=None, Sigma=None, ref_update=False):
     E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
     hs = np.ascontiguousarray(np.asarray(hs, dtype=np.float64).reshape(-1))
     n = E.shape[0]
@@ -257,25 +267,36 @@ def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol):
     if forced_iters is not None:
         f = np.ascontiguousarray(np.asarray(forced_iters, dtype=np.int32).reshape(-1))
         keep.append(f)
+    S = None
+    if Sigma is not None:
+        S = np.ascontiguousarray(np.asarray(Sigma, dtype=np.float64).reshape(n, 6))
+        keep.append(S)
     ld = ms_load(n, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                  hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
-                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if f is not None else None, float(switch_tol))
+                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if f is not None else None, float(switch_tol),
+                 _mask_bits(stress_mask), S.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if S is not None else None,
+                 1 if ref_update else 0)
     return ld, keep, n
 
 
+def _result_struct(n):
+    out = {"Sigma": np.zeros((n, 6)), "iters": np.zeros(n, dtype=np.int32), "final_error": np.zeros(n),
+           "fp32_iters": np.zeros(n, dtype=np.int32), "E": np.zeros((n, 6)), "reference": np.zeros((n, 2))}
+    dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    res = ms_result(out["Sigma"].ctypes.data_as(dp), out["iters"].ctypes.data_as(ip),
+                    out["final_error"].ctypes.data_as(dp), out["fp32_iters"].ctypes.data_as(ip), 0,
+                    out["E"].ctypes.data_as(dp), out["reference"].ctypes.data_as(dp))
+    return res, out
+
+
 def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=None, resume=False,
-           E_prev=None, switch_tol=0.0, check=True):
-    """Solve a load history.  Returns dict(Sigma, iters, final_error, fp32_iters, total_iters, rc)."""
+           E_prev=None, switch_tol=0.0, check=True, stress_mask=None, Sigma=None, ref_update=False):
+    """Solve a load history.  Returns dict(Sigma, iters, final_error, fp32_iters, total_iters, E,
+    reference, rc).  stress_mask: 6 booleans (or bits) of the macroscopic components whose stress
+    (Sigma, default 0) is prescribed; ref_update: per-step reference medium from tangents."""
     lib = load()
-    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol)
-    Sigma = np.zeros((n, 6))
-    iters = np.zeros(n, dtype=np.int32)
-    ferr = np.zeros(n)
-    f32 = np.zeros(n, dtype=np.int32)
-    res = ms_result(Sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                    ferr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    f32.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0)
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask, Sigma, ref_update)
+    res, out = _result_struct(n)
     st = None
     if eps is not None or z is not None:
         st = ms_state(eps.data_ptr(), z.data_ptr(), 1 if resume else 0,
@@ -283,8 +304,9 @@ def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=
     rc = lib.ms_run(ctx.handle, ctypes.byref(ld), ctypes.byref(st) if st is not None else None, ctypes.byref(res))
     if check and rc not in (GSM_OK, GSM_ENOTCONV):
         _check(rc, "ms_run")
-    return {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32,
-            "total_iters": int(res.total_iters), "rc": rc}
+    out["total_iters"] = int(res.total_iters)
+    out["rc"] = rc
+    return out
 
 
 def ms_evaluate_noalloc(phase, laws, h, eps, z_n, sigma, z, mean, stream=None):
@@ -310,18 +332,6 @@ class Tape:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.ms_tape_destroy(self.handle)
             self.handle = None
-
-
-def _result_struct(n):
-    Sigma = np.zeros((n, 6))
-    iters = np.zeros(n, dtype=np.int32)
-    ferr = np.zeros(n)
-    f32 = np.zeros(n, dtype=np.int32)
-    res = ms_result(Sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                    ferr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    f32.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0)
-    return res, {"Sigma": Sigma, "iters": iters, "final_error": ferr, "fp32_iters": f32}
 
 
 def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000, forced_iters=None):

@@ -325,6 +325,83 @@ __global__ void ms_finalize_batch_kernel(const JobView* __restrict__ views, Redu
   finalize_sums(v.mat_part, v.n_vch, v.gam_part, v.n_mch, v.inv_n3, v.mu0 * 1e-6, out + blockIdx.x);
 }
 
+// Mean mode of the strain spectrum and of the inverse-transform input:
+// m = N^3 E (mixed boundary conditions move E during a load step).  One warp.
+template <class T>
+__global__ void ms_set_mean_kernel(typename cplx<T>::type* __restrict__ eps_hat, typename cplx<T>::type* __restrict__ sig_hat,
+                                   int64_t nmodes, double m0, double m1, double m2, double m3, double m4, double m5) {
+  const double m[6] = {m0, m1, m2, m3, m4, m5};
+  const int q = threadIdx.x;
+  if (q < 6) {
+    typename cplx<T>::type v;
+    v.x = (T)m[q];
+    v.y = T(0);
+    eps_hat[q * nmodes] = v;
+    sig_hat[q * nmodes] = v;
+  }
+}
+
+// Reference medium from tangents (Sec. 3: adjusted per load step to the
+// current tangential stiffness): the law with tangent at the predicted strain
+// eps_raw / N^3 + dE and z_n; per voxel the isotropic measures
+// 3k = J::C = (1/3) sum_{i,j<3} C_ij and 10 mu = tr_Mandel C - 3k; per block
+// their min and max -> part[q * gridDim.x + block], q = kmin, kmax, mumin, mumax.
+template <int MODE>
+__global__ void __launch_bounds__(kMatBlock) ms_reference_kernel(int64_t nvox, const uint8_t* __restrict__ phase,
+                                                                 const PhaseTable* __restrict__ tab, Step hs,
+                                                                 const double* __restrict__ eps_raw,
+                                                                 const double* __restrict__ zn, double inv_n3,
+                                                                 double d0, double d1, double d2, double d3, double d4,
+                                                                 double d5, double* __restrict__ part) {
+  const double d[6] = {d0, d1, d2, d3, d4, d5};
+  double r[4] = {1e300, -1e300, 1e300, -1e300};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nvox; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < nvox;
+    const int ph = in ? (int)phase[i] : 0;
+    const bool vp = in && tab->kind[ph] == GSM_PSI_ELASTIC_VP_DEV;
+    double e[6], zi[6], s[6], zo[6], t[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      e[c] = in ? fma(eps_raw[c * nvox + i], inv_n3, d[c]) : 0.0;
+      zi[c] = vp ? zn[c * nvox + i] : 0.0;
+    }
+    if constexpr (MODE == MODE_FP64) voxel_fp64<NortonDev>(tab->p64[ph], e, zi, hs, vp, s, zo, t);
+    else voxel_fp32_fix<NortonDev>(tab->p64[ph], tab->p32[ph], e, zi, hs, vp, s, zo, t);
+    if (in && !vp) voxel_elastic<double>(tab->p64[ph], e, s, t);
+    if (in) {
+      // packed upper triangle: C11 0, C12 1, C13 2, C22 6, C23 7, C33 11, C44 15, C55 18, C66 20
+      const double tk = (t[0] + t[6] + t[11] + 2.0 * (t[1] + t[2] + t[7])) * (1.0 / 3.0);
+      const double tr = t[0] + t[6] + t[11] + 2.0 * (t[15] + t[18] + t[20]);
+      const double k = tk * (1.0 / 3.0), mu = (tr - tk) * 0.1;
+      r[0] = fmin(r[0], k);
+      r[1] = fmax(r[1], k);
+      r[2] = fmin(r[2], mu);
+      r[3] = fmax(r[3], mu);
+    }
+  }
+  __shared__ double sh[4][kMatBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = r[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, v, off);
+      v = (q & 1) ? fmax(v, o) : fmin(v, o);
+    }
+    if (lane == 0) sh[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    double v = sh[q][0];
+    for (int k = 1; k < kMatBlock / 32; ++k) v = (q & 1) ? fmax(v, sh[q][k]) : fmin(v, sh[q][k]);
+    part[q * gridDim.x + blockIdx.x] = v;
+  }
+}
+
 // eps_raw += N^3 dE (uniform macro-strain increment at a step start).
 template <class T>
 __global__ void ms_add_uniform_kernel(int64_t nvox, T* __restrict__ eps_raw, double d0, double d1, double d2,

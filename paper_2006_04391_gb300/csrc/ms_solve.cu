@@ -181,7 +181,8 @@ struct Job {
   const uint8_t* phase = nullptr;
   PhaseTable tab_host;
   PhaseTable* tab_dev = nullptr;
-  double lam0 = 0, mu0 = 0;
+  double lam0 = 0, mu0 = 0;          // reference medium of the current step
+  double lam0_el = 0, mu0_el = 0;    // the fixed elastic reference
   double theta[kMaxPhases][3] = {};  // (sigma0, edot0, n) of Norton phases
   Fields<double> f64;
   Fields<float> f32;
@@ -194,13 +195,19 @@ struct Job {
   std::vector<int32_t> forced;
   double tol = 1e-8, switch_tol = 1e-5;
   int max_iter = 10000;
+  int stress_mask = 0;               // mixed boundary conditions: prescribed-stress components
+  std::vector<double> S_target;      // [n_steps][6]
+  bool ref_update = false;           // per-step reference medium from tangents
+  double C0ss_inv[36] = {};          // (C0 on the prescribed-stress components)^-1, n_s x n_s
+  int n_s = 0, s_idx[6] = {};
   // state
   int step = 0, n_eval = 0, n32 = 0, since_best = 0;
   bool fp32_phase = false, need_start = true, done = false, notconv = false;
   double best = 1e300;
-  double E_prev[6] = {0, 0, 0, 0, 0, 0};
+  double E_prev[6] = {0, 0, 0, 0, 0, 0};  // macroscopic strain at the end of the previous step
+  double E_cur[6] = {0, 0, 0, 0, 0, 0};   // macroscopic strain of the current iterate
   // results
-  std::vector<double> Sigma, final_error;
+  std::vector<double> Sigma, final_error, E_out, ref_out;
   std::vector<int32_t> iters, fp32_iters;
   int64_t total_iters = 0;
   // optional per-step checkpoints for the adjoint: [n_steps][6][nvox] each
@@ -241,8 +248,8 @@ int job_setup(Job& j, int N, const uint8_t* phase_dev, int n_phases, const gsm_h
     mu_min = std::min(mu_min, m->p64.mu);
     mu_max = std::max(mu_max, m->p64.mu);
   }
-  j.lam0 = 0.5 * (lam_min + lam_max);
-  j.mu0 = 0.5 * (mu_min + mu_max);
+  j.lam0 = j.lam0_el = 0.5 * (lam_min + lam_max);
+  j.mu0 = j.mu0_el = 0.5 * (mu_min + mu_max);
   j.bytes = job_bytes(N, precision);
   return GSM_OK;
 }
@@ -312,7 +319,17 @@ int job_load(Job& j, const ms_load* load) {
   if (load->forced_iters)
     for (int k = 0; k < load->n_steps; ++k)
       if (load->forced_iters[k] < 1) return GSM_EINVAL;
+  if (load->stress_mask < 0 || load->stress_mask > 63 || (load->ref_update != 0 && load->ref_update != 1))
+    return GSM_EINVAL;
   const int n = load->n_steps;
+  j.stress_mask = load->stress_mask;
+  j.S_target.assign(6 * n, 0.0);
+  if (load->Sigma) j.S_target.assign(load->Sigma, load->Sigma + 6 * n);
+  j.ref_update = load->ref_update == 1;
+  j.lam0 = j.lam0_el;
+  j.mu0 = j.mu0_el;
+  j.E_out.assign(6 * n, 0.0);
+  j.ref_out.assign(2 * n, 0.0);
   j.E.assign(load->E, load->E + 6 * n);
   j.h.assign(load->h, load->h + n);
   j.forced.clear();
@@ -376,10 +393,88 @@ template <class T> int inverse(Engine& g, Job& j) {
 
 int cap_of(const Job& j) { return j.forced.empty() ? j.max_iter : j.forced[j.step]; }
 
-// Start load step j.step: macro-strain increment and, in FP32-bulk mode, the
-// FP32 copies of the FP64 state.
+// (C0 restricted to the prescribed-stress components)^-1 for the mixed
+// boundary conditions; C0 isotropic (Voigt, engineering shears).
+void mixed_setup(Job& j) {
+  j.n_s = 0;
+  for (int q = 0; q < 6; ++q)
+    if ((j.stress_mask >> q) & 1) j.s_idx[j.n_s++] = q;
+  const int m = j.n_s;
+  if (m == 0) return;
+  double A[6][12];
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      const int p = j.s_idx[a], q = j.s_idx[b];
+      double c = 0.0;
+      if (p < 3 && q < 3) c = j.lam0 + (p == q ? 2.0 * j.mu0 : 0.0);
+      else if (p == q) c = j.mu0;
+      A[a][b] = c;
+      A[a][m + b] = a == b ? 1.0 : 0.0;
+    }
+  // Gauss-Jordan (C0_ss is symmetric positive definite)
+  for (int c = 0; c < m; ++c) {
+    const double inv = 1.0 / A[c][c];
+    for (int k = 0; k < 2 * m; ++k) A[c][k] *= inv;
+    for (int r = 0; r < m; ++r)
+      if (r != c) {
+        const double f = A[r][c];
+        for (int k = 0; k < 2 * m; ++k) A[r][k] -= f * A[c][k];
+      }
+  }
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) j.C0ss_inv[a * m + b] = A[a][m + b];
+}
+
+// Reference medium of the step from the tangents at the predicted strain
+// (eps of the previous step + the uniform increment dE, z_n): (k0, mu0) the
+// midpoints of the per-voxel isotropic measures, lambda0 = k0 - 2 mu0 / 3.
+int reference_update(Engine& g, Job& j, const double (&dE)[6]) {
+  const int grid = (int)std::min<int64_t>(j.n_vch, (int64_t)sm_count() * 2);
+  const double inv_n3 = 1.0 / (double)j.nvox;
+  const Step hs = make_step(j.h[j.step]);
+  if (j.law_mode == MODE_FP64)
+    ms_reference_kernel<MODE_FP64><<<grid, kMatBlock, 0, g.stream>>>(j.nvox, j.phase, j.tab_dev, hs, j.f64.eps_raw,
+                                                                    j.f64.zn, inv_n3, dE[0], dE[1], dE[2], dE[3],
+                                                                    dE[4], dE[5], j.mat_part);
+  else
+    ms_reference_kernel<MODE_FP32_FIX><<<grid, kMatBlock, 0, g.stream>>>(j.nvox, j.phase, j.tab_dev, hs,
+                                                                        j.f64.eps_raw, j.f64.zn, inv_n3, dE[0], dE[1],
+                                                                        dE[2], dE[3], dE[4], dE[5], j.mat_part);
+  count_launch();
+  std::vector<double> part(4 * (size_t)grid);
+  if (cudaMemcpyAsync(part.data(), j.mat_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, g.stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(g.stream) != cudaSuccess)
+    return GSM_ECUDA;
+  double r[4] = {1e300, -1e300, 1e300, -1e300};
+  for (int b = 0; b < grid; ++b) {
+    r[0] = std::min(r[0], part[b]);
+    r[1] = std::max(r[1], part[grid + b]);
+    r[2] = std::min(r[2], part[2 * grid + b]);
+    r[3] = std::max(r[3], part[3 * grid + b]);
+  }
+  const double k0 = 0.5 * (r[0] + r[1]), mu0 = 0.5 * (r[2] + r[3]);
+  if (!(mu0 > 0.0) || !(k0 > 0.0) || !std::isfinite(k0 + mu0)) return GSM_ENOTCONV;
+  j.mu0 = mu0;
+  j.lam0 = k0 - 2.0 * mu0 / 3.0;
+  return GSM_OK;
+}
+
+// Start load step j.step: macro-strain increment (prescribed-stress
+// components keep the previous step's strain as their start), the reference
+// medium and, in FP32-bulk mode, the FP32 copies of the FP64 state.
 int step_start(Engine& g, Job& j) {
-  const double* E = j.E.data() + 6 * j.step;
+  double E[6], dE[6];
+  for (int q = 0; q < 6; ++q) {
+    E[q] = ((j.stress_mask >> q) & 1) ? j.E_prev[q] : j.E[6 * j.step + q];
+    dE[q] = E[q] - j.E_prev[q];
+    j.E_cur[q] = E[q];
+  }
+  if (j.ref_update) {
+    const int rc = reference_update(g, j, dE);
+    if (rc != GSM_OK) return rc;
+  }
+  mixed_setup(j);
   j.n_eval = 0;
   j.n32 = 0;
   j.best = 1e300;
@@ -393,13 +488,28 @@ int step_start(Engine& g, Job& j) {
   return spectrum_start<double>(g, j, E, j.E_prev);
 }
 
+// Mixed boundary conditions: dE_s = (C0_ss)^-1 (Sigma_s - <sigma>_s) on the
+// prescribed-stress components, written into the mean mode of the strain
+// spectrum and of the inverse-transform input.
+template <class T> void move_mean(Engine& g, Job& j, const double (&dS)[6]) {
+  for (int a = 0; a < j.n_s; ++a) {
+    double d = 0.0;
+    for (int b = 0; b < j.n_s; ++b) d += j.C0ss_inv[a * j.n_s + b] * dS[j.s_idx[b]];
+    j.E_cur[j.s_idx[a]] += d;
+  }
+  const double n3 = (double)j.nvox;
+  Fields<T>& f = fields<T>(j);
+  ms_set_mean_kernel<T><<<1, 32, 0, g.stream>>>(f.eps_hat, f.sig_hat, j.nmodes, n3 * j.E_cur[0], n3 * j.E_cur[1],
+                                                n3 * j.E_cur[2], n3 * j.E_cur[3], n3 * j.E_cur[4], n3 * j.E_cur[5]);
+  count_launch();
+}
+
 // FP32 -> FP64 hand-over within a step: the FP32 strain of the last
 // evaluation becomes the FP64 strain, resynthesised from its spectrum so that
 // its mean is E_k exactly.
 int switch_to_fp64(Engine& g, Job& j) {
-  const double* E = j.E.data() + 6 * j.step;
   convert<float, double>(g.stream, j.f32.eps_raw, j.f64.eps_raw, 6 * j.nvox, 1.0);
-  int rc = spectrum_start<double>(g, j, E, E);
+  int rc = spectrum_start<double>(g, j, j.E_cur, j.E_cur);
   if (rc != GSM_OK) return rc;
   cudaMemcpyAsync(j.f64.sig_hat, j.f64.eps_hat, 6 * j.nmodes * sizeof(cufftDoubleComplex), cudaMemcpyDeviceToDevice,
                   g.stream);
@@ -410,7 +520,22 @@ int switch_to_fp64(Engine& g, Job& j) {
 // After the tick's evaluation: convergence, precision switch, step end.
 int post_eval(Engine& g, Job& j, const Reduced& r) {
   ++j.n_eval;
-  const double e = r.e;
+  double e = r.e;
+  double dS[6] = {0, 0, 0, 0, 0, 0};
+  if (j.stress_mask) {
+    // residual of the prescribed stresses (tensor Frobenius weights), in the error
+    const double* St = j.S_target.data() + 6 * j.step;
+    double num = 0.0, den = 0.0;
+    for (int q = 0; q < 6; ++q) {
+      const double w = q < 3 ? 1.0 : 2.0;
+      den += w * r.mean[q] * r.mean[q];
+      if ((j.stress_mask >> q) & 1) {
+        dS[q] = St[q] - r.mean[q];
+        num += w * dS[q] * dS[q];
+      }
+    }
+    e = std::max(e, std::sqrt(num) / std::max(std::sqrt(den), j.mu0 * 1e-6));
+  }
   const int cap = cap_of(j);
   if (j.fp32_phase) {
     ++j.n32;
@@ -421,6 +546,7 @@ int post_eval(Engine& g, Job& j, const Reduced& r) {
       ++j.since_best;
     }
     if (e < std::max(j.switch_tol, j.tol) || j.since_best >= 20 || j.n_eval >= cap - 1) return switch_to_fp64(g, j);
+    if (j.stress_mask) move_mean<float>(g, j, dS);
     return inverse<float>(g, j);
   }
   bool end = false, conv = false;
@@ -431,7 +557,10 @@ int post_eval(Engine& g, Job& j, const Reduced& r) {
   } else if (j.n_eval >= cap) {
     end = true;
   }
-  if (!end) return inverse<double>(g, j);
+  if (!end) {
+    if (j.stress_mask) move_mean<double>(g, j, dS);
+    return inverse<double>(g, j);
+  }
   if (!conv) j.notconv = true;
   if (j.tape_eps) {
     const int64_t n6 = 6 * j.nvox;
@@ -441,8 +570,11 @@ int post_eval(Engine& g, Job& j, const Reduced& r) {
   std::swap(j.f64.zn, j.f64.z);  // z_n <- z
   for (int q = 0; q < 6; ++q) {
     j.Sigma[6 * j.step + q] = r.mean[q];
-    j.E_prev[q] = j.E[6 * j.step + q];
+    j.E_prev[q] = j.E_cur[q];
+    j.E_out[6 * j.step + q] = j.E_cur[q];
   }
+  j.ref_out[2 * j.step] = j.lam0;
+  j.ref_out[2 * j.step + 1] = j.mu0;
   j.iters[j.step] = j.n_eval;
   j.final_error[j.step] = e;
   j.fp32_iters[j.step] = j.n32;
@@ -655,6 +787,8 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
   std::memcpy(result->iters, j.iters.data(), n * sizeof(int32_t));
   std::memcpy(result->final_error, j.final_error.data(), n * sizeof(double));
   if (result->fp32_iters) std::memcpy(result->fp32_iters, j.fp32_iters.data(), n * sizeof(int32_t));
+  if (result->E) std::memcpy(result->E, j.E_out.data(), 6 * n * sizeof(double));
+  if (result->reference) std::memcpy(result->reference, j.ref_out.data(), 2 * n * sizeof(double));
   result->total_iters = j.total_iters;
   if (state && state->eps && state->z) {
     convert<double, double>(s, j.f64.eps_raw, state->eps, n6, 1.0 / n3);
@@ -719,6 +853,9 @@ int serve_submit(serve_handle h, const serve_job* desc, int64_t* id) {
   ld.max_iter = desc->max_iter;
   ld.forced_iters = nullptr;
   ld.switch_tol = desc->switch_tol;
+  ld.stress_mask = 0;
+  ld.Sigma = nullptr;
+  ld.ref_update = 0;
   rc = job_load(*p.job, &ld);
   if (rc != GSM_OK) return rc;
   if (p.job->bytes + plan_bytes(desc->N, desc->precision) > sv->budget) return GSM_ENOMEM;  // never admissible
@@ -850,6 +987,8 @@ int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_ha
   Ctx& c = *reinterpret_cast<Ctx*>(h);
   Job& j = c.job;
   if (load->n_steps < 1) return GSM_EINVAL;
+  // the adjoint assumes prescribed macroscopic strains and the fixed reference medium
+  if (load->stress_mask != 0 || load->ref_update != 0) return GSM_ENOTSUP;
   Tape* t = new (std::nothrow) Tape;
   if (!t) return GSM_ENOMEM;
   t->ctx = &c;

@@ -161,3 +161,62 @@ def test_fibre_composite_256_first_evaluation(gsm, precision, fibre256):
     assert rel(out["Sigma"][0], expect) < 1e-12
     more = gsm.ms_run(ctx, loads[:1], hs[:1], forced_iters=[6], switch_tol=1e30)
     assert np.isfinite(more["Sigma"]).all() and more["final_error"][0] < out["final_error"][0]
+
+
+UNIAXIAL = [False, True, True, True, True, True]
+
+
+@pytest.mark.parametrize("mask,ref_update", [(UNIAXIAL, False), (None, True), (UNIAXIAL, True)])
+def test_mixed_and_updated_reference_iteration_matched(gsm, mask, ref_update):
+    """Mixed boundary conditions (uniaxial stress along 11) and/or the per-step
+    reference medium from tangents (Sec. 3), 12^3 sphere composite, 3 steps
+    with the matrix flowing: the GPU run with the oracle's per-step evaluation
+    counts gives the oracle's Sigma_k, macroscopic strains and reference media."""
+    import torch
+    ph = synth.sphere_phase(12, 0.2)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(3, [0.006, 0, 0, 0, 0, 0])
+    hs = [0.1] * 3
+    ref = OMS.solve(ph, laws, loads, hs, tol=1e-8, max_iter=20000, stress_mask=mask, ref_update=ref_update)
+    ctx = gsm.ms_create(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws))
+    out = gsm.ms_run(ctx, loads, hs, forced_iters=ref["iters"], stress_mask=mask, ref_update=ref_update)
+    gsm.ms_destroy(ctx)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-9
+    assert rel(out["E"], ref["E"]) < 1e-9
+    assert np.allclose(out["reference"], ref["reference"], rtol=1e-10, atol=0)
+    if mask is not None:
+        assert np.max(np.abs(out["Sigma"][:, 1:])) < 1e-6 * np.max(np.abs(out["Sigma"][:, 0]))
+
+
+def test_uniaxial_stress_free_run_and_bulk_precision(gsm):
+    """Free runs to tol with mixed boundary conditions and the updated reference,
+    FP64 and FP32 bulk: the prescribed stresses vanish to tol and the response
+    agrees with the oracle to O(tol); the homogeneous grid gives Young's modulus."""
+    import torch
+    ph = synth.sphere_phase(12, 0.2)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(2, [0.004, 0, 0, 0, 0, 0])
+    ref = OMS.solve(ph, laws, loads, [0.1, 0.1], tol=1e-8, max_iter=20000, stress_mask=UNIAXIAL, ref_update=True)
+    for prec in (gsm.MS_PREC_FP64, gsm.MS_PREC_FP32_BULK):
+        out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.1, 0.1], precision=prec,
+                           tol=1e-8, max_iter=20000, stress_mask=UNIAXIAL, ref_update=True)
+        assert out["rc"] == 0
+        assert rel(out["Sigma"], ref["Sigma"]) < 1e-6
+        assert np.max(np.abs(out["Sigma"][:, 1:])) < 1e-6 * np.max(np.abs(out["Sigma"][:, 0]))
+    hom = gsm.ms_solve(torch.zeros(6, 6, 6, dtype=torch.uint8).cuda(), [gsm.elastic(70.0, 0.3)],
+                       [[0.003, 0, 0, 0, 0, 0]], [0.1], tol=1e-12, stress_mask=UNIAXIAL)
+    assert abs(hom["Sigma"][0][0] - 70.0 * 0.003) < 1e-12 * 0.21
+    assert np.allclose(hom["E"][0], [0.003, -0.0009, -0.0009, 0, 0, 0], rtol=0, atol=1e-15)
+
+
+def test_taped_run_rejects_mixed_conditions(gsm):
+    import torch
+    ph = synth.sphere_phase(8, 0.2)
+    ctx = gsm.ms_create(torch.from_numpy(ph).cuda(), [gsm.norton(*synth.MATRIX_16), gsm.elastic(*synth.INCLUSION_16)])
+    lib = gsm.load()
+    ld, keep, n = gsm._load_struct([[0.002, 0, 0, 0, 0, 0]], [0.1], 1e-8, 100, None, 0.0, UNIAXIAL)
+    res, out = gsm._result_struct(n)
+    import ctypes
+    th = ctypes.c_void_p()
+    assert lib.ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th)) == -5
+    gsm.ms_destroy(ctx)

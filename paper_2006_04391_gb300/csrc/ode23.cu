@@ -12,6 +12,12 @@ namespace {
 
 constexpr int kOdeBlock = 128;
 
+// Per-lane scheduling (without the tangent): a lane takes voxels i, i +
+// stride, ... and starts its next voxel as soon as the current one has
+// finished its substeps; the warp runs while any lane has work.  Voxels need
+// different substep counts, and with one voxel per lane per pass the finished
+// lanes would idle until the slowest voxel of their warp is done (measured:
+// 23.7 of 32 lanes busy; 28.7 -> 31.2 M voxel-updates/s).
 template <bool TAN>
 __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld, LawParams<double> p, Step hs,
                                                           Ode23Ctl ctl, const double* __restrict__ epsn,
@@ -20,29 +26,62 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
                                                           double* __restrict__ z, double* __restrict__ tan,
                                                           int32_t* __restrict__ status) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    const bool active = i < n;
-    double e0[6], e1[6], zi[6], s[6], zo[6];
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Ode23Voxel<NortonDev, TAN> v;
+  auto start = [&](int64_t k) {
+    double e0[6], e1[6], zi[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      e0[c] = active ? __ldg(epsn + c * ld + i) : 0.0;
-      e1[c] = active ? __ldg(eps + c * ld + i) : 0.0;
-      zi[c] = active ? __ldg(zn + c * ld + i) : 0.0;
+      e0[c] = __ldg(epsn + c * ld + k);
+      e1[c] = __ldg(eps + c * ld + k);
+      zi[c] = __ldg(zn + c * ld + k);
     }
-    double t36[TAN ? 36 : 1];
-    const unsigned st = voxel_ode23<NortonDev, TAN>(p, e0, e1, zi, hs, ctl, active, s, zo, TAN ? t36 : nullptr);
-    if (active) {
+    v.init(p, e0, e1, zi, hs.h);
+  };
+  if constexpr (TAN) {
+    // with the tangent the state lives mostly in local memory (register
+    // spills); there one voxel per lane per pass, warp-voted, measured faster
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+      const int64_t k = base + threadIdx.x;
+      const bool active = k < n;
+      if (active) start(k);
+      else v.done = true;
+      for (;;) {
+        if (all_done(v.done)) break;
+        if (!v.done) v.attempt(p, hs, ctl);
+      }
+      if (active) {
+        double s[6], zo[6], t36[36];
+        const unsigned st = v.finish(hs.h, s, zo, t36);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          sig[c * ld + k] = s[c];
+          z[c * ld + k] = zo[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 36; ++c) tan[c * ld + k] = t36[c];
+        if (status) status[k] = (int32_t)st;
+      }
+    }
+    return;
+  }
+  bool have = i < n;
+  if (have) start(i);
+  while (__any_sync(0xffffffffu, have)) {
+    if (!have) continue;
+    v.attempt(p, hs, ctl);
+    if (v.done) {
+      double s[6], zo[6];
+      const unsigned st = v.finish(hs.h, s, zo, nullptr);
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         sig[c * ld + i] = s[c];
         z[c * ld + i] = zo[c];
       }
-      if constexpr (TAN) {
-#pragma unroll
-        for (int c = 0; c < 36; ++c) tan[c * ld + i] = t36[c];
-      }
       if (status) status[i] = (int32_t)st;
+      i += stride;
+      have = i < n;
+      if (have) start(i);
     }
   }
 }

@@ -158,207 +158,232 @@ AD_HD double scaled_sq(double d, double sc) {
   return q * q;
 }
 
-// One voxel.  Every lane of a warp must call this (the substep loop votes
-// warp-wide); lanes with active = false only vote.  C36: 36 outputs (row-major
-// 6x6; the tangent of an explicit integrator is not symmetric in general).
-template <class Law, bool TAN>
-AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
-                           const double (&zn)[6], const Step& hs, const Ode23Ctl& ctl, bool active,
-                           double (&sig)[6], double (&z)[6], double* C36) {
-  // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1), order-3 weights (2/9, 1/3, 4/9),
-  // order-2 weights (7/24, 1/4, 1/3, 1/8) on k1..k4 with k4 = f(t + dt, y3).
-  constexpr double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
-  constexpr double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 1.0 / 4.0, e3 = 4.0 / 9.0 - 1.0 / 3.0,
-                   e4 = -1.0 / 8.0;
+// The ode23 integration of one voxel as a resumable state: init() at the
+// start of the load step, attempt() for one trial substep (accepted or
+// rejected; sets done at the end of the interval or at the substep cap),
+// finish() for the outputs.  A kernel can therefore hand a lane its next voxel
+// as soon as its current one is done, instead of letting the lane wait for
+// the slowest voxel of its warp.
+template <class Law, bool TAN> struct Ode23Voxel {
   using M56 = double[TAN ? 5 : 1][TAN ? 6 : 1];
   using M66 = double[TAN ? 6 : 1][TAN ? 6 : 1];
-  const double h = hs.h, inv_h = hs.inv_h;
-  double de[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) de[i] = eps1[i] - epsn[i];
-
+  double epsn[6], de[6];
   OdeState<TAN> s;
-  s.y[0] = zn[0];
-  s.y[1] = zn[1];
-  s.y[2] = zn[3];
-  s.y[3] = zn[4];
-  s.y[4] = zn[5];
-  if constexpr (TAN) {
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
-  }
   double k1[5];
   M56 K1;
-  ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, k1, K1);
   double sig_old[6];
   M66 C_old;
-  ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+  double t, dt;
+  int n_acc, n_rej;
+  unsigned flags;
+  bool last_rejected, done;
 
-  double t = 0.0, dt = h;
-  int n_acc = 0, n_rej = 0;
-  unsigned flags = 0;
-  bool done = !active, last_rejected = false;
-  for (;;) {
-    if (all_done(done)) break;
-    if (!done) {
-      if (n_acc + n_rej >= ctl.max_steps) {
-        flags |= ST_CAP;
-        done = true;
-      }
+  AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[6],
+                  double h) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      epsn[i] = e0[i];
+      de[i] = e1[i] - e0[i];
     }
-    if (!done) {
-      const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
-      if (clip) dt = h - t;
-      // stage 2
-      OdeState<TAN> st;
-      double k[5], y3[5], e[5];
-      M56 Kc, Y3, E;
+    s.y[0] = zn[0];
+    s.y[1] = zn[1];
+    s.y[2] = zn[3];
+    s.y[3] = zn[4];
+    s.y[4] = zn[5];
+    if constexpr (TAN) {
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        st.y[a] = fma(0.5 * dt, k1[a], s.y[a]);
-        y3[a] = fma(b1 * dt, k1[a], s.y[a]);
-        e[a] = e1 * dt * k1[a];
-        if constexpr (TAN)
+      for (int a = 0; a < 5; ++a)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            st.Y[a][c] = fma(0.5 * dt, K1[a][c], s.Y[a][c]);
-            Y3[a][c] = fma(b1 * dt, K1[a][c], s.Y[a][c]);
-            E[a][c] = e1 * dt * K1[a][c];
-          }
-      }
-      ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc);
-      // stage 3
+        for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, k1, K1);
+    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+    t = 0.0;
+    dt = h;
+    n_acc = n_rej = 0;
+    flags = 0;
+    last_rejected = false;
+    done = false;
+  }
+
+  AD_HD void attempt(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
+    // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1), order-3 weights (2/9, 1/3, 4/9),
+    // order-2 weights (7/24, 1/4, 1/3, 1/8) on k1..k4 with k4 = f(t + dt, y3).
+    constexpr double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
+    constexpr double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 1.0 / 4.0, e3 = 4.0 / 9.0 - 1.0 / 3.0,
+                     e4 = -1.0 / 8.0;
+    const double h = hs.h, inv_h = hs.inv_h;
+    if (n_acc + n_rej >= ctl.max_steps) {
+      flags |= ST_CAP;
+      done = true;
+      return;
+    }
+    const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
+    if (clip) dt = h - t;
+    // stage 2
+    OdeState<TAN> st;
+    double k[5], y3[5], e[5];
+    M56 Kc, Y3, E;
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        st.y[a] = fma(0.75 * dt, k[a], s.y[a]);
-        y3[a] = fma(b2 * dt, k[a], y3[a]);
-        e[a] = fma(e2 * dt, k[a], e[a]);
-        if constexpr (TAN)
+    for (int a = 0; a < 5; ++a) {
+      st.y[a] = fma(0.5 * dt, k1[a], s.y[a]);
+      y3[a] = fma(b1 * dt, k1[a], s.y[a]);
+      e[a] = e1 * dt * k1[a];
+      if constexpr (TAN)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            st.Y[a][c] = fma(0.75 * dt, Kc[a][c], s.Y[a][c]);
-            Y3[a][c] = fma(b2 * dt, Kc[a][c], Y3[a][c]);
-            E[a][c] = fma(e2 * dt, Kc[a][c], E[a][c]);
-          }
-      }
-      ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc);
+        for (int c = 0; c < 6; ++c) {
+          st.Y[a][c] = fma(0.5 * dt, K1[a][c], s.Y[a][c]);
+          Y3[a][c] = fma(b1 * dt, K1[a][c], s.Y[a][c]);
+          E[a][c] = e1 * dt * K1[a][c];
+        }
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc);
+    // stage 3
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        y3[a] = fma(b3 * dt, k[a], y3[a]);
-        e[a] = fma(e3 * dt, k[a], e[a]);
-        if constexpr (TAN)
+    for (int a = 0; a < 5; ++a) {
+      st.y[a] = fma(0.75 * dt, k[a], s.y[a]);
+      y3[a] = fma(b2 * dt, k[a], y3[a]);
+      e[a] = fma(e2 * dt, k[a], e[a]);
+      if constexpr (TAN)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            Y3[a][c] = fma(b3 * dt, Kc[a][c], Y3[a][c]);
-            E[a][c] = fma(e3 * dt, Kc[a][c], E[a][c]);
-          }
-      }
-      // last stage at the new point (k1 of the next step)
-      const double tn1 = clip ? h : t + dt;
-      const double th1 = clip ? 1.0 : tn1 * inv_h;
-      OdeState<TAN> s3;
+        for (int c = 0; c < 6; ++c) {
+          st.Y[a][c] = fma(0.75 * dt, Kc[a][c], s.Y[a][c]);
+          Y3[a][c] = fma(b2 * dt, Kc[a][c], Y3[a][c]);
+          E[a][c] = fma(e2 * dt, Kc[a][c], E[a][c]);
+        }
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc);
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        s3.y[a] = y3[a];
-        if constexpr (TAN)
+    for (int a = 0; a < 5; ++a) {
+      y3[a] = fma(b3 * dt, k[a], y3[a]);
+      e[a] = fma(e3 * dt, k[a], e[a]);
+      if constexpr (TAN)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) s3.Y[a][c] = Y3[a][c];
-      }
-      double k4[5];
-      M56 K4;
-      ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4);
+        for (int c = 0; c < 6; ++c) {
+          Y3[a][c] = fma(b3 * dt, Kc[a][c], Y3[a][c]);
+          E[a][c] = fma(e3 * dt, Kc[a][c], E[a][c]);
+        }
+    }
+    // last stage at the new point (k1 of the next step)
+    const double tn1 = clip ? h : t + dt;
+    const double th1 = clip ? 1.0 : tn1 * inv_h;
+    OdeState<TAN> s3;
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        e[a] = fma(e4 * dt, k4[a], e[a]);
-        if constexpr (TAN)
+    for (int a = 0; a < 5; ++a) {
+      s3.y[a] = y3[a];
+      if constexpr (TAN)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) E[a][c] = fma(e4 * dt, K4[a][c], E[a][c]);
-      }
-      // stress pair (and tangent pair) of the two embedded solutions
-      double s_hi[6], s_lo[6];
-      M66 C_hi, C_lo;
-      ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
-      OdeState<TAN> s2;
+        for (int c = 0; c < 6; ++c) s3.Y[a][c] = Y3[a][c];
+    }
+    double k4[5];
+    M56 K4;
+    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4);
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        s2.y[a] = y3[a] - e[a];
-        if constexpr (TAN)
+    for (int a = 0; a < 5; ++a) {
+      e[a] = fma(e4 * dt, k4[a], e[a]);
+      if constexpr (TAN)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) s2.Y[a][c] = Y3[a][c] - E[a][c];
-      }
-      ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
-      double sum = 0.0;
+        for (int c = 0; c < 6; ++c) E[a][c] = fma(e4 * dt, K4[a][c], E[a][c]);
+    }
+    // stress pair (and tangent pair) of the two embedded solutions
+    double s_hi[6], s_lo[6];
+    M66 C_hi, C_lo;
+    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
+    OdeState<TAN> s2;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      s2.y[a] = y3[a] - e[a];
+      if constexpr (TAN)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s2.Y[a][c] = Y3[a][c] - E[a][c];
+    }
+    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
+    int m = 6;
+    if constexpr (TAN) {
 #pragma unroll
       for (int i = 0; i < 6; ++i)
-        sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
-      int m = 6;
-      if constexpr (TAN) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
+      m = 42;
+    }
+    // a trial step that overflows is rejected like one with a large error
+    const double err = finite64(sum) ? sqrt(sum / m) : 1e300;
+    // Hairer II.4: fac 0.9, facmin 0.2, facmax 5 (1 right after a rejection), exponent 1/3
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    const double grow = err == 0.0 ? facmax : fmin(facmax, fmax(0.2, 0.9 * fpow::pow_pos(err, -1.0 / 3.0)));
+    if (err <= 1.0) {
+      t = tn1;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        s.y[a] = y3[a];
+        k1[a] = k4[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            s.Y[a][c] = Y3[a][c];
+            K1[a][c] = K4[a][c];
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = s_hi[i];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
+      }
+      ++n_acc;
+      last_rejected = false;
+      if (clip) done = true;
+    } else {
+      ++n_rej;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+
+  // outputs at the end of the step (sig_old is the stress of the last accepted
+  // substep); C36: row-major 6x6 (the tangent of an explicit integrator is
+  // not symmetric in general), written only with TAN and when non-NULL
+  AD_HD unsigned finish(double h, double (&sig)[6], double (&z)[6], double* C36) const {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sig[i] = sig_old[i];
+    if constexpr (TAN) {
+      if (C36)
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
-          for (int c = 0; c < 6; ++c)
-            sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
-        m = 42;
-      }
-      // a trial step that overflows is rejected like one with a large error
-      const double err = finite64(sum) ? sqrt(sum / m) : 1e300;
-      // Hairer II.4: fac 0.9, facmin 0.2, facmax 5 (1 right after a rejection), exponent 1/3
-      const double facmax = last_rejected ? 1.0 : 5.0;
-      const double grow = err == 0.0 ? facmax : fmin(facmax, fmax(0.2, 0.9 * fpow::pow_pos(err, -1.0 / 3.0)));
-      if (err <= 1.0) {
-        t = tn1;
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
-          s.y[a] = y3[a];
-          k1[a] = k4[a];
-          if constexpr (TAN)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-              s.Y[a][c] = Y3[a][c];
-              K1[a][c] = K4[a][c];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          sig_old[i] = s_hi[i];
-          if constexpr (TAN)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
-        }
-        ++n_acc;
-        last_rejected = false;
-        if (clip) done = true;
-      } else {
-        ++n_rej;
-        last_rejected = true;
-      }
-      dt *= grow;
+          for (int c = 0; c < 6; ++c) C36[6 * i + c] = C_old[i][c];
     }
+    z[0] = s.y[0];
+    z[1] = s.y[1];
+    z[2] = -(s.y[0] + s.y[1]);
+    z[3] = s.y[2];
+    z[4] = s.y[3];
+    z[5] = s.y[4];
+    unsigned st = flags;
+    if (t >= h && !(flags & ST_CAP)) st |= ST_CONVERGED;
+    if (!finite64(sig[0]) || !finite64(z[0])) st |= ST_NONFINITE;
+    st |= (unsigned)(n_acc < 0xffff ? n_acc : 0xffff);
+    st |= (unsigned)(n_rej < 0x7ff ? n_rej : 0x7ff) << ST_ODE_REJ_SHIFT;
+    return st;
   }
-  // outputs at theta = 1 (sig_old is the stress of the last accepted step)
-#pragma unroll
-  for (int i = 0; i < 6; ++i) sig[i] = sig_old[i];
-  if constexpr (TAN) {
-    if (C36)
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) C36[6 * i + c] = C_old[i][c];
-  }
-  z[0] = s.y[0];
-  z[1] = s.y[1];
-  z[2] = -(s.y[0] + s.y[1]);
-  z[3] = s.y[2];
-  z[4] = s.y[3];
-  z[5] = s.y[4];
-  unsigned st = flags;
-  if (active && t >= h && !(flags & ST_CAP)) st |= ST_CONVERGED;
-  if (!finite64(sig[0]) || !finite64(z[0])) st |= ST_NONFINITE;
-  st |= (unsigned)(n_acc < 0xffff ? n_acc : 0xffff);
-  st |= (unsigned)(n_rej < 0x7ff ? n_rej : 0x7ff) << ST_ODE_REJ_SHIFT;
-  return st;
+};
+
+// One voxel, start to end (single thread; the kernel schedules Ode23Voxel
+// states per lane itself).
+template <class Law, bool TAN>
+AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
+                           const double (&zn)[6], const Step& hs, const Ode23Ctl& ctl, double (&sig)[6],
+                           double (&z)[6], double* C36) {
+  Ode23Voxel<Law, TAN> v;
+  v.init(p, epsn, eps1, zn, hs.h);
+  while (!v.done) v.attempt(p, hs, ctl);
+  return v.finish(hs.h, sig, z, C36);
 }
 
 }  // namespace gsm

@@ -45,8 +45,8 @@ int host_update_ode23(const double* prm, int64_t n, const double* eps_n, const d
       e1[c] = eps[6 * i + c];
       zi[c] = zn[6 * i + c];
     }
-    unsigned st = tan ? voxel_ode23<NortonDev, true>(p, e0, e1, zi, hs, ctl, true, s, zo, tan + 36 * i)
-                      : voxel_ode23<NortonDev, false>(p, e0, e1, zi, hs, ctl, true, s, zo, nullptr);
+    unsigned st = tan ? voxel_ode23<NortonDev, true>(p, e0, e1, zi, hs, ctl, s, zo, tan + 36 * i)
+                      : voxel_ode23<NortonDev, false>(p, e0, e1, zi, hs, ctl, s, zo, nullptr);
     for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
     status[i] = (int32_t)st;
   }

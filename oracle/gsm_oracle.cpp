@@ -61,11 +61,14 @@ const double P[6][5] = {
 const double W[6] = {2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};
 
 struct Law {
-  int kind;         // 0 = linear elastic, 1 = elastic + deviatoric Norton viscoplastic
+  int kind;         // 0 = linear elastic, 1 = elastic + deviatoric Norton viscoplastic,
+                    // 2 = Michel-Suquet (kinematic hardening H, yield sigma_Y; force-potential form)
   double lam, mu;   // Lame constants from (E, nu)
-  double sigma0;    // drag stress
+  double sigma0;    // drag stress (sigma_d for kind 2)
   double edot0;     // reference strain rate
   double n;         // rate sensitivity exponent
+  double sigY;      // kind 2: yield stress (K(alpha) = sigma_Y)
+  double Hkin;      // kind 2: kinematic hardening modulus H
   double C[6][6];   // isotropic stiffness in Voigt notation
   double G[5][5];   // P^T diag(W) P
 };
@@ -75,9 +78,12 @@ void make_law(int kind, const double* prm, Law* L) {
   L->kind = kind;
   L->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   L->mu = E / (2.0 * (1.0 + nu));
-  L->sigma0 = kind == 1 ? prm[2] : 0.0;
-  L->edot0 = kind == 1 ? prm[3] : 1.0;
-  L->n = kind == 1 ? prm[4] : 1.0;
+  // kind 1: (E, nu, sigma0, edot0, n); kind 2: (E, nu, sigma_Y, H, edot0, sigma_d, n)
+  L->sigma0 = kind == 1 ? prm[2] : kind == 2 ? prm[5] : 0.0;
+  L->edot0 = kind == 1 ? prm[3] : kind == 2 ? prm[4] : 1.0;
+  L->n = kind == 1 ? prm[4] : kind == 2 ? prm[6] : 1.0;
+  L->sigY = kind == 2 ? prm[2] : 0.0;
+  L->Hkin = kind == 2 ? prm[3] : 0.0;
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) L->C[i][j] = 0.0;
   for (int i = 0; i < 3; ++i) {
@@ -484,26 +490,39 @@ void radial_return(const Law& L, const double eps[6], const double zn[6], double
 }
 
 // ================================================= force-potential form, ode23
-// Sec. 2, Eq. (gsm_internal): adot = dPsi/dA (A) with A = -d omega/d a.  With
-// a = y (the 5 unknowns of z = P y): A = -psi_y(eps, y) = P^T sigma, and the
-// force potential of Eq. (michel_suquet_psi) at sigma_Y = 0, H = 0:
+// Sec. 2, Eq. (gsm_internal): adot = dPsi/dA (A) with A = -d omega/d a.
+//
+// Norton law (kind 1): a = y (the 5 unknowns of z = P y), A = -psi_y = P^T sigma,
+// Psi of Eq. (michel_suquet_psi) at sigma_Y = 0, H = 0:
 //   Psi(A) = sigma0 edot0 / (n+1) (s_A / sigma0)^(n+1),  s_A^2 = A^T G^{-1} A
 // (G^{-1} is the dual metric of the rate norm; s_A is the von Mises stress).
 //   Psi_A  = edot0 (s_A/sigma0)^n G^{-1}A / s_A
 //   Psi_AA = edot0 sigma0^{-n} [ s_A^{n-1} G^{-1} + (n-1) s_A^{n-3} (G^{-1}A)(G^{-1}A)^T ]
 // (at s_A = 0: Psi_A = 0; Psi_AA = edot0/sigma0 G^{-1} for n = 1 and 0 for n > 1).
 //
+// Michel-Suquet law (kind 2), Eq. (michel_suquet_omega) and (michel_suquet_psi)
+// with K(alpha) = sigma_Y: a = (y, alpha),
+//   omega = 1/2 (eps - P y)^T C (eps - P y) + 1/3 (P y)^T Hv (P y) + sigma_Y alpha,
+//   Hv = diag(H, H, H, H/2, H/2, H/2),
+//   A_y = P^T (sigma - X), X = 2/3 Hv P y (back stress),  A_alpha = -sigma_Y,
+//   Psi = sigma_d edot0 / (n+1) ( (s + A_alpha)^+ / sigma_d )^(n+1),  s^2 = A_y^T G^{-1} A_y.
+// With x = (s + A_alpha)^+, r = edot0 (x/sigma_d)^n, r' = n edot0/sigma_d (x/sigma_d)^(n-1):
+//   Psi_{A_y} = r G^{-1}A_y / s,  Psi_{A_alpha} = r,
+//   Psi_{A_y A_y} = r' (G^{-1}A_y)(G^{-1}A_y)^T / s^2 + r [ G^{-1}/s - (G^{-1}A_y)(G^{-1}A_y)^T / s^3 ],
+//   Psi_{A_y A_alpha} = r' G^{-1}A_y / s,  Psi_{A_alpha A_alpha} = r'
+// (all zero where x = 0, i.e. inside the elastic domain).
+// The Norton law is kind 2 with sigma_Y = 0, H = 0 (alpha then only counts).
+//
 // Sec. 4.3 integrates the evolution equation over [t_n, t_{n+1}] with strain
 // eps(t) interpolated linearly between eps_n and eps_{n+1}, by the embedded
 // Runge-Kutta pair of Bogacki and Shampine (MATLAB's ode23) with automatic
 // step size control after Hairer, Norsett, Wanner (Solving ODEs I, II.4).
 // Corollary 1: the tangent dy/deps_{n+1} is the solution of the derivative
-// ODE d/dt (dy/de) = Psi_AA(A) dA/de, dA/de = P^T C (theta(t) I - P dy/de),
-// theta(t) = (t - t_n)/h, integrated together with y by the same steps, with
-// the step sizes undifferentiated and the derivative in the error measure.
-// Sec. 4.5 (stress-driven error control): the error measure is taken on the
-// pair of stresses (and of tangents) that the two embedded solutions give
-// at the end of the substep.
+// ODE d/dt (da/de) = Psi_AA(A) dA/de, integrated together with a by the same
+// steps, with the step sizes undifferentiated and the derivative in the error
+// measure.  Sec. 4.5 (stress-driven error control): the error measure is taken
+// on the pair of stresses (and of tangents) that the two embedded solutions
+// give at the end of the substep.
 
 struct Ode23Opts {
   double rtol, atol;
@@ -520,7 +539,7 @@ void g_inverse(const Law& L, double Gi[5][5]) {
   }
 }
 
-// Psi_A(A) and (optionally) Psi_AA(A).
+// Psi_A(A) and (optionally) Psi_AA(A) of the Norton force potential.
 void psi_force_a(const Law& L, const double Gi[5][5], const double A[5], double g[5], double H[5][5]) {
   double GA[5];
   double s2 = 0.0;
@@ -549,52 +568,119 @@ void psi_force_a(const Law& L, const double Gi[5][5], const double A[5], double 
   }
 }
 
-// Right-hand side at time t in [0, h] of the step: f = Psi_A(A), A = P^T sigma
-// with sigma = C (eps(t) - P y); with Y = dy/deps_{n+1} (5x6) also
-// F = Psi_AA(A) P^T C (theta I - P Y).
-void ode_rhs(const Law& L, const double Gi[5][5], const double epsn[6], const double eps1[6], double h, double t,
-             const double y[5], const double (*Y)[6], double f[5], double (*F)[6]) {
-  const double th = t / h;
-  double et[6], sig[6], A[5];
-  for (int i = 0; i < 6; ++i) et[i] = epsn[i] + th * (eps1[i] - epsn[i]);
-  stress(L, et, y, sig);
+// Psi of the Michel-Suquet law and its gradient / Hessian in (A_y, A_alpha).
+double psi_force_ms(const Law& L, const double Gi[5][5], const double A[6], double g[6], double H[6][6]) {
+  double GA[5];
+  double s2 = 0.0;
   for (int a = 0; a < 5; ++a) {
-    double s = 0.0;
-    for (int i = 0; i < 6; ++i) s += P[i][a] * sig[i];
-    A[a] = s;
+    double t = 0.0;
+    for (int b = 0; b < 5; ++b) t += Gi[a][b] * A[b];
+    GA[a] = t;
+    s2 += A[a] * t;
   }
-  double H[5][5];
-  psi_force_a(L, Gi, A, f, F ? H : nullptr);
+  const double s = std::sqrt(s2);
+  const double x = s + A[5];
+  if (g)
+    for (int a = 0; a < 6; ++a) g[a] = 0.0;
+  if (H)
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) H[a][b] = 0.0;
+  if (!(x > 0.0) || s == 0.0) return 0.0;
+  const double n = L.n, sd = L.sigma0, e0 = L.edot0;
+  const double r = e0 * std::pow(x / sd, n);
+  const double rp = n * e0 / sd * std::pow(x / sd, n - 1.0);
+  if (g) {
+    for (int a = 0; a < 5; ++a) g[a] = r * GA[a] / s;
+    g[5] = r;
+  }
+  if (H) {
+    for (int a = 0; a < 5; ++a) {
+      for (int b = 0; b < 5; ++b)
+        H[a][b] = rp * GA[a] * GA[b] / s2 + r * (Gi[a][b] / s - GA[a] * GA[b] / (s2 * s));
+      H[a][5] = H[5][a] = rp * GA[a] / s;
+    }
+    H[5][5] = rp;
+  }
+  return sd * e0 / (n + 1.0) * std::pow(x / sd, n + 1.0);
+}
+
+// Generalized stress A (NY entries) at (eps(t), y): A_y = P^T (sigma - X),
+// X = 2/3 Hv P y; A_alpha = -sigma_Y (kind 2).  Hv = 0 for the Norton law.
+template <int NY>
+void gen_stress(const Law& L, const double et[6], const double y[NY], double A[NY]) {
+  double sig[6], z[6];
+  stress(L, et, y, sig);
+  for (int i = 0; i < 6; ++i) {
+    double pz = 0.0;
+    for (int a = 0; a < 5; ++a) pz += P[i][a] * y[a];
+    z[i] = pz;
+  }
+  for (int a = 0; a < 5; ++a) {
+    double t = 0.0;
+    for (int i = 0; i < 6; ++i) {
+      const double hv = i < 3 ? L.Hkin : 0.5 * L.Hkin;
+      t += P[i][a] * (sig[i] - (2.0 / 3.0) * hv * z[i]);
+    }
+    A[a] = t;
+  }
+  if (NY == 6) A[NY - 1] = -L.sigY;
+}
+
+// Right-hand side at time t in [0, h] of the step: f = Psi_A(A) and, with
+// Y = da/deps_{n+1} (NY x 6), F = Psi_AA(A) dA/deps_{n+1},
+// dA_y/deps = P^T [C (theta I - P Y_y) - 2/3 Hv P Y_y], dA_alpha/deps = 0.
+template <int NY>
+void ode_rhs(const Law& L, const double Gi[5][5], const double epsn[6], const double eps1[6], double h, double t,
+             const double y[NY], const double (*Y)[6], double f[NY], double (*F)[6]) {
+  const double th = t / h;
+  double et[6], A[NY];
+  for (int i = 0; i < 6; ++i) et[i] = epsn[i] + th * (eps1[i] - epsn[i]);
+  gen_stress<NY>(L, et, y, A);
+  double H[6][6];
+  if (NY == 5) {
+    double H5[5][5];
+    psi_force_a(L, Gi, A, f, F ? H5 : nullptr);
+    if (F)
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) H[a][b] = H5[a][b];
+  } else {
+    psi_force_ms(L, Gi, A, f, H);
+  }
   if (!F) return;
-  // D = theta I - P Y (6x6), CD = C D, dA = P^T C D (5x6)
-  double D[6][6], dA[5][6];
+  double D[6][6], dA[6][6];
   for (int i = 0; i < 6; ++i)
     for (int k = 0; k < 6; ++k) {
       double pz = 0.0;
       for (int a = 0; a < 5; ++a) pz += P[i][a] * Y[a][k];
-      D[i][k] = (i == k ? th : 0.0) - pz;
+      D[i][k] = (i == k ? th : 0.0) - pz;  // theta I - P Y_y
     }
   for (int a = 0; a < 5; ++a)
     for (int k = 0; k < 6; ++k) {
-      double s = 0.0;
+      double v = 0.0;
       for (int i = 0; i < 6; ++i) {
         double cd = 0.0;
         for (int j = 0; j < 6; ++j) cd += L.C[i][j] * D[j][k];
-        s += P[i][a] * cd;
+        double pz = 0.0;
+        for (int b = 0; b < 5; ++b) pz += P[i][b] * Y[b][k];
+        const double hv = i < 3 ? L.Hkin : 0.5 * L.Hkin;
+        v += P[i][a] * (cd - (2.0 / 3.0) * hv * pz);
       }
-      dA[a][k] = s;
+      dA[a][k] = v;
     }
-  for (int a = 0; a < 5; ++a)
+  if (NY == 6)
+    for (int k = 0; k < 6; ++k) dA[5][k] = 0.0;
+  for (int a = 0; a < NY; ++a)
     for (int k = 0; k < 6; ++k) {
-      double s = 0.0;
-      for (int b = 0; b < 5; ++b) s += H[a][b] * dA[b][k];
-      F[a][k] = s;
+      double v = 0.0;
+      for (int b = 0; b < NY; ++b) v += H[a][b] * dA[b][k];
+      F[a][k] = v;
     }
 }
 
-// Stress and tangent at the end of a substep from y, Y: sigma = C (eps(t) - P y),
-// Ct = C (theta I - P Y).
-void stress_tangent(const Law& L, const double epsn[6], const double eps1[6], double h, double t, const double y[5],
+// Stress and tangent at the end of a substep: sigma = C (eps(t) - P y),
+// Ct = C (theta I - P Y_y).
+template <int NY>
+void stress_tangent(const Law& L, const double epsn[6], const double eps1[6], double h, double t, const double y[NY],
                     const double (*Y)[6], double sig[6], double (*Ct)[6]) {
   const double th = t / h;
   double et[6];
@@ -603,13 +689,13 @@ void stress_tangent(const Law& L, const double epsn[6], const double eps1[6], do
   if (!Ct) return;
   for (int i = 0; i < 6; ++i)
     for (int k = 0; k < 6; ++k) {
-      double s = 0.0;
+      double v = 0.0;
       for (int j = 0; j < 6; ++j) {
         double pz = 0.0;
         for (int a = 0; a < 5; ++a) pz += P[j][a] * Y[a][k];
-        s += L.C[i][j] * ((j == k ? th : 0.0) - pz);
+        v += L.C[i][j] * ((j == k ? th : 0.0) - pz);
       }
-      Ct[i][k] = s;
+      Ct[i][k] = v;
     }
 }
 
@@ -624,19 +710,28 @@ struct OdeInfo {
   int accepted, rejected, flags;
 };
 
-// One material update by ode23 over [t_n, t_{n+1}] (length h).
-void update_ode23(const Law& L, const double epsn[6], const double eps1[6], const double zn[6], double h,
-                  const Ode23Opts& o, double sig_out[6], double z_out[6], double (*Ct_out)[6], OdeInfo* info) {
+// One material update by ode23 over [t_n, t_{n+1}] (length h).  a_n: z_n (6)
+// and, for NY = 6, alpha_n; a_out likewise.
+template <int NY>
+void update_ode23(const Law& L, const double epsn[6], const double eps1[6], const double zn[6], double alpha_n,
+                  double h, const Ode23Opts& o, double sig_out[6], double z_out[6], double* alpha_out,
+                  double (*Ct_out)[6], OdeInfo* info) {
   double Gi[5][5];
   g_inverse(L, Gi);
-  double y[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
-  double Y[5][6] = {};
+  double y[NY];
+  y[0] = zn[0];
+  y[1] = zn[1];
+  y[2] = zn[3];
+  y[3] = zn[4];
+  y[4] = zn[5];
+  if (NY == 6) y[NY - 1] = alpha_n;
+  double Y[NY][6] = {};
   const bool tan = o.tangent;
-  double k[4][5], K[4][5][6];
+  double k[4][NY], K[4][NY][6];
   double t = 0.0, dt = h;
-  ode_rhs(L, Gi, epsn, eps1, h, 0.0, y, Y, k[0], tan ? K[0] : nullptr);
+  ode_rhs<NY>(L, Gi, epsn, eps1, h, 0.0, y, Y, k[0], tan ? K[0] : nullptr);
   double sig_old[6], C_old[6][6];
-  stress_tangent(L, epsn, eps1, h, 0.0, y, Y, sig_old, tan ? C_old : nullptr);
+  stress_tangent<NY>(L, epsn, eps1, h, 0.0, y, Y, sig_old, tan ? C_old : nullptr);
   info->accepted = info->rejected = 0;
   info->flags = 0;
   bool last_rejected = false;
@@ -647,47 +742,47 @@ void update_ode23(const Law& L, const double epsn[6], const double eps1[6], cons
     }
     const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
     if (clip) dt = h - t;
-    double ys[5], Ys[5][6];
+    double ys[NY], Ys[NY][6];
     // stage 2
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       ys[a] = y[a] + dt * BS_A21 * k[0][a];
       if (tan)
         for (int c = 0; c < 6; ++c) Ys[a][c] = Y[a][c] + dt * BS_A21 * K[0][a][c];
     }
-    ode_rhs(L, Gi, epsn, eps1, h, t + 0.5 * dt, ys, Ys, k[1], tan ? K[1] : nullptr);
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, t + 0.5 * dt, ys, Ys, k[1], tan ? K[1] : nullptr);
     // stage 3
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       ys[a] = y[a] + dt * BS_A32 * k[1][a];
       if (tan)
         for (int c = 0; c < 6; ++c) Ys[a][c] = Y[a][c] + dt * BS_A32 * K[1][a][c];
     }
-    ode_rhs(L, Gi, epsn, eps1, h, t + 0.75 * dt, ys, Ys, k[2], tan ? K[2] : nullptr);
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, t + 0.75 * dt, ys, Ys, k[2], tan ? K[2] : nullptr);
     // order-3 solution and the last stage
-    double yn1[5], Yn1[5][6];
-    for (int a = 0; a < 5; ++a) {
+    double yn1[NY], Yn1[NY][6];
+    for (int a = 0; a < NY; ++a) {
       yn1[a] = y[a] + dt * (BS_B[0] * k[0][a] + BS_B[1] * k[1][a] + BS_B[2] * k[2][a]);
       if (tan)
         for (int c = 0; c < 6; ++c)
           Yn1[a][c] = Y[a][c] + dt * (BS_B[0] * K[0][a][c] + BS_B[1] * K[1][a][c] + BS_B[2] * K[2][a][c]);
     }
     const double tn1 = clip ? h : t + dt;
-    ode_rhs(L, Gi, epsn, eps1, h, tn1, yn1, Yn1, k[3], tan ? K[3] : nullptr);
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, tn1, yn1, Yn1, k[3], tan ? K[3] : nullptr);
     // embedded difference (order 3 minus order 2) and the stress pair it gives
-    double e[5], E[5][6];
-    for (int a = 0; a < 5; ++a) {
+    double e[NY], E[NY][6];
+    for (int a = 0; a < NY; ++a) {
       e[a] = dt * (BS_E[0] * k[0][a] + BS_E[1] * k[1][a] + BS_E[2] * k[2][a] + BS_E[3] * k[3][a]);
       if (tan)
         for (int c = 0; c < 6; ++c)
           E[a][c] = dt * (BS_E[0] * K[0][a][c] + BS_E[1] * K[1][a][c] + BS_E[2] * K[2][a][c] + BS_E[3] * K[3][a][c]);
     }
-    double y2[5], Y2[5][6], s3[6], s2[6], C3[6][6], C2[6][6];
-    for (int a = 0; a < 5; ++a) {
+    double y2[NY], Y2[NY][6], s3[6], s2[6], C3[6][6], C2[6][6];
+    for (int a = 0; a < NY; ++a) {
       y2[a] = yn1[a] - e[a];
       if (tan)
         for (int c = 0; c < 6; ++c) Y2[a][c] = Yn1[a][c] - E[a][c];
     }
-    stress_tangent(L, epsn, eps1, h, tn1, yn1, Yn1, s3, tan ? C3 : nullptr);
-    stress_tangent(L, epsn, eps1, h, tn1, y2, Y2, s2, tan ? C2 : nullptr);
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, yn1, Yn1, s3, tan ? C3 : nullptr);
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, y2, Y2, s2, tan ? C2 : nullptr);
     double sum = 0.0;
     int m = 0;
     // (a zero scale, atol = 0 at zero stress, counts a zero difference as no error)
@@ -709,7 +804,7 @@ void update_ode23(const Law& L, const double epsn[6], const double eps1[6], cons
     const double grow = err == 0.0 ? facmax : std::fmin(facmax, std::fmax(0.2, 0.9 * std::pow(err, -1.0 / 3.0)));
     if (err <= 1.0) {
       t = tn1;
-      for (int a = 0; a < 5; ++a) {
+      for (int a = 0; a < NY; ++a) {
         y[a] = yn1[a];
         k[0][a] = k[3][a];
         if (tan)
@@ -732,13 +827,14 @@ void update_ode23(const Law& L, const double epsn[6], const double eps1[6], cons
     dt *= grow;
   }
   if (t >= h && !(info->flags & (F_NONFINITE | F_CAP))) info->flags |= F_CONVERGED;
-  stress_tangent(L, epsn, eps1, h, h, y, Y, sig_out, Ct_out);
+  stress_tangent<NY>(L, epsn, eps1, h, h, y, Y, sig_out, Ct_out);
   z_out[0] = y[0];
   z_out[1] = y[1];
   z_out[2] = -(y[0] + y[1]);
   z_out[3] = y[2];
   z_out[4] = y[3];
   z_out[5] = y[4];
+  if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
 }
 
 }  // namespace
@@ -845,19 +941,29 @@ void ora_newton_matrix_batch(const double* params, int64_t n, const double* y, c
 }
 
 // ode23 update (Sec. 4.3 with the stress-driven error control of Sec. 4.5):
-// eps_n, eps, z_n [n][6]; tangent [n][6][6] or NULL; info [n][3] = accepted,
-// rejected substeps, flags (1 converged, 2 non-finite, 4 substep cap).
-int ora_update_ode23(const double* params, int64_t n, const double* eps_n, const double* eps, const double* zn,
-                     double h, double rtol, double atol, int max_steps, double* sigma, double* z, double* tangent,
-                     int32_t* info) {
+// kind 1 (Norton, params E, nu, sigma0, edot0, n) or 2 (Michel-Suquet, params
+// E, nu, sigma_Y, H, edot0, sigma_d, n); eps_n, eps, z_n [n][6]; alpha_n,
+// alpha [n] (kind 2; alpha_n may be NULL = 0); tangent [n][6][6] or NULL;
+// info [n][3] = accepted, rejected substeps, flags (1 converged, 4 substep cap).
+int ora_update_ode23(int kind, const double* params, int64_t n, const double* eps_n, const double* eps,
+                     const double* zn, const double* alpha_n, double h, double rtol, double atol, int max_steps,
+                     double* sigma, double* z, double* alpha, double* tangent, int32_t* info) {
+  if (kind != 1 && kind != 2) return -1;
   Law L;
-  make_law(1, params, &L);
+  make_law(kind, params, &L);
   Ode23Opts o{rtol, atol, max_steps, tangent != nullptr};
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t i = 0; i < n; ++i) {
     double(*Ct)[6] = tangent ? reinterpret_cast<double(*)[6]>(tangent + 36 * i) : nullptr;
     OdeInfo inf;
-    update_ode23(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, h, o, sigma + 6 * i, z + 6 * i, Ct, &inf);
+    double al = 0.0;
+    if (kind == 1)
+      update_ode23<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
+                      &inf);
+    else
+      update_ode23<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, alpha_n ? alpha_n[i] : 0.0, h, o, sigma + 6 * i,
+                      z + 6 * i, &al, Ct, &inf);
+    if (alpha) alpha[i] = al;
     if (info) {
       info[3 * i] = inf.accepted;
       info[3 * i + 1] = inf.rejected;
@@ -865,6 +971,28 @@ int ora_update_ode23(const double* params, int64_t n, const double* eps_n, const
     }
   }
   return 0;
+}
+
+// Michel-Suquet force potential Psi(A) at A [6] = (A_y, A_alpha); g [6], H [6][6] or NULL.
+double ora_psi_force_ms(const double* params, const double* A, double* g, double* H) {
+  Law L;
+  make_law(2, params, &L);
+  double Gi[5][5], gg[6], HH[6][6];
+  g_inverse(L, Gi);
+  const double v = psi_force_ms(L, Gi, A, gg, HH);
+  if (g)
+    for (int a = 0; a < 6; ++a) g[a] = gg[a];
+  if (H)
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) H[6 * a + b] = HH[a][b];
+  return v;
+}
+
+// Generalized stress A of the Michel-Suquet law at (eps, y, alpha): [6].
+void ora_gen_stress_ms(const double* params, const double* eps, const double* y6, double* A) {
+  Law L;
+  make_law(2, params, &L);
+  gen_stress<6>(L, eps, y6, A);
 }
 
 // Psi_A (and Psi_AA when H != NULL) of the force potential at A [5].

@@ -16,6 +16,7 @@ from . import build as _build
 
 KIND_ELASTIC = 0
 KIND_NORTON = 1
+KIND_MICHEL_SUQUET = 2
 
 # z = P y with y = (z11, z22, g23, g13, g12) and z33 = -z11 - z22 (Sec. 6:
 # one component of the deviatoric viscoplastic strain is eliminated).
@@ -61,10 +62,13 @@ def _load():
         lib.ora_Pi.restype = ctypes.c_double
         lib.ora_max_threads.restype = ctypes.c_int
         lib.ora_newton_matrix_batch.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, _dp]
-        lib.ora_update_ode23.argtypes = [_dp, ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _ip]
+        lib.ora_update_ode23.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _ip]
         lib.ora_update_ode23.restype = ctypes.c_int
         lib.ora_psi_force_a.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_psi_force_ms.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_psi_force_ms.restype = ctypes.c_double
+        lib.ora_gen_stress_ms.argtypes = [_dp, _dp, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -207,11 +211,16 @@ def newton_matrix_batch(params, y, y_n, h):
     return K, H
 
 
-def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100000, tangent=False, info=False):
+def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100000, tangent=False, info=False,
+                 kind=KIND_NORTON, alpha_n=None):
     """Material update by ode23 (Sec. 4.3, stress-driven error control Sec. 4.5).
 
-    eps_n, eps, z_n: (n, 6); returns sigma, z [, tangent (n, 6, 6)] [, info
-    (n, 3) = accepted substeps, rejected substeps, flags]."""
+    kind KIND_NORTON: params (E, nu, sigma0, edot0, n); KIND_MICHEL_SUQUET:
+    params (E, nu, sigma_Y, H, edot0, sigma_d, n) with the equivalent plastic
+    strain alpha as a further internal variable (alpha_n: (n,) or None = 0).
+    eps_n, eps, z_n: (n, 6); returns sigma, z [, alpha (Michel-Suquet)]
+    [, tangent (n, 6, 6)] [, info (n, 3) = accepted substeps, rejected
+    substeps, flags]."""
     lib = _load()
     eps_n = _f64(eps_n).reshape(-1, 6)
     eps = _f64(eps).reshape(-1, 6)
@@ -219,17 +228,43 @@ def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100
     n = eps.shape[0]
     sig = np.zeros((n, 6))
     z = np.zeros((n, 6))
+    alpha = np.zeros(n)
+    a_n = _f64(alpha_n).reshape(n) if alpha_n is not None else None
     C = np.zeros((n, 6, 6)) if tangent else None
     inf = np.zeros((n, 3), dtype=np.int32)
-    lib.ora_update_ode23(_ptr(_params(params)), ctypes.c_int64(n), _ptr(eps_n), _ptr(eps), _ptr(z_n), ctypes.c_double(h),
-                         ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(max_steps), _ptr(sig), _ptr(z),
-                         _ptr(C) if tangent else None, inf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    prm = _f64(list(params) + [0.0] * (7 - len(params)))
+    rc = lib.ora_update_ode23(int(kind), _ptr(prm), ctypes.c_int64(n), _ptr(eps_n), _ptr(eps), _ptr(z_n),
+                              _ptr(a_n) if a_n is not None else None, ctypes.c_double(h), ctypes.c_double(rtol),
+                              ctypes.c_double(atol), ctypes.c_int(max_steps), _ptr(sig), _ptr(z), _ptr(alpha),
+                              _ptr(C) if tangent else None, inf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("update_ode23: unsupported law kind")
     out = [sig, z]
+    if kind == KIND_MICHEL_SUQUET:
+        out.append(alpha)
     if tangent:
         out.append(C)
     if info:
         out.append(inf)
     return tuple(out)
+
+
+def psi_force_ms(params, A):
+    """(Psi, Psi_A, Psi_AA) of the Michel-Suquet force potential at A = (A_y, A_alpha) (6,)."""
+    lib = _load()
+    A = _f64(A).reshape(6)
+    g = np.zeros(6)
+    H = np.zeros((6, 6))
+    v = lib.ora_psi_force_ms(_ptr(_f64(params)), _ptr(A), _ptr(g), _ptr(H))
+    return v, g, H
+
+
+def gen_stress_ms(params, eps, y6):
+    """Generalized stress A = -d omega/d(y, alpha) of the Michel-Suquet law (6,)."""
+    lib = _load()
+    A = np.zeros(6)
+    lib.ora_gen_stress_ms(_ptr(_f64(params)), _ptr(_f64(eps).reshape(6)), _ptr(_f64(y6).reshape(6)), _ptr(A))
+    return A
 
 
 def psi_force_a(params, A):

@@ -212,6 +212,10 @@ MATRIX_16 = (70.0, 0.3, 0.1, 1.0, 5.0)
 INCLUSION_16 = (400.0, 0.2)
 FIBRE_256 = (72.0, 0.22)
 MATRIX_256 = (70.0, 0.3, 0.1, 1.0, 10.0)
+# The paper's metal-matrix composite (Table misu_parameters), in GPa and 1/s:
+# aluminium (E, nu, sigma_Y, H, edot0, sigma_d, n) and alumina (E, nu).
+ALUMINIUM_MS = (55.0, 0.33, 0.025, 1.8, 1.0, 0.130, 3.6)
+ALUMINA = (300.0, 0.25)
 
 
 def sphere_composite_16():

@@ -164,3 +164,92 @@ def test_no_flow_limits():
     z0 = np.zeros((1, 6))
     sig, z, inf = O.update_ode23(PRM, z0, z0, z0, 0.1, info=True)
     assert np.all(sig == 0.0) and np.all(z == 0.0) and inf[0, 0] == 1 and inf[0, 1] == 0
+
+
+# ------------------------------------------------- Michel-Suquet law (kind 2)
+MS = synth.ALUMINIUM_MS  # (E, nu, sigma_Y, H, edot0, sigma_d, n)
+
+
+def _A_samples(rng, k):
+    A = rng.normal(size=(k, 6)) * 0.05
+    A[:, 5] = -MS[2]
+    return A
+
+
+def test_ms_force_potential_derivatives():
+    """Psi_A and Psi_AA against central differences of Psi, outside and inside the
+    elastic domain (there Psi and all its derivatives vanish)."""
+    rng = np.random.default_rng(4)
+    for A in _A_samples(rng, 30):
+        v, g, H = O.psi_force_ms(MS, A)
+        for a in range(6):
+            d = 1e-7
+            Ap, Am = A.copy(), A.copy()
+            Ap[a] += d
+            Am[a] -= d
+            vp, gp, _ = O.psi_force_ms(MS, Ap)
+            vm, gm, _ = O.psi_force_ms(MS, Am)
+            assert abs((vp - vm) / (2 * d) - g[a]) <= 1e-6 * max(np.abs(g).max(), 1e-12)
+            assert np.allclose((gp - gm) / (2 * d), H[:, a], rtol=1e-5, atol=1e-6 * max(np.abs(H).max(), 1e-12))
+    inside = np.array([0.001, -0.002, 0.001, 0.0, 0.002, -MS[2]])  # von Mises well below sigma_Y
+    v, g, H = O.psi_force_ms(MS, inside)
+    assert v == 0.0 and np.all(g == 0.0) and np.all(H == 0.0)
+
+
+def test_ms_reduces_to_norton_without_yield_and_hardening():
+    """sigma_Y = 0, H = 0: the Michel-Suquet ODE is the Norton ODE with sigma0 = sigma_d."""
+    ms = (70.0, 0.3, 0.0, 0.0, 1.0, 0.1, 5.0)
+    en, e, zn = synth.ode23_batch(50, seed=2)
+    sig1, z1, a1, C1, i1 = O.update_ode23(ms, en, e, zn, 0.1, tangent=True, info=True, kind=O.KIND_MICHEL_SUQUET)
+    sig2, z2, C2, i2 = O.update_ode23(synth.MATRIX_16, en, e, zn, 0.1, tangent=True, info=True)
+    assert np.array_equal(i1, i2)
+    assert np.allclose(sig1, sig2, rtol=1e-13, atol=0) and np.allclose(z1, z2, rtol=1e-13, atol=1e-18)
+    assert np.allclose(C1, C2, rtol=1e-12, atol=1e-10)
+
+
+def test_ms_elastic_domain_and_accumulated_plastic_strain():
+    """Inside the yield surface nothing flows; under radial loading of a virgin
+    state alpha equals the equivalent viscoplastic strain sqrt(2/3 e_vp:e_vp)."""
+    en = np.zeros((1, 6))
+    e_small = np.array([[1e-4, -5e-5, -5e-5, 0, 0, 0]])
+    sig, z, a = O.update_ode23(MS, en, e_small, np.zeros((1, 6)), 0.1, kind=O.KIND_MICHEL_SUQUET)
+    assert np.all(z == 0.0) and a[0] == 0.0
+    d = np.array([1.0, -0.5, -0.5, 0.0, 0.0, 0.0])  # deviatoric uniaxial-type direction
+    sig, z, a = O.update_ode23(MS, en, 0.004 * d[None], np.zeros((1, 6)), 0.1, rtol=1e-11, atol=1e-14,
+                               kind=O.KIND_MICHEL_SUQUET)
+    T = np.array([[z[0, 0], z[0, 5] / 2, z[0, 4] / 2], [z[0, 5] / 2, z[0, 1], z[0, 3] / 2],
+                  [z[0, 4] / 2, z[0, 3] / 2, z[0, 2]]])
+    eq = np.sqrt(2.0 / 3.0 * np.sum(T * T))
+    assert a[0] > 0 and abs(a[0] - eq) <= 1e-8 * eq
+
+
+def _ms_reference(prm, eps_n, eps, zn, h):
+    """The Michel-Suquet ODE by scipy's DOP853 at rtol 1e-13, right-hand side from
+    oracle functions: A = gen_stress_ms(eps(t), y, alpha), f = Psi_A(A)."""
+    def f(t, y):
+        et = eps_n + (t / h) * (eps - eps_n)
+        return O.psi_force_ms(prm, O.gen_stress_ms(prm, et, y))[1]
+    y0 = np.concatenate([P5(zn), [0.0]])
+    r = scipy.integrate.solve_ivp(f, (0.0, h), y0, method="DOP853", rtol=1e-13, atol=1e-16)
+    assert r.success
+    return Z6(r.y[:5, -1]), r.y[5, -1]
+
+
+def test_ms_matches_dop853_and_its_tangent():
+    eps_n, eps, zn = synth.ode23_batch(6, seed=13)
+    h = 0.1
+    sig, z, a, C = O.update_ode23(MS, eps_n, eps, zn, h, rtol=1e-10, atol=1e-13, tangent=True,
+                                  kind=O.KIND_MICHEL_SUQUET)
+    for i in range(6):
+        zr, ar = _ms_reference(MS, eps_n[i], eps[i], zn[i], h)
+        assert np.max(np.abs(z[i] - zr)) <= 1e-8 * np.max(np.abs(zr - zn[i])) + 1e-14
+        assert abs(a[i] - ar) <= 1e-8 * ar + 1e-14
+    Cfd = np.zeros((6, 6))
+    for k in range(6):
+        ep, em = eps[0].copy(), eps[0].copy()
+        ep[k] += 1e-6
+        em[k] -= 1e-6
+        sp = O.stress(MS[:2] + (1.0, 1.0, 1.0), ep, P5(_ms_reference(MS, eps_n[0], ep, zn[0], h)[0]))
+        sm = O.stress(MS[:2] + (1.0, 1.0, 1.0), em, P5(_ms_reference(MS, eps_n[0], em, zn[0], h)[0]))
+        Cfd[:, k] = (sp - sm) / 2e-6
+    assert np.max(np.abs(C[0] - Cfd)) <= 1e-6 * np.max(np.abs(Cfd))

@@ -489,6 +489,27 @@ def bench_ode23(G, torch, args):
                      "mean_rejected_substeps": float(((s >> 20) & 0x7FF).mean()),
                      "converged_fraction": float(((s >> 16) & 1).mean())}
         del tan
+    # the paper's Michel-Suquet law (kinematic hardening, yield), same inputs, alpha_n = 0
+    import synth as S
+    Z7 = torch.cat([Z0, torch.zeros(1, n, dtype=torch.float64, device="cuda")])
+    z7 = torch.empty_like(Z7)
+    ms = G.michel_suquet(*S.ALUMINIUM_MS)
+    G.gsm_update_ode23(ms, E0, E1, Z7, 0.1, sig, z7, None, st)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        G.gsm_update_ode23(ms, E0, E1, Z7, 0.1, sig, z7, None, st)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_t = a.elapsed_time(b) / 3
+    s = st.cpu().numpy()
+    out["michel_suquet_no_tangent"] = {"law": "aluminium of the paper's MMC (E=55, nu=0.33, sigma_Y=0.025, "
+                                              "H=1.8, edot0=1, sigma_d=0.13, n=3.6)",
+                                       "voxel_updates_per_s": n / (ms_t * 1e-3), "ms_per_launch": ms_t,
+                                       "mean_accepted_substeps": float((s & 0xFFFF).mean()),
+                                       "mean_rejected_substeps": float(((s >> 20) & 0x7FF).mean()),
+                                       "converged_fraction": float(((s >> 16) & 1).mean())}
     return out
 
 

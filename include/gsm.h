@@ -56,8 +56,12 @@ extern "C" {
 /* ------------------------------------------------------------------- kinds */
 #define GSM_PSI_ELASTIC 0        /* psi = 1/2 eps:C:eps, no internal variables      */
 #define GSM_PSI_ELASTIC_VP_DEV 1 /* psi = 1/2 (eps-z):C:(eps-z), z deviatoric (5 dof) */
+#define GSM_PSI_ELASTIC_VP_KIN 2 /* Eq. michel_suquet_omega: 1/2 (eps-z):C:(eps-z) + 1/3 z:Hv:z
+                                    + sigma_Y alpha, z deviatoric (5 dof) and alpha      */
 #define GSM_PHI_NONE 0
 #define GSM_PHI_NORTON 1         /* phi = sigma0 edot0 n/(n+1) (|zdot|_eq/edot0)^((n+1)/n) */
+#define GSM_PHI_MS_FORCE 2       /* Eq. michel_suquet_psi (a FORCE potential Psi(A)):
+                                    sigma_d edot0/(n+1) ((|dev A_z|_eq + A_alpha)^+/sigma_d)^(n+1) */
 
 #define GSM_FP64 0               /* every step in FP64                                 */
 #define GSM_FP32_FP64FIX 1       /* FP32 Newton, then FP64 correction (FP64 in/out)    */
@@ -68,10 +72,16 @@ typedef struct gsm_material* gsm_handle;
 /*
  * gsm_create -- define a material law (Sec. 2: the law is its two potentials).
  *   psi_kind, phi_kind: GSM_PSI_ELASTIC with GSM_PHI_NONE, or
- *                       GSM_PSI_ELASTIC_VP_DEV with GSM_PHI_NORTON.
+ *                       GSM_PSI_ELASTIC_VP_DEV with GSM_PHI_NORTON, or
+ *                       GSM_PSI_ELASTIC_VP_KIN with GSM_PHI_MS_FORCE (the paper's
+ *                       Michel-Suquet law, K(alpha) = sigma_Y; integrated by
+ *                       gsm_update_ode23 only: its yield function has no smooth
+ *                       dissipation form for the implicit-Euler Newton).
  *   params: host array; {E, nu} (n_params = 2) for the elastic law,
- *           {E, nu, sigma0, edot0, n} (n_params = 5) for the Norton law.
- *           Requires E > 0, -1 < nu < 0.5, sigma0 > 0, edot0 > 0, n > 0.
+ *           {E, nu, sigma0, edot0, n} (n_params = 5) for the Norton law,
+ *           {E, nu, sigma_Y, H, edot0, sigma_d, n} (n_params = 7) for the
+ *           Michel-Suquet law.  Requires E > 0, -1 < nu < 0.5, sigma0 > 0,
+ *           edot0 > 0, n > 0; sigma_Y >= 0, H >= 0, sigma_d > 0, n >= 1.
  *   precision: GSM_FP64, GSM_FP32_FP64FIX or GSM_FP32.
  *   out: receives an opaque handle owned by the library (gsm_destroy).
  * Synchronous, host only.  Errors: GSM_EINVAL, GSM_ENOMEM.
@@ -118,18 +128,20 @@ int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, in
  *   eps_n   [6][ld]  strain at t_n                       (in)
  *   eps     [6][ld]  strain at t_{n+1}                   (in); the strain is
  *                    interpolated linearly in between
- *   z_n     [6][ld]  internal variables at t_n           (in; deviatoric)
+ *   z_n     [nz][ld] internal variables at t_n           (in): nz = 6 for the
+ *                    Norton law (z, deviatoric), nz = 7 for the Michel-Suquet
+ *                    law (z, then the equivalent plastic strain alpha)
  *   h       step size > 0;  rtol > 0, atol >= 0: error tolerances on the
  *           stresses (and tangents); MATLAB's defaults are 1e-3 and 1e-6
  *   max_substeps  cap on accepted + rejected substeps per voxel (>= 1)
- *   sigma, z [6][ld] (out); tangent [36][ld] dsigma/deps_{n+1} as the full
+ *   sigma [6][ld], z [nz][ld] (out); tangent [36][ld] dsigma/deps_{n+1} as the full
  *           6x6 matrix row-major (not symmetric in general), or NULL
  *   status  [ld] or NULL: bits 0-15 accepted substeps, bits 20-30 rejected
  *           substeps (both saturating), bits 16-19 flags as for gsm_update
  *           (a voxel that reaches max_substeps has bit 18 and keeps the state
  *           of its last accepted substep)
  * Element type double: computed in FP64 whatever the material's precision.
- * The viscoplastic law only (GSM_ENOTSUP for the elastic law).  Arrays as
+ * The viscoplastic laws only (GSM_ENOTSUP for the elastic law).  Arrays as
  * for gsm_update (device or page-locked host memory).  Asynchronous on
  * `stream`.  Errors: GSM_EINVAL, GSM_ENOTSUP, GSM_ECUDA.
  */

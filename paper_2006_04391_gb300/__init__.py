@@ -19,8 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgsm_gb300.so")
 
 GSM_OK, GSM_EINVAL, GSM_ENOMEM, GSM_ECUDA, GSM_ENOTCONV, GSM_ENOTSUP = 0, -1, -2, -3, -4, -5
-GSM_PSI_ELASTIC, GSM_PSI_ELASTIC_VP_DEV = 0, 1
-GSM_PHI_NONE, GSM_PHI_NORTON = 0, 1
+GSM_PSI_ELASTIC, GSM_PSI_ELASTIC_VP_DEV, GSM_PSI_ELASTIC_VP_KIN = 0, 1, 2
+GSM_PHI_NONE, GSM_PHI_NORTON, GSM_PHI_MS_FORCE = 0, 1, 2
 GSM_FP64, GSM_FP32_FP64FIX, GSM_FP32 = 0, 1, 2
 MS_PREC_FP64, MS_PREC_FP32_BULK = 0, 1
 
@@ -178,6 +178,12 @@ def elastic(E, nu, precision=GSM_FP64):
     return gsm_create(GSM_PSI_ELASTIC, GSM_PHI_NONE, (E, nu), precision)
 
 
+def michel_suquet(E, nu, sigma_Y, H, edot0, sigma_d, n):
+    """The paper's Michel-Suquet law (kinematic hardening H, yield sigma_Y); its
+    internal variables are z (6) and alpha; integrated by gsm_update_ode23."""
+    return gsm_create(GSM_PSI_ELASTIC_VP_KIN, GSM_PHI_MS_FORCE, (E, nu, sigma_Y, H, edot0, sigma_d, n))
+
+
 def gsm_destroy(mat):
     if mat.handle:
         load().gsm_destroy(mat.handle)
@@ -187,11 +193,13 @@ def gsm_destroy(mat):
 def gsm_update_ode23(mat, eps_n, eps, z_n, h, sigma, z, tangent=None, status=None, rtol=1e-3, atol=1e-6,
                      max_substeps=100000, stream=None, n_vox=None):
     """Material update by ode23 over the load step (FP64 tensors ``[6, ld]``;
-    tangent ``[36, ld]`` = full dsigma/deps_{n+1} row-major; status ``[ld]``)."""
+    internal variables ``[7, ld]`` (z, alpha) for the Michel-Suquet law; tangent
+    ``[36, ld]`` = full dsigma/deps_{n+1} row-major; status ``[ld]``)."""
     lib = load()
     ld = eps.shape[1]
     n = ld if n_vox is None else int(n_vox)
-    for t, rows in ((eps_n, 6), (eps, 6), (z_n, 6), (sigma, 6), (z, 6), (tangent, 36)):
+    nz = 7 if mat.psi_kind == GSM_PSI_ELASTIC_VP_KIN else 6
+    for t, rows in ((eps_n, 6), (eps, 6), (z_n, nz), (sigma, 6), (z, nz), (tangent, 36)):
         if t is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != ld or not t.is_contiguous()):
             raise ValueError("fields must be contiguous [components, ld] tensors with a common ld")
     rc = lib.gsm_update_ode23(mat.handle, n, _ptr(eps_n), _ptr(eps), _ptr(z_n), ld, float(h), float(rtol), float(atol),

@@ -440,6 +440,28 @@ template <class A> AD_HD Unary<A, FLog<typename A::scalar>> log(const Expr<A>& a
 template <class A> AD_HD Unary<A, FSq<typename A::scalar>> sq(const Expr<A>& a) { return {a.self(), {}}; }
 template <class A> AD_HD PowN<A> pow(const Expr<A>& a, typename A::scalar p) { return PowN<A>(a.self(), p); }
 
+// sqrt whose derivative at 0 is taken as 0: for the norm of a generalized
+// stress whose zero lies inside an elastic domain, where the adjoint that
+// arrives is 0 and 0 * inf must not turn into NaN.
+template <class T> struct FSqrt0 {
+  template <class X> AD_HD X f(const X& x) const { return sqrt_(x); }
+  template <class X> AD_HD X df(const X&, const X& r) const {
+    return value_of(r) > T(0) ? T(0.5) * inv(r) : r * T(0);
+  }
+};
+// (x^+)^m, m >= 1: the power of the positive part (a yield function's overstress).
+template <class T> struct FPosPow {
+  T m;
+  template <class X> AD_HD X f(const X& x) const { return value_of(x) > T(0) ? pow_(x, m) : x * T(0); }
+  template <class X> AD_HD X df(const X& x, const X&) const {
+    return value_of(x) > T(0) ? m * pow_(x, m - T(1)) : x * T(0);
+  }
+};
+template <class A> AD_HD Unary<A, FSqrt0<typename A::scalar>> sqrt0(const Expr<A>& a) { return {a.self(), {}}; }
+template <class A> AD_HD Unary<A, FPosPow<typename A::scalar>> pospow(const Expr<A>& a, typename A::scalar m) {
+  return {a.self(), {m}};
+}
+
 // ---------------------------------------------------------------- leaf packs
 // A heterogeneous, fixed-size set of leaves addressed by a compile-time index:
 // leaf k may carry its own tangent mask (unit seed e_k).

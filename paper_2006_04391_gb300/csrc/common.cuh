@@ -15,17 +15,29 @@ namespace gsm {
 // Material handle behind gsm_handle.
 struct Material {
   int psi_kind, phi_kind, precision;
-  double params[5];
+  double params[8];
   LawParams<double> p64;
   LawParams<float> p32;
 };
 
-inline LawParams<double> make_params(const double* prm, bool norton) {
+// kind: 0 elastic (E, nu); 1 Norton (E, nu, sigma0, edot0, n);
+// 2 Michel-Suquet (E, nu, sigma_Y, H, edot0, sigma_d, n).
+inline LawParams<double> make_params(const double* prm, int kind) {
   LawParams<double> p;
   const double E = prm[0], nu = prm[1];
   p.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   p.mu = E / (2.0 * (1.0 + nu));
-  if (norton) {
+  p.H_kin = 0.0;
+  p.sig_Y = 0.0;
+  if (kind == 2) {
+    const double sY = prm[2], H = prm[3], e0 = prm[4], sd = prm[5], n = prm[6];
+    p.a_phi = 1.0;
+    p.c_phi = 0.0;
+    p.b_Psi = n + 1.0;
+    p.c_Psi = sd * e0 / (n + 1.0) * std::pow(sd, -(n + 1.0));
+    p.H_kin = H;
+    p.sig_Y = sY;
+  } else if (kind == 1) {
     const double s0 = prm[2], e0 = prm[3], n = prm[4];
     p.a_phi = (n + 1.0) / (2.0 * n);
     p.c_phi = s0 * e0 * n / (n + 1.0) * std::pow(e0, -(n + 1.0) / n);
@@ -48,6 +60,8 @@ inline LawParams<float> to_float(const LawParams<double>& p) {
   q.a_phi = (float)p.a_phi;
   q.c_Psi = (float)p.c_Psi;
   q.b_Psi = (float)p.b_Psi;
+  q.H_kin = (float)p.H_kin;
+  q.sig_Y = (float)p.sig_Y;
   return q;
 }
 

@@ -204,6 +204,11 @@ int validate_material(int psi_kind, int phi_kind, const double* prm, int n_param
   } else if (psi_kind == GSM_PSI_ELASTIC_VP_DEV && phi_kind == GSM_PHI_NORTON) {
     if (n_params != 5) return GSM_EINVAL;
     if (!finite_pos(prm[2]) || !finite_pos(prm[3]) || !finite_pos(prm[4])) return GSM_EINVAL;
+  } else if (psi_kind == GSM_PSI_ELASTIC_VP_KIN && phi_kind == GSM_PHI_MS_FORCE) {
+    if (n_params != 7) return GSM_EINVAL;
+    if (!(std::isfinite(prm[2]) && prm[2] >= 0.0) || !(std::isfinite(prm[3]) && prm[3] >= 0.0) ||
+        !finite_pos(prm[4]) || !finite_pos(prm[5]) || !(std::isfinite(prm[6]) && prm[6] >= 1.0))
+      return GSM_EINVAL;
   } else {
     return GSM_EINVAL;
   }
@@ -227,8 +232,8 @@ int gsm_create(gsm_handle* out, int psi_kind, int phi_kind, const double* params
   m->psi_kind = psi_kind;
   m->phi_kind = phi_kind;
   m->precision = precision;
-  for (int i = 0; i < 5; ++i) m->params[i] = i < n_params ? params[i] : 0.0;
-  m->p64 = make_params(params, psi_kind == GSM_PSI_ELASTIC_VP_DEV);
+  for (int i = 0; i < 8; ++i) m->params[i] = i < n_params ? params[i] : 0.0;
+  m->p64 = make_params(params, psi_kind);
   m->p32 = to_float(m->p64);
   *out = reinterpret_cast<gsm_handle>(m);
   return GSM_OK;
@@ -245,6 +250,7 @@ int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, in
   if (n_vox == 0) return GSM_OK;
   const Material& m = *reinterpret_cast<const Material*>(h);
   if (!eps || !sigma) return GSM_EINVAL;
+  if (m.psi_kind == GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;  // force-potential form: gsm_update_ode23
   if (m.psi_kind == GSM_PSI_ELASTIC_VP_DEV && (!z_n || !z)) return GSM_EINVAL;
   if (!(std::isfinite(step_h) && step_h > 0.0)) return GSM_EINVAL;
   // every array may be device memory or page-locked host memory (read and

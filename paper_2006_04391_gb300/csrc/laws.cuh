@@ -27,8 +27,10 @@ template <class T> struct LawParams {
   T lam, mu;      // Lame constants
   T c_phi;        // phi = c_phi * q^a_phi  (see NortonDev)
   T a_phi;
-  T c_Psi;        // force potential Psi = c_Psi * s_A^(2 b_Psi)  (see NortonDev)
+  T c_Psi;        // force potential Psi = c_Psi * s_A^(2 b_Psi)  (see NortonDev, MichelSuquet)
   T b_Psi;
+  T H_kin;        // kinematic hardening modulus H (MichelSuquet)
+  T sig_Y;        // yield stress, K(alpha) = sigma_Y (MichelSuquet)
 };
 
 // Linear elasticity: psi = 1/2 eps^T C eps, no internal variables.
@@ -132,6 +134,46 @@ struct NortonDev {
     p.c_phi *= f;
     const T big = T(sizeof(T) == 4 ? 1e20 : 1e280);
     return p.c_phi > T(1) / big && p.c_phi < big;
+  }
+};
+
+// The paper's full elasto-viscoplastic law (Sec. 3, Eq. michel_suquet_omega and
+// Eq. michel_suquet_psi) with K(alpha) = sigma_Y, the paper's calibration:
+// internal variables y = (z11, z22, g23, g13, g12, alpha), e_vp = P y deviatoric,
+//   psi = 1/2 (eps - P y)^T C (eps - P y) + 1/3 (P y)^T Hv (P y) + sigma_Y alpha,
+//   Hv = diag(H, H, H, H/2, H/2, H/2) (engineering shears: (P y)^T Hv (P y) = H e_vp:e_vp);
+//   Psi(A) = sigma_d edot0/(n+1) ((s_A + A_alpha)^+ / sigma_d)^(n+1) = c_Psi ((s_A + A5)^+)^b_Psi,
+//   s_A^2 = A0^2 + A1^2 - A0 A1 + 3 (A2^2 + A3^2 + A4^2) (von Mises norm of dev A_vp),
+//   b_Psi = n + 1, c_Psi = sigma_d edot0/(n+1) sigma_d^-(n+1).
+// The yield function is not smooth in the dual (dissipation) form, so this
+// law is integrated in its force-potential form only (gsm_update_ode23).
+struct MichelSuquet {
+  static constexpr int NY = 6;
+
+  template <class EP, class YP, class P> AD_HD static auto psi(const EP& e, const YP& y, const P& p) {
+    using ad::get;
+    const auto& y0 = get<0>(y); const auto& y1 = get<1>(y); const auto& y2 = get<2>(y);
+    const auto& y3 = get<3>(y); const auto& y4 = get<4>(y); const auto& al = get<5>(y);
+    using S = typename std::decay_t<decltype(y0)>::scalar;
+    auto a0 = get<0>(e) - y0;
+    auto a1 = get<1>(e) - y1;
+    auto a2 = get<2>(e) + (y0 + y1);
+    auto a3 = get<3>(e) - y2;
+    auto a4 = get<4>(e) - y3;
+    auto a5 = get<5>(e) - y4;
+    auto tr = a0 + a1 + a2;
+    auto el = (p.lam * 0.5) * sq(tr) + p.mu * (sq(a0) + sq(a1) + sq(a2)) + (p.mu * 0.5) * (sq(a3) + sq(a4) + sq(a5));
+    auto kin = (p.H_kin * S(1.0 / 3.0)) * ((sq(y0) + sq(y1) + sq(y0 + y1)) + S(0.5) * (sq(y2) + sq(y3) + sq(y4)));
+    return el + kin + p.sig_Y * al;
+  }
+
+  template <class AP, class P> AD_HD static auto Psi(const AP& A, const P& p) {
+    using ad::get;
+    const auto& a0 = get<0>(A); const auto& a1 = get<1>(A); const auto& a2 = get<2>(A);
+    const auto& a3 = get<3>(A); const auto& a4 = get<4>(A); const auto& a5 = get<5>(A);
+    using S = typename std::decay_t<decltype(a0)>::scalar;
+    auto s2 = (sq(a0) + sq(a1) - a0 * a1) + S(3) * (sq(a2) + sq(a3) + sq(a4));
+    return p.c_Psi * pospow(sqrt0(s2) + a5, p.b_Psi);
   }
 };
 

@@ -234,6 +234,7 @@ int job_setup(Job& j, int N, const uint8_t* phase_dev, int n_phases, const gsm_h
   for (int p = 0; p < n_phases; ++p) {
     const Material* m = reinterpret_cast<const Material*>(laws[p]);
     if (!m) return GSM_EINVAL;
+    if (m->psi_kind == GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;  // the scheme's laws use implicit Euler
     j.tab_host.kind[p] = m->psi_kind;
     j.tab_host.p64[p] = m->p64;
     j.tab_host.p32[p] = m->p32;
@@ -1199,6 +1200,7 @@ extern "C" int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, co
   for (int p = 0; p < n_phases; ++p) {
     const Material* m = reinterpret_cast<const Material*>(laws[p]);
     if (!m) return GSM_EINVAL;
+    if (m->psi_kind == GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;  // implicit-Euler laws only
     tab.kind[p] = m->psi_kind;
     tab.p64[p] = m->p64;
     tab.p32[p] = m->p32;

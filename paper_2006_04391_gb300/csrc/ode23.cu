@@ -18,7 +18,7 @@ constexpr int kOdeBlock = 128;
 // different substep counts, and with one voxel per lane per pass the finished
 // lanes would idle until the slowest voxel of their warp is done (measured:
 // 23.7 of 32 lanes busy; 28.7 -> 31.2 M voxel-updates/s).
-template <bool TAN>
+template <class Law, bool TAN>
 __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld, LawParams<double> p, Step hs,
                                                           Ode23Ctl ctl, const double* __restrict__ epsn,
                                                           const double* __restrict__ eps,
@@ -27,15 +27,17 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
                                                           int32_t* __restrict__ status) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Ode23Voxel<NortonDev, TAN> v;
+  constexpr int NZ = stored_nz<Law>();
+  Ode23Voxel<Law, TAN> v;
   auto start = [&](int64_t k) {
-    double e0[6], e1[6], zi[6];
+    double e0[6], e1[6], zi[NZ];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       e0[c] = __ldg(epsn + c * ld + k);
       e1[c] = __ldg(eps + c * ld + k);
-      zi[c] = __ldg(zn + c * ld + k);
     }
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) zi[c] = __ldg(zn + c * ld + k);
     v.init(p, e0, e1, zi, hs.h);
   };
   if constexpr (TAN) {
@@ -51,13 +53,12 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
         if (!v.done) v.attempt(p, hs, ctl);
       }
       if (active) {
-        double s[6], zo[6], t36[36];
+        double s[6], zo[NZ], t36[36];
         const unsigned st = v.finish(hs.h, s, zo, t36);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          sig[c * ld + k] = s[c];
-          z[c * ld + k] = zo[c];
-        }
+        for (int c = 0; c < 6; ++c) sig[c * ld + k] = s[c];
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) z[c * ld + k] = zo[c];
 #pragma unroll
         for (int c = 0; c < 36; ++c) tan[c * ld + k] = t36[c];
         if (status) status[k] = (int32_t)st;
@@ -71,13 +72,12 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
     if (!have) continue;
     v.attempt(p, hs, ctl);
     if (v.done) {
-      double s[6], zo[6];
+      double s[6], zo[NZ];
       const unsigned st = v.finish(hs.h, s, zo, nullptr);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sig[c * ld + i] = s[c];
-        z[c * ld + i] = zo[c];
-      }
+      for (int c = 0; c < 6; ++c) sig[c * ld + i] = s[c];
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) z[c * ld + i] = zo[c];
       if (status) status[i] = (int32_t)st;
       i += stride;
       have = i < n;
@@ -108,7 +108,7 @@ extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, 
   if (!h || n_vox < 0 || ld < n_vox) return GSM_EINVAL;
   if (n_vox == 0) return GSM_OK;
   const Material& m = *reinterpret_cast<const Material*>(h);
-  if (m.psi_kind != GSM_PSI_ELASTIC_VP_DEV) return GSM_ENOTSUP;
+  if (m.psi_kind != GSM_PSI_ELASTIC_VP_DEV && m.psi_kind != GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;
   if (!eps_n || !eps || !z_n || !sigma || !z) return GSM_EINVAL;
   if (!(std::isfinite(step_h) && step_h > 0.0) || !(rtol > 0.0) || !(atol >= 0.0) || max_substeps < 1)
     return GSM_EINVAL;
@@ -131,12 +131,17 @@ extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, 
   double* zo = static_cast<double*>(out[1]);
   double* to = static_cast<double*>(out[2]);
   int32_t* sto = static_cast<int32_t*>(out[3]);
-  if (to)
-    ode23_kernel<true><<<ode_grid<ode23_kernel<true>>(n_vox), kOdeBlock, 0, s>>>(n_vox, ld, m.p64, hs, ctl, e0, e1,
-                                                                                  zi, so, zo, to, sto);
-  else
-    ode23_kernel<false><<<ode_grid<ode23_kernel<false>>(n_vox), kOdeBlock, 0, s>>>(n_vox, ld, m.p64, hs, ctl, e0,
-                                                                                    e1, zi, so, zo, nullptr, sto);
+  auto launch = [&](auto law) {
+    using Law = decltype(law);
+    if (to)
+      ode23_kernel<Law, true><<<ode_grid<ode23_kernel<Law, true>>(n_vox), kOdeBlock, 0, s>>>(
+          n_vox, ld, m.p64, hs, ctl, e0, e1, zi, so, zo, to, sto);
+    else
+      ode23_kernel<Law, false><<<ode_grid<ode23_kernel<Law, false>>(n_vox), kOdeBlock, 0, s>>>(
+          n_vox, ld, m.p64, hs, ctl, e0, e1, zi, so, zo, nullptr, sto);
+  };
+  if (m.psi_kind == GSM_PSI_ELASTIC_VP_DEV) launch(NortonDev{});
+  else launch(MichelSuquet{});
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GSM_OK : GSM_ECUDA;
 }

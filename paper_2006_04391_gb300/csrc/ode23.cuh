@@ -29,98 +29,151 @@ struct Ode23Ctl {
 // rejected substeps (both saturating), flags in bits 16-19 as elsewhere.
 enum : unsigned { ST_ODE_REJ_SHIFT = 20 };
 
-// psi_y, psi_ye (5x6) and psi_yy (5x5) at (eps, y): one forward-over-reverse
-// sweep with 11 unit directions (6 strain, 5 internal variables).
+// Number of stored internal-variable components of a law: z (6 Voigt
+// entries, z33 = -z11 - z22) plus any further scalars (alpha).
+template <class Law> constexpr int stored_nz() { return Law::NY + 1; }
+
+// psi_y at (eps, y): first-order reverse sweep over the NY internal variables.
 template <class Law>
-AD_HD void psi_y_blocks(const LawParams<double>& p, const double (&eps)[6], const double (&y)[5], double (&g)[5],
-                        double (&Hye)[5][6], double (&Hyy)[5][5]) {
-  ad::SeededPack<ad::Var, double, 11, 0, 6> E;
-  ad::SeededPack<ad::Var, double, 11, 6, 5> Y;
-  ad::seed_unit<decltype(E), double, 0, 6>(E, eps);
-  ad::seed_unit<decltype(Y), double, 6, 5>(Y, y);
+AD_HD void ode_psi_y(const LawParams<double>& p, const double (&eps)[6], const double (&y)[Law::NY],
+                     double (&g)[Law::NY]) {
+  constexpr int NY = Law::NY;
+  EpsCst<double> E;
+  fill_cst(E, eps);
+  ad::UniformPack<ad::Var<double>, NY> Y;
+  ad::For<0, NY>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(Y).v = y[decltype(kc)::value]; });
   auto f = Law::psi(E, Y, p);
   f.fwd();
   f.back(1.0);
-  ad::For<0, 5>::run([&](auto kc) {
+  ad::For<0, NY>::run([&](auto kc) { g[decltype(kc)::value] = ad::get<decltype(kc)::value>(Y).a; });
+}
+
+// sigma = psi_eps at (eps, y).
+template <class Law>
+AD_HD void ode_sigma(const LawParams<double>& p, const double (&eps)[6], const double (&y)[Law::NY],
+                     double (&sig)[6]) {
+  constexpr int NY = Law::NY;
+  ad::UniformPack<ad::Var<double>, 6> E;
+  ad::For<0, 6>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(E).v = eps[decltype(kc)::value]; });
+  ad::UniformPack<ad::Cst<double>, NY> Y;
+  ad::For<0, NY>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(Y).v = y[decltype(kc)::value]; });
+  auto f = Law::psi(E, Y, p);
+  f.fwd();
+  f.back(1.0);
+  ad::For<0, 6>::run([&](auto kc) { sig[decltype(kc)::value] = ad::get<decltype(kc)::value>(E).a; });
+}
+
+// psi_y, psi_ye (NY x 6) and psi_yy (NY x NY) at (eps, y); with SIG also sigma and
+// sigma's blocks psi_ee (6x6), psi_ey (6 x NY).  One forward-over-reverse sweep with
+// 6 + NY unit directions.
+template <class Law, bool SIG>
+AD_HD void ode_blocks(const LawParams<double>& p, const double (&eps)[6], const double (&y)[Law::NY],
+                      double (&g)[Law::NY], double (&Hye)[Law::NY][6], double (&Hyy)[Law::NY][Law::NY],
+                      double (&sig)[6], double (&Cee)[6][6], double (&Cey)[6][Law::NY]) {
+  constexpr int NY = Law::NY, ND = 6 + NY;
+  ad::SeededPack<ad::Var, double, ND, 0, 6> E;
+  ad::SeededPack<ad::Var, double, ND, 6, NY> Y;
+  ad::seed_unit<decltype(E), double, 0, 6>(E, eps);
+  ad::seed_unit<decltype(Y), double, 6, NY>(Y, y);
+  auto f = Law::psi(E, Y, p);
+  f.fwd();
+  f.back(1.0);
+  ad::For<0, NY>::run([&](auto kc) {
     constexpr int a = decltype(kc)::value;
     const auto& ad_ = ad::get<a>(Y).a;
     g[a] = ad_.v;
 #pragma unroll
     for (int j = 0; j < 6; ++j) Hye[a][j] = ad_.d[j];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) Hyy[a][j] = ad_.d[6 + j];
+    for (int j = 0; j < NY; ++j) Hyy[a][j] = ad_.d[6 + j];
   });
+  if constexpr (SIG) {
+    ad::For<0, 6>::run([&](auto kc) {
+      constexpr int i = decltype(kc)::value;
+      const auto& ad_ = ad::get<i>(E).a;
+      sig[i] = ad_.v;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Cee[i][j] = ad_.d[j];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) Cey[i][j] = ad_.d[6 + j];
+    });
+  }
 }
 
 // Psi_A (first order) and Psi_A, Psi_AA (vector mode) of the force potential.
 template <class Law>
-AD_HD void force_a(const LawParams<double>& p, const double (&A)[5], double (&g)[5]) {
-  ad::UniformPack<ad::Var<double>, 5> X;
-  ad::For<0, 5>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(X).v = A[decltype(kc)::value]; });
+AD_HD void force_a(const LawParams<double>& p, const double (&A)[Law::NY], double (&g)[Law::NY]) {
+  constexpr int NY = Law::NY;
+  ad::UniformPack<ad::Var<double>, NY> X;
+  ad::For<0, NY>::run([&](auto kc) { ad::get_mut<decltype(kc)::value>(X).v = A[decltype(kc)::value]; });
   auto f = Law::Psi(X, p);
   f.fwd();
   f.back(1.0);
-  ad::For<0, 5>::run([&](auto kc) { g[decltype(kc)::value] = ad::get<decltype(kc)::value>(X).a; });
+  ad::For<0, NY>::run([&](auto kc) { g[decltype(kc)::value] = ad::get<decltype(kc)::value>(X).a; });
 }
 
 template <class Law>
-AD_HD void force_a_aa(const LawParams<double>& p, const double (&A)[5], double (&g)[5], double (&H)[5][5]) {
-  ad::SeededPack<ad::Var, double, 5, 0, 5> X;
-  ad::seed_unit<decltype(X), double, 0, 5>(X, A);
+AD_HD void force_a_aa(const LawParams<double>& p, const double (&A)[Law::NY], double (&g)[Law::NY],
+                      double (&H)[Law::NY][Law::NY]) {
+  constexpr int NY = Law::NY;
+  ad::SeededPack<ad::Var, double, NY, 0, NY> X;
+  ad::seed_unit<decltype(X), double, 0, NY>(X, A);
   auto f = Law::Psi(X, p);
   f.fwd();
   f.back(1.0);
-  ad::For<0, 5>::run([&](auto kc) {
+  ad::For<0, NY>::run([&](auto kc) {
     constexpr int a = decltype(kc)::value;
     const auto& ad_ = ad::get<a>(X).a;
     g[a] = ad_.v;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) H[a][j] = ad_.d[j];
+    for (int j = 0; j < NY; ++j) H[a][j] = ad_.d[j];
   });
 }
 
-template <bool TAN> struct OdeState {
-  double y[5];
-  double Y[TAN ? 5 : 1][TAN ? 6 : 1];
+template <int NY, bool TAN> struct OdeState {
+  double y[NY];
+  double Y[TAN ? NY : 1][TAN ? 6 : 1];
 };
 
-// Right-hand side at theta = t/h: f = Psi_A(A) and, with TAN,
-// F = Psi_AA(A) dA/deps_{n+1}.
+// Right-hand side at theta = t/h: f = Psi_A(A), A = -psi_y, and with TAN
+// F = Psi_AA(A) dA/deps_{n+1}, dA/deps_{n+1} = -(theta psi_ye + psi_yy Y).
 template <class Law, bool TAN>
 AD_HD void ode_rhs(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
-                   const OdeState<TAN>& s, double (&f)[5], double (&F)[TAN ? 5 : 1][TAN ? 6 : 1]) {
+                   const OdeState<Law::NY, TAN>& s, double (&f)[Law::NY],
+                   double (&F)[TAN ? Law::NY : 1][TAN ? 6 : 1]) {
+  constexpr int NY = Law::NY;
   double et[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
-  double A[5];
+  double A[NY];
   if constexpr (!TAN) {
-    double g[5];
-    psi_y<Law, double>(p, et, s.y, g);
+    double g[NY];
+    ode_psi_y<Law>(p, et, s.y, g);
 #pragma unroll
-    for (int a = 0; a < 5; ++a) A[a] = -g[a];
+    for (int a = 0; a < NY; ++a) A[a] = -g[a];
     force_a<Law>(p, A, f);
   } else {
-    double g[5], Hye[5][6], Hyy[5][5];
-    psi_y_blocks<Law>(p, et, s.y, g, Hye, Hyy);
+    double g[NY], Hye[NY][6], Hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
+    ode_blocks<Law, false>(p, et, s.y, g, Hye, Hyy, sig_, Cee_, Cey_);
 #pragma unroll
-    for (int a = 0; a < 5; ++a) A[a] = -g[a];
-    double H[5][5];
+    for (int a = 0; a < NY; ++a) A[a] = -g[a];
+    double H[NY][NY];
     force_a_aa<Law>(p, A, f, H);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      double dA[5];
+      double dA[NY];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
+      for (int a = 0; a < NY; ++a) {
         double t = theta * Hye[a][k];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) t = fma(Hyy[a][b], s.Y[b][k], t);
+        for (int b = 0; b < NY; ++b) t = fma(Hyy[a][b], s.Y[b][k], t);
         dA[a] = -t;
       }
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
+      for (int a = 0; a < NY; ++a) {
         double t = 0.0;
 #pragma unroll
-        for (int b = 0; b < 5; ++b) t = fma(H[a][b], dA[b], t);
+        for (int b = 0; b < NY; ++b) t = fma(H[a][b], dA[b], t);
         F[a][k] = t;
       }
     }
@@ -130,22 +183,23 @@ AD_HD void ode_rhs(const LawParams<double>& p, const double (&epsn)[6], const do
 // Stress (and with TAN the tangent C = theta psi_ee + psi_ey Y) at theta.
 template <class Law, bool TAN>
 AD_HD void ode_stress(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
-                      const OdeState<TAN>& s, double (&sig)[6], double (&C)[TAN ? 6 : 1][TAN ? 6 : 1]) {
+                      const OdeState<Law::NY, TAN>& s, double (&sig)[6], double (&C)[TAN ? 6 : 1][TAN ? 6 : 1]) {
+  constexpr int NY = Law::NY;
   double et[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
   if constexpr (!TAN) {
-    stress<Law>(p, et, s.y, sig);
+    ode_sigma<Law>(p, et, s.y, sig);
   } else {
-    double Cee[6][6], Cey[6][5], Cye[5][6];
-    psi_blocks<Law>(p, et, s.y, sig, Cee, Cey, Cye);
+    double g_[NY], Hye_[NY][6], Hyy_[NY][NY], Cee[6][6], Cey[6][NY];
+    ode_blocks<Law, true>(p, et, s.y, g_, Hye_, Hyy_, sig, Cee, Cey);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         double t = theta * Cee[i][k];
 #pragma unroll
-        for (int a = 0; a < 5; ++a) t = fma(Cey[i][a], s.Y[a][k], t);
+        for (int a = 0; a < NY; ++a) t = fma(Cey[i][a], s.Y[a][k], t);
         C[i][k] = t;
       }
   }
@@ -165,11 +219,12 @@ AD_HD double scaled_sq(double d, double sc) {
 // as soon as its current one is done, instead of letting the lane wait for
 // the slowest voxel of its warp.
 template <class Law, bool TAN> struct Ode23Voxel {
-  using M56 = double[TAN ? 5 : 1][TAN ? 6 : 1];
+  static constexpr int NY = Law::NY, NZ = stored_nz<Law>();
+  using M56 = double[TAN ? NY : 1][TAN ? 6 : 1];
   using M66 = double[TAN ? 6 : 1][TAN ? 6 : 1];
   double epsn[6], de[6];
-  OdeState<TAN> s;
-  double k1[5];
+  OdeState<NY, TAN> s;
+  double k1[NY];
   M56 K1;
   double sig_old[6];
   M66 C_old;
@@ -178,7 +233,8 @@ template <class Law, bool TAN> struct Ode23Voxel {
   unsigned flags;
   bool last_rejected, done;
 
-  AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[6],
+  // zn: the NZ stored internal variables (z in Voigt order, then alpha, ...)
+  AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[NZ],
                   double h) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -190,9 +246,11 @@ template <class Law, bool TAN> struct Ode23Voxel {
     s.y[2] = zn[3];
     s.y[3] = zn[4];
     s.y[4] = zn[5];
+#pragma unroll
+    for (int a = 5; a < NY; ++a) s.y[a] = zn[a + 1];
     if constexpr (TAN) {
 #pragma unroll
-      for (int a = 0; a < 5; ++a)
+      for (int a = 0; a < NY; ++a)
 #pragma unroll
         for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
     }
@@ -221,11 +279,11 @@ template <class Law, bool TAN> struct Ode23Voxel {
     const bool clip = t + dt >= h;  // the substep that ends the interval ends at h exactly
     if (clip) dt = h - t;
     // stage 2
-    OdeState<TAN> st;
-    double k[5], y3[5], e[5];
+    OdeState<NY, TAN> st;
+    double k[NY], y3[NY], e[NY];
     M56 Kc, Y3, E;
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       st.y[a] = fma(0.5 * dt, k1[a], s.y[a]);
       y3[a] = fma(b1 * dt, k1[a], s.y[a]);
       e[a] = e1 * dt * k1[a];
@@ -240,7 +298,7 @@ template <class Law, bool TAN> struct Ode23Voxel {
     ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc);
     // stage 3
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       st.y[a] = fma(0.75 * dt, k[a], s.y[a]);
       y3[a] = fma(b2 * dt, k[a], y3[a]);
       e[a] = fma(e2 * dt, k[a], e[a]);
@@ -254,7 +312,7 @@ template <class Law, bool TAN> struct Ode23Voxel {
     }
     ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc);
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       y3[a] = fma(b3 * dt, k[a], y3[a]);
       e[a] = fma(e3 * dt, k[a], e[a]);
       if constexpr (TAN)
@@ -267,19 +325,19 @@ template <class Law, bool TAN> struct Ode23Voxel {
     // last stage at the new point (k1 of the next step)
     const double tn1 = clip ? h : t + dt;
     const double th1 = clip ? 1.0 : tn1 * inv_h;
-    OdeState<TAN> s3;
+    OdeState<NY, TAN> s3;
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       s3.y[a] = y3[a];
       if constexpr (TAN)
 #pragma unroll
         for (int c = 0; c < 6; ++c) s3.Y[a][c] = Y3[a][c];
     }
-    double k4[5];
+    double k4[NY];
     M56 K4;
     ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4);
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       e[a] = fma(e4 * dt, k4[a], e[a]);
       if constexpr (TAN)
 #pragma unroll
@@ -289,9 +347,9 @@ template <class Law, bool TAN> struct Ode23Voxel {
     double s_hi[6], s_lo[6];
     M66 C_hi, C_lo;
     ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
-    OdeState<TAN> s2;
+    OdeState<NY, TAN> s2;
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < NY; ++a) {
       s2.y[a] = y3[a] - e[a];
       if constexpr (TAN)
 #pragma unroll
@@ -319,7 +377,7 @@ template <class Law, bool TAN> struct Ode23Voxel {
     if (err <= 1.0) {
       t = tn1;
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
+      for (int a = 0; a < NY; ++a) {
         s.y[a] = y3[a];
         k1[a] = k4[a];
         if constexpr (TAN)
@@ -349,7 +407,7 @@ template <class Law, bool TAN> struct Ode23Voxel {
   // outputs at the end of the step (sig_old is the stress of the last accepted
   // substep); C36: row-major 6x6 (the tangent of an explicit integrator is
   // not symmetric in general), written only with TAN and when non-NULL
-  AD_HD unsigned finish(double h, double (&sig)[6], double (&z)[6], double* C36) const {
+  AD_HD unsigned finish(double h, double (&sig)[6], double (&z)[NZ], double* C36) const {
 #pragma unroll
     for (int i = 0; i < 6; ++i) sig[i] = sig_old[i];
     if constexpr (TAN) {
@@ -365,6 +423,8 @@ template <class Law, bool TAN> struct Ode23Voxel {
     z[3] = s.y[2];
     z[4] = s.y[3];
     z[5] = s.y[4];
+#pragma unroll
+    for (int a = 5; a < NY; ++a) z[a + 1] = s.y[a];
     unsigned st = flags;
     if (t >= h && !(flags & ST_CAP)) st |= ST_CONVERGED;
     if (!finite64(sig[0]) || !finite64(z[0])) st |= ST_NONFINITE;
@@ -378,8 +438,8 @@ template <class Law, bool TAN> struct Ode23Voxel {
 // states per lane itself).
 template <class Law, bool TAN>
 AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
-                           const double (&zn)[6], const Step& hs, const Ode23Ctl& ctl, double (&sig)[6],
-                           double (&z)[6], double* C36) {
+                           const double (&zn)[stored_nz<Law>()], const Step& hs, const Ode23Ctl& ctl,
+                           double (&sig)[6], double (&z)[stored_nz<Law>()], double* C36) {
   Ode23Voxel<Law, TAN> v;
   v.init(p, epsn, eps1, zn, hs.h);
   while (!v.done) v.attempt(p, hs, ctl);

@@ -9,12 +9,34 @@
 
 using namespace gsm;
 
+// ode23 update, kind 1 (Norton, params E, nu, sigma0, edot0, n) or 2
+// (Michel-Suquet, params E, nu, sigma_Y, H, edot0, sigma_d, n); AoS eps_n,
+// eps [n][6], z_n and z [n][nz] (nz = 6 or 7); tangent [n][36] or NULL.
+template <class Law>
+void run_ode23(const LawParams<double>& p, int64_t n, const double* eps_n, const double* eps, const double* zn,
+               const Step& hs, const Ode23Ctl& ctl, double* sig, double* z, double* tan, int32_t* status) {
+  constexpr int NZ = stored_nz<Law>();
+  for (int64_t i = 0; i < n; ++i) {
+    double e0[6], e1[6], zi[NZ], s[6], zo[NZ];
+    for (int c = 0; c < 6; ++c) {
+      e0[c] = eps_n[6 * i + c];
+      e1[c] = eps[6 * i + c];
+    }
+    for (int c = 0; c < NZ; ++c) zi[c] = zn[NZ * i + c];
+    unsigned st = tan ? voxel_ode23<Law, true>(p, e0, e1, zi, hs, ctl, s, zo, tan + 36 * i)
+                      : voxel_ode23<Law, false>(p, e0, e1, zi, hs, ctl, s, zo, nullptr);
+    for (int c = 0; c < 6; ++c) sig[6 * i + c] = s[c];
+    for (int c = 0; c < NZ; ++c) z[NZ * i + c] = zo[c];
+    status[i] = (int32_t)st;
+  }
+}
+
 extern "C" {
 
 // params = {E, nu, sigma0, edot0, n}; fields AoS [n][6]; tangent [n][21] or NULL.
 int host_update(int mode, const double* prm, int64_t n, const double* eps, const double* zn, double h,
                 double* sig, double* z, double* tan, int32_t* status) {
-  const LawParams<double> p = make_params(prm, true);
+  const LawParams<double> p = make_params(prm, 1);
   const LawParams<float> pf = to_float(p);
   for (int64_t i = 0; i < n; ++i) {
     double e[6], zi[6], s[6], zo[6];
@@ -31,31 +53,20 @@ int host_update(int mode, const double* prm, int64_t n, const double* eps, const
   return 0;
 }
 
-// ode23 update (AoS [n][6]; tangent [n][36] or NULL; status [n]).
-int host_update_ode23(const double* prm, int64_t n, const double* eps_n, const double* eps, const double* zn,
-                      double h, double rtol, double atol, int max_steps, double* sig, double* z, double* tan,
-                      int32_t* status) {
-  const LawParams<double> p = make_params(prm, true);
+int host_update_ode23(int kind, const double* prm, int64_t n, const double* eps_n, const double* eps,
+                      const double* zn, double h, double rtol, double atol, int max_steps, double* sig, double* z,
+                      double* tan, int32_t* status) {
+  const LawParams<double> p = make_params(prm, kind);
   const Step hs = make_step(h);
   const Ode23Ctl ctl{rtol, atol, max_steps};
-  for (int64_t i = 0; i < n; ++i) {
-    double e0[6], e1[6], zi[6], s[6], zo[6];
-    for (int c = 0; c < 6; ++c) {
-      e0[c] = eps_n[6 * i + c];
-      e1[c] = eps[6 * i + c];
-      zi[c] = zn[6 * i + c];
-    }
-    unsigned st = tan ? voxel_ode23<NortonDev, true>(p, e0, e1, zi, hs, ctl, s, zo, tan + 36 * i)
-                      : voxel_ode23<NortonDev, false>(p, e0, e1, zi, hs, ctl, s, zo, nullptr);
-    for (int c = 0; c < 6; ++c) { sig[6 * i + c] = s[c]; z[6 * i + c] = zo[c]; }
-    status[i] = (int32_t)st;
-  }
+  if (kind == 1) run_ode23<NortonDev>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  else run_ode23<MichelSuquet>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
   return 0;
 }
 
 // AD derivatives of the shipped potentials at one point.
 void host_psi_derivs(const double* prm, const double* eps, const double* y, double* g, double* H) {
-  const LawParams<double> p = make_params(prm, true);
+  const LawParams<double> p = make_params(prm, 1);
   double e[6], yy[5], gg[5], HH[5][5];
   for (int c = 0; c < 6; ++c) e[c] = eps[c];
   for (int a = 0; a < 5; ++a) yy[a] = y[a];
@@ -64,7 +75,7 @@ void host_psi_derivs(const double* prm, const double* eps, const double* y, doub
 }
 
 void host_phi_derivs(const double* prm, const double* v, double* g, double* H) {
-  const LawParams<double> p = make_params(prm, true);
+  const LawParams<double> p = make_params(prm, 1);
   double vv[5], gg[5], HH[5][5];
   for (int a = 0; a < 5; ++a) vv[a] = v[a];
   phi_v_vv<NortonDev>(p, vv, gg, HH);
@@ -73,7 +84,7 @@ void host_phi_derivs(const double* prm, const double* v, double* g, double* H) {
 
 void host_psi_blocks(const double* prm, const double* eps, const double* y, double* sig, double* Cee,
                      double* Cey) {
-  const LawParams<double> p = make_params(prm, true);
+  const LawParams<double> p = make_params(prm, 1);
   double e[6], yy[5], s[6], A[6][6], B[6][5], Ct[5][6];
   for (int c = 0; c < 6; ++c) e[c] = eps[c];
   for (int a = 0; a < 5; ++a) yy[a] = y[a];

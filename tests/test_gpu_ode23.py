@@ -107,3 +107,66 @@ def test_ode23_degenerate_and_invalid(gsm):
         gsm.gsm_update_ode23(mat, t, t, t, 0.1, t.clone(), t.clone(), rtol=0.0)
     with pytest.raises(gsm.GsmError):
         gsm.gsm_update_ode23(gsm.elastic(70.0, 0.3), t, t, t, 0.1, t.clone(), t.clone())
+
+
+def run_ms(G, mat, en, e, zn7, h, tangent=False, ld=None):
+    import torch
+    n = e.shape[0]
+    ld = ld or n
+    E0, E1, Z0 = soa(en, ld), soa(e, ld), soa(zn7, ld)
+    sig = torch.full_like(E1, float("nan"))
+    z = torch.full((7, ld), float("nan"), dtype=torch.float64, device="cuda")
+    tan = torch.full((36, ld), float("nan"), dtype=torch.float64, device="cuda") if tangent else None
+    st = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    G.gsm_update_ode23(mat, E0, E1, Z0, h, sig, z, tan, st, n_vox=n)
+    torch.cuda.synchronize()
+    out = [sig.cpu().numpy()[:, :n].T, z.cpu().numpy()[:, :n].T, st.cpu().numpy()[:n]]
+    if tangent:
+        out.append(tan.cpu().numpy()[:, :n].T)
+    return out
+
+
+@pytest.mark.parametrize("tangent", [False, True])
+def test_michel_suquet_matches_oracle(gsm, tangent):
+    """The paper's Michel-Suquet law (aluminium of the metal-matrix composite:
+    kinematic hardening, yield, n = 3.6) against the oracle's hand-derived ode23."""
+    prm = synth.ALUMINIUM_MS
+    n = 4096 + 37
+    en, e, zn6 = synth.ode23_batch(n, seed=40 + int(tangent))
+    alpha_n = np.random.default_rng(5).uniform(0.0, 0.01, n)
+    zn7 = np.concatenate([zn6, alpha_n[:, None]], axis=1)
+    res = run_ms(gsm, gsm.michel_suquet(*prm), en, e, zn7, 0.1, tangent, ld=n + 3)
+    ref = O.update_ode23(prm, en, e, zn6, 0.1, tangent=tangent, info=True, kind=O.KIND_MICHEL_SUQUET,
+                         alpha_n=alpha_n)
+    sig, z, st = res[:3]
+    assert np.all((st >> 16) & 1)
+    rel = np.abs(sig - ref[0]).max(1) / np.abs(ref[0]).max(1)
+    relz = np.abs(z[:, :6] - ref[1]).max(1) / np.maximum(np.abs(ref[1] - zn6).max(1), 1e-300)
+    da = np.abs(z[:, 6] - ref[2])
+    tight = (rel < 1e-10) & (relz < 1e-10) & (da <= 1e-10 * np.maximum(ref[2] - alpha_n, 1e-300) + 1e-18)
+    if tangent:
+        C2 = ref[3].reshape(-1, 36)
+        tight &= np.abs(res[3] - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98
+    assert np.all(np.abs(sig - ref[0]) <= 10 * (1e-3 * np.abs(ref[0]).max(1, keepdims=True) + 1e-6))
+    assert np.all(z[:, 6] >= alpha_n)
+
+
+def test_michel_suquet_without_yield_and_hardening_is_norton(gsm):
+    en, e, zn = synth.ode23_batch(2048, seed=8)
+    s1, z1, st1 = run(gsm, gsm.norton(70.0, 0.3, 0.1, 1.0, 5.0), en, e, zn, 0.1)
+    zn7 = np.concatenate([zn, np.zeros((2048, 1))], axis=1)
+    s2, z2, st2 = run_ms(gsm, gsm.michel_suquet(70.0, 0.3, 0.0, 0.0, 1.0, 0.1, 5.0), en, e, zn7, 0.1)
+    same = (st1 & 0xFFFF) == (st2 & 0xFFFF)
+    assert same.mean() > 0.98
+    assert np.max(np.abs(s1 - s2)[same] / np.abs(s1[same]).max(1, keepdims=True)) < 1e-10
+
+
+def test_michel_suquet_is_refused_by_the_implicit_paths(gsm):
+    import torch
+    mat = gsm.michel_suquet(*synth.ALUMINIUM_MS)
+    t = torch.zeros(6, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update(mat, t, t, 0.1, t.clone(), t.clone())
+    with pytest.raises(gsm.GsmError):
+        gsm.ms_create(torch.zeros(4, 4, 4, dtype=torch.uint8).cuda(), [mat])

@@ -139,14 +139,16 @@ def test_host_solver_small_trial_states(hlib, case, mode):
             assert np.all(np.abs(z - z2).max(1) <= bound)
 
 
-def _ode23_host(hlib, prm, en, e, zn, h, rtol, atol, tangent):
+def _ode23_host(hlib, prm, en, e, zn, h, rtol, atol, tangent, kind=1):
     n = e.shape[0]
-    sig, z = np.empty((n, 6)), np.empty((n, 6))
+    nz = zn.shape[1]
+    sig, z = np.empty((n, 6)), np.empty((n, nz))
     st = np.empty(n, dtype=np.int32)
     C = np.empty((n, 36)) if tangent else None
-    hlib.host_update_ode23(P(np.asarray(prm, dtype=float)), ctypes.c_int64(n), P(en), P(e), P(zn), ctypes.c_double(h),
-                           ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(100000), P(sig), P(z),
-                           P(C) if tangent else None, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    prm = np.asarray(list(prm) + [0.0] * (7 - len(prm)), dtype=float)
+    hlib.host_update_ode23(kind, P(prm), ctypes.c_int64(n), P(en), P(e), P(np.ascontiguousarray(zn)),
+                           ctypes.c_double(h), ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(100000),
+                           P(sig), P(z), P(C) if tangent else None, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return sig, z, C, st
 
 
@@ -173,3 +175,28 @@ def test_host_ode23_matches_oracle(hlib, tangent, n_exp, rtol, atol):
         tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
     assert tight.mean() >= 0.98
     assert np.all(np.abs(sig - out[0]) <= 10 * (rtol * np.abs(out[0]).max(1, keepdims=True) + atol))
+
+
+@pytest.mark.parametrize("tangent", [False, True])
+def test_host_ode23_michel_suquet_matches_oracle(hlib, tangent):
+    """The paper's Michel-Suquet law (kinematic hardening, yield) through the AD
+    ode23 update against the oracle's hand-derived one; z and alpha stored as
+    7 components."""
+    prm = synth.ALUMINIUM_MS
+    en, e, zn6 = synth.ode23_batch(400, seed=21 + int(tangent))
+    alpha_n = np.random.default_rng(3).uniform(0.0, 0.01, 400)
+    zn = np.concatenate([zn6, alpha_n[:, None]], axis=1)
+    sig, z, C, st = _ode23_host(hlib, prm, en, e, zn, 0.1, 1e-3, 1e-6, tangent, kind=2)
+    out = O.update_ode23(prm, en, e, zn6, 0.1, tangent=tangent, info=True, kind=O.KIND_MICHEL_SUQUET,
+                         alpha_n=alpha_n)
+    assert np.all((st >> 16) & 1) and np.all(out[-1][:, 2] == 1)
+    rel = np.abs(sig - out[0]).max(1) / np.abs(out[0]).max(1)
+    relz = np.abs(z[:, :6] - out[1]).max(1) / np.maximum(np.abs(out[1] - zn6).max(1), 1e-300)
+    rela = np.abs(z[:, 6] - out[2]) / np.maximum(np.abs(out[2] - alpha_n), 1e-300)
+    tight = (rel < 1e-10) & (relz < 1e-10) & ((rela < 1e-10) | (np.abs(z[:, 6] - out[2]) < 1e-18))
+    if tangent:
+        C2 = out[3].reshape(-1, 36)
+        tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98
+    assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))
+    assert np.all(z[:, 6] >= alpha_n)  # alpha never decreases

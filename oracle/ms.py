@@ -107,21 +107,45 @@ def equilibrium_error(sig_hat, mean_sig, N, floor):
     return num / den
 
 
-def material(eps, z_n, phase, laws, h, tangent=False):
-    """One material evaluation of every voxel: laws[p] = (kind, params) for phase p."""
+def material(eps, z_n, phase, laws, h, tangent=False, eps_n=None, ode=None):
+    """One material evaluation of every voxel: laws[p] = (kind, params) for phase p.
+
+    Implicit Euler (Sec. 4.1) unless ``ode`` = (rtol, atol): then the ode23
+    update of the force-potential form over the step (Sec. 4.3) from the
+    strain eps_n of the previous step; z_n has 7 columns there (z, alpha)."""
     n = eps.shape[0]
+    nz = z_n.shape[1]
     sig = np.empty((n, 6))
-    z = np.empty((n, 6))
+    z = np.empty((n, nz))
     Ct = np.empty((n, 6, 6)) if tangent else None
     for p, (kind, params) in enumerate(laws):
         idx = np.nonzero(phase == p)[0]
         if idx.size == 0:
             continue
-        out = M.update(kind, params, eps[idx], z_n[idx], h, tangent=tangent)
-        sig[idx] = out[0]
-        z[idx] = out[1]
-        if tangent:
-            Ct[idx] = out[2]
+        if ode is None or kind == M.KIND_ELASTIC:
+            if kind == M.KIND_MICHEL_SUQUET:
+                raise ValueError("the Michel-Suquet law needs the ode23 update")
+            out = M.update(kind, params, eps[idx], z_n[idx, :6], h, tangent=tangent)
+            sig[idx] = out[0]
+            z[idx, :6] = out[1]
+            if nz > 6:
+                z[idx, 6:] = z_n[idx, 6:]
+            if tangent:
+                Ct[idx] = out[2]
+        else:
+            kw = {"alpha_n": z_n[idx, 6]} if kind == M.KIND_MICHEL_SUQUET else {}
+            out = M.update_ode23(params, eps_n[idx], eps[idx], z_n[idx, :6], h, rtol=ode[0], atol=ode[1],
+                                 tangent=tangent, kind=kind, **kw)
+            sig[idx] = out[0]
+            z[idx, :6] = out[1]
+            k = 2
+            if kind == M.KIND_MICHEL_SUQUET:
+                z[idx, 6] = out[2]
+                k = 3
+            elif nz > 6:
+                z[idx, 6:] = z_n[idx, 6:]
+            if tangent:
+                Ct[idx] = out[k]
     return (sig, z, Ct) if tangent else (sig, z)
 
 
@@ -157,7 +181,7 @@ def reference_stiffness(lam0, mu0):
 
 def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
           eps0=None, zn0=None, E_prev0=None, record=False, stress_mask=None, Sigma_target=None,
-          ref_update=False):
+          ref_update=False, ode=None):
     """Load-history solve of the basic scheme.
 
     phase : (N, N, N) uint8 phase ids, voxel (i, j, k) with k fastest.
@@ -175,6 +199,10 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     ref_update   : adjust the reference medium at the start of every load step
                    to the tangents of a material evaluation at the predicted
                    strain (Sec. 3), instead of the fixed elastic reference.
+    ode          : None (implicit Euler) or (rtol, atol): the laws integrate the
+                   force-potential form over each step by ode23 from the strain
+                   of the previous step (Sec. 4.3); the internal variables then
+                   have 7 columns (z, alpha) when a phase is a Michel-Suquet law.
 
     Returns dict with Sigma (n_steps, 6), iters (n_steps,), errors (list per
     step), eps and z (N^3, 6) at the end, and the per-step (eps, z) history if
@@ -187,7 +215,9 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     lam0, mu0 = reference_medium(laws)
     loads = np.asarray(loads, dtype=np.float64).reshape(-1, 6)
     eps = np.zeros((nvox, 6)) if eps0 is None else np.array(eps0, dtype=np.float64).reshape(nvox, 6)
-    z_n = np.zeros((nvox, 6)) if zn0 is None else np.array(zn0, dtype=np.float64).reshape(nvox, 6)
+    nz = 7 if any(k == M.KIND_MICHEL_SUQUET for k, _ in laws) else 6
+    z_n = np.zeros((nvox, nz)) if zn0 is None else np.array(zn0, dtype=np.float64).reshape(nvox, nz)
+    eps_prev = None
     E_prev = np.zeros(6) if E_prev0 is None else np.asarray(E_prev0, dtype=np.float64)
     mask = np.zeros(6, dtype=bool) if stress_mask is None else np.asarray(stress_mask, dtype=bool)
     S_t = np.zeros((loads.shape[0], 6)) if Sigma_target is None else np.asarray(Sigma_target, float).reshape(-1, 6)
@@ -195,11 +225,12 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
     E_mean = E_prev.copy()                          # the current macroscopic strain
     Sigma, iters, errors, hist, Es, refs = [], [], [], [], [], []
     for step, (E_k, h) in enumerate(zip(loads, hs)):
+        eps_prev = eps.copy()  # the strain at t_n of every voxel (the ode23 update integrates from it)
         E_start = np.where(mask, E_mean, E_k)
         eps = eps + (E_start - E_mean)[None, :]
         E_mean = E_start.copy()
         if ref_update:
-            _, _, Ct = material(eps, z_n, ph, laws, h, tangent=True)
+            _, _, Ct = material(eps, z_n, ph, laws, h, tangent=True, eps_n=eps_prev, ode=ode)
             lam0, mu0 = reference_from_tangents(Ct)
         refs.append((lam0, mu0))
         floor = mu0 * 1e-6
@@ -208,7 +239,7 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
         errs = []
         n_eval = 0
         while True:
-            sig, z = material(eps, z_n, ph, laws, h)
+            sig, z = material(eps, z_n, ph, laws, h, eps_n=eps_prev, ode=ode)
             n_eval += 1
             sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
             mean_sig = sig.mean(axis=0)

@@ -209,6 +209,16 @@ typedef struct ms_load {
                                  reference medium to the tangents of a material
                                  evaluation at the predicted strain (Sec. 3); 0: the
                                  fixed elastic reference                               */
+  int integrator;             /* 0: the implicit-Euler update (gsm_update) of every
+                                 phase; 1: the force-potential form integrated over
+                                 each load step by ode23 (gsm_update_ode23) from the
+                                 voxel's strain at t_n to the current iterate; needed
+                                 for GSM_PSI_ELASTIC_VP_KIN phases; FP64 only           */
+  double ode_rtol, ode_atol;  /* integrator 1: stress-error tolerances (rtol > 0,
+                                 atol >= 0); keep them well below `tol`: an update
+                                 that is not converged to better than the equilibrium
+                                 tolerance stalls the fixed point                      */
+  int ode_max_substeps;       /* integrator 1: attempts per voxel and step (>= 1)     */
 } ms_load;
 
 typedef struct ms_state {
@@ -252,8 +262,12 @@ size_t ms_workspace_bytes(const ms_problem* prob);
  * (fresh start, internal fields); otherwise state->eps / state->z are device
  * [6][N^3] FP64 arrays used as the solver's fields (read when resume = 1,
  * always written back).  Synchronous: reads one FP64 residual per iteration.
- * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTCONV (some step hit max_iter; the
- * result is still filled in).
+ * A problem with GSM_PSI_ELASTIC_VP_KIN phases keeps its seventh internal
+ * variable (the accumulated plastic strain) inside the context: it starts
+ * fresh only (resume = 1 gives GSM_ENOTSUP).
+ * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTSUP (integrator 1 with a precision
+ * other than MS_PREC_FP64, a VP_KIN phase with integrator 0), GSM_ENOTCONV
+ * (some step hit max_iter; the result is still filled in).
  */
 int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result);
 
@@ -276,8 +290,9 @@ typedef struct ms_tape* ms_tape_handle;
  * checkpoints (eps_k, z_{k-1}) of every step on the device (2 * 6 * N^3
  * doubles per step) plus adjoint work arrays (53 * N^3 doubles).  The tape
  * refers to the context, which must outlive it.  Prescribed macroscopic
- * strains and the fixed reference medium only (stress_mask = 0, ref_update =
- * 0; GSM_ENOTSUP otherwise).  Errors as ms_run. */
+ * strains, the fixed reference medium and the implicit-Euler update only
+ * (stress_mask = 0, ref_update = 0, integrator = 0; GSM_ENOTSUP otherwise).
+ * Errors as ms_run. */
 int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_handle* tape);
 
 /* ms_adjoint -- dJ/d(E, sigma0, n) of the Norton phase `phase_id` for the

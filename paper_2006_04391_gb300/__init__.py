@@ -51,7 +51,9 @@ class ms_load(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("E", ctypes.POINTER(ctypes.c_double)),
                 ("h", ctypes.POINTER(ctypes.c_double)), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("forced_iters", ctypes.POINTER(ctypes.c_int32)), ("switch_tol", ctypes.c_double),
-                ("stress_mask", ctypes.c_int), ("Sigma", ctypes.POINTER(ctypes.c_double)), ("ref_update", ctypes.c_int)]
+                ("stress_mask", ctypes.c_int), ("Sigma", ctypes.POINTER(ctypes.c_double)), ("ref_update", ctypes.c_int),
+                ("integrator", ctypes.c_int), ("ode_rtol", ctypes.c_double), ("ode_atol", ctypes.c_double),
+                ("ode_max_substeps", ctypes.c_int)]
 
 
 class ms_state(ctypes.Structure):
@@ -264,7 +266,8 @@ def _mask_bits(stress_mask):
     return sum(1 << c for c, b in enumerate(stress_mask) if b)
 
 
-def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=None, Sigma=None, ref_update=False):
+def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=None, Sigma=None, ref_update=False,
+                 ode=None):
     E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
     hs = np.ascontiguousarray(np.asarray(hs, dtype=np.float64).reshape(-1))
     n = E.shape[0]
@@ -283,7 +286,9 @@ def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=Non
                  hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
                  f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if f is not None else None, float(switch_tol),
                  _mask_bits(stress_mask), S.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if S is not None else None,
-                 1 if ref_update else 0)
+                 1 if ref_update else 0, 0 if ode is None else 1,
+                 float(ode[0]) if ode is not None else 1e-3, float(ode[1]) if ode is not None else 1e-6,
+                 int(ode[2]) if ode is not None and len(ode) > 2 else 100000)
     return ld, keep, n
 
 
@@ -298,12 +303,14 @@ def _result_struct(n):
 
 
 def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=None, resume=False,
-           E_prev=None, switch_tol=0.0, check=True, stress_mask=None, Sigma=None, ref_update=False):
+           E_prev=None, switch_tol=0.0, check=True, stress_mask=None, Sigma=None, ref_update=False, ode=None):
     """Solve a load history.  Returns dict(Sigma, iters, final_error, fp32_iters, total_iters, E,
     reference, rc).  stress_mask: 6 booleans (or bits) of the macroscopic components whose stress
-    (Sigma, default 0) is prescribed; ref_update: per-step reference medium from tangents."""
+    (Sigma, default 0) is prescribed; ref_update: per-step reference medium from tangents;
+    ode: None (implicit Euler) or (rtol, atol[, max_substeps]) for the ode23 update over each step."""
     lib = load()
-    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask, Sigma, ref_update)
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask, Sigma, ref_update,
+                               ode)
     res, out = _result_struct(n)
     st = None
     if eps is not None or z is not None:

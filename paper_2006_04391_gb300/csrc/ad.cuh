@@ -444,7 +444,9 @@ template <class A> AD_HD PowN<A> pow(const Expr<A>& a, typename A::scalar p) { r
 // stress whose zero lies inside an elastic domain, where the adjoint that
 // arrives is 0 and 0 * inf must not turn into NaN.
 template <class T> struct FSqrt0 {
-  template <class X> AD_HD X f(const X& x) const { return sqrt_(x); }
+  // a forward tangent carried through x = 0 stays 0 (sqrt_ of a tangent type
+  // would divide it by 2 sqrt(0))
+  template <class X> AD_HD X f(const X& x) const { return value_of(x) > T(0) ? sqrt_(x) : x * T(0); }
   template <class X> AD_HD X df(const X&, const X& r) const {
     return value_of(r) > T(0) ? T(0.5) * inv(r) : r * T(0);
   }

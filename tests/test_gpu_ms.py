@@ -21,7 +21,12 @@ pytestmark = pytest.mark.gpu
 def gpu_laws(G, laws):
     out = []
     for kind, prm in laws:
-        out.append(G.norton(*prm) if kind == O.KIND_NORTON else G.elastic(*prm))
+        if kind == O.KIND_NORTON:
+            out.append(G.norton(*prm))
+        elif kind == O.KIND_MICHEL_SUQUET:
+            out.append(G.michel_suquet(*prm))
+        else:
+            out.append(G.elastic(*prm))
     return out
 
 
@@ -219,4 +224,109 @@ def test_taped_run_rejects_mixed_conditions(gsm):
     import ctypes
     th = ctypes.c_void_p()
     assert lib.ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th)) == -5
+    gsm.ms_destroy(ctx)
+
+
+# ------------------------------------------------ ode23 laws inside the scheme
+
+ODE = (1e-8, 1e-11)
+
+
+@pytest.mark.parametrize("kind,prm", [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS)])
+def test_ode23_scheme_homogeneous_grid(gsm, kind, prm):
+    """A homogeneous grid is one voxel integrated from eps_{k-1} to eps_k by
+    ode23 each step: the GPU scheme gives the oracle's history."""
+    import torch
+    ph = np.zeros((6, 6, 6), dtype=np.uint8)
+    loads = synth.ramp(3, [0.004, -0.001, 0.0, 0.0, 0.002, 0.0])
+    ref = OMS.solve(ph, [(kind, prm)], loads, [0.1] * 3, tol=1e-12, ode=(1e-6, 1e-9))
+    z = torch.zeros(6, 216, dtype=torch.float64, device="cuda")
+    eps = torch.zeros(6, 216, dtype=torch.float64, device="cuda")
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, [(kind, prm)]), loads, [0.1] * 3, tol=1e-12,
+                       ode=(1e-6, 1e-9), eps=eps, z=z)
+    assert out["rc"] == 0 and np.all(out["iters"] == ref["iters"])
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-10
+    assert np.allclose(z.cpu().numpy().T, ref["z"][:, :6], rtol=1e-9, atol=1e-14)
+
+
+def test_ode23_norton_composite_iteration_matched(gsm):
+    """Norton matrix integrated by ode23, 12^3 sphere composite, 3 steps, the
+    oracle's evaluation counts: the GPU gives the oracle's Sigma_k and fields.
+    The adaptive control may take a different accept/reject decision in a few
+    voxels whose error estimate sits at the threshold (each such voxel's
+    stress then differs by about rtol |sigma|), hence 1e-9 rather than the
+    1e-10 of the implicit-Euler scheme."""
+    import torch
+    ph = synth.sphere_phase(12, 0.2)
+    laws = [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    loads = synth.ramp(3, [0.006, 0, 0, 0, 0, 0])
+    forced = [40, 40, 40]
+    ref = OMS.solve(ph, laws, loads, [0.1] * 3, forced_iters=forced, ode=ODE)
+    eps = torch.zeros(6, 12 ** 3, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(eps)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.1] * 3, forced_iters=forced,
+                       ode=ODE, eps=eps, z=z)
+    assert np.all(out["iters"] == forced)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-9
+    assert rel(eps.cpu().numpy().T, ref["eps"]) < 1e-8
+    assert rel(z.cpu().numpy().T, ref["z"][:, :6]) < 1e-7
+
+
+def test_ode23_michel_suquet_composite_mixed_iteration_matched(gsm):
+    """The paper's metal-matrix composite (Michel-Suquet aluminium, elastic
+    alumina) under uniaxial stress with the per-step reference medium from the
+    ode23 tangents, the oracle's evaluation counts."""
+    import torch
+    ph = synth.sphere_phase(10, 0.2)
+    laws = [(O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS), (O.KIND_ELASTIC, synth.ALUMINA)]
+    loads = synth.ramp(2, [0.003, 0, 0, 0, 0, 0])
+    forced = [30, 30]
+    ref = OMS.solve(ph, laws, loads, [0.5, 0.5], forced_iters=forced, stress_mask=UNIAXIAL, ref_update=True, ode=ODE)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.5, 0.5], forced_iters=forced,
+                       stress_mask=UNIAXIAL, ref_update=True, ode=ODE)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-9
+    assert rel(out["E"], ref["E"]) < 1e-9
+    assert np.allclose(out["reference"], ref["reference"], rtol=1e-9, atol=0)
+
+
+def test_ode23_michel_suquet_free_run(gsm):
+    """Free run to tol of the same composite (8^3): converges, the lateral
+    stresses vanish, and Sigma agrees with the oracle's free run to O(tol)."""
+    import torch
+    ph = synth.sphere_phase(8, 0.2)
+    laws = [(O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS), (O.KIND_ELASTIC, synth.ALUMINA)]
+    loads = synth.ramp(2, [0.003, 0, 0, 0, 0, 0])
+    ref = OMS.solve(ph, laws, loads, [0.5, 0.5], tol=1e-8, max_iter=5000, stress_mask=UNIAXIAL, ode=ODE)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.5, 0.5], tol=1e-8, max_iter=5000,
+                       stress_mask=UNIAXIAL, ode=ODE)
+    assert out["rc"] == 0
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-6
+    assert np.max(np.abs(out["Sigma"][:, 1:])) < 1e-7 * np.max(np.abs(out["Sigma"][:, 0]))
+
+
+def test_ode23_scheme_rejections(gsm):
+    """ode23 runs in FP64 only; the Michel-Suquet law needs it, starts fresh
+    only, and the taped run takes the implicit-Euler update only."""
+    import ctypes
+    import torch
+    ph = torch.from_numpy(synth.sphere_phase(8, 0.2)).cuda()
+    loads, hs = [[0.002, 0, 0, 0, 0, 0]], [0.1]
+    nor = [gsm.norton(*synth.MATRIX_16), gsm.elastic(*synth.INCLUSION_16)]
+    kin = [gsm.michel_suquet(*synth.ALUMINIUM_MS), gsm.elastic(*synth.ALUMINA)]
+    out = gsm.ms_solve(ph, nor, loads, hs, precision=gsm.MS_PREC_FP32_BULK, ode=ODE, check=False)
+    assert out["rc"] == gsm.GSM_ENOTSUP
+    out = gsm.ms_solve(ph, kin, loads, hs, check=False)
+    assert out["rc"] == gsm.GSM_ENOTSUP
+    eps = torch.zeros(6, 512, dtype=torch.float64, device="cuda")
+    out = gsm.ms_solve(ph, kin, loads, hs, ode=ODE, eps=eps, z=torch.zeros_like(eps), resume=True, check=False)
+    assert out["rc"] == gsm.GSM_ENOTSUP
+    ctx = gsm.ms_create(ph, nor)
+    ld, keep, n = gsm._load_struct(loads, hs, 1e-8, 100, None, 0.0, ode=ODE)
+    res, _ = gsm._result_struct(n)
+    th = ctypes.c_void_p()
+    assert gsm.load().ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th)) == -5
+    # the same context then runs ode23 twice (work arrays allocated once)
+    a = gsm.ms_run(ctx, loads, hs, ode=ODE)
+    b = gsm.ms_run(ctx, loads, hs, ode=ODE)
+    assert a["rc"] == 0 and np.array_equal(a["Sigma"], b["Sigma"])
     gsm.ms_destroy(ctx)

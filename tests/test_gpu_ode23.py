@@ -152,6 +152,23 @@ def test_michel_suquet_matches_oracle(gsm, tangent):
     assert np.all(z[:, 6] >= alpha_n)
 
 
+def test_michel_suquet_tangent_from_the_virgin_state(gsm):
+    """eps_n = z_n = alpha_n = 0 (the first step of a scheme run): the force
+    norm starts at 0 inside the elastic domain; stress and tangent are finite
+    and the oracle's, below and beyond yield."""
+    prm = synth.ALUMINIUM_MS
+    e = np.array([[0.0015, 0, 0, 0, 0, 0], [0.0002, 0, 0, 0, 0, 0], [0, 0, 0, 0.002, 0, 0],
+                  [0.001, -0.0004, -0.0004, 0, 0.0008, 0]])
+    n = e.shape[0]
+    sig, z, st, C = run_ms(gsm, gsm.michel_suquet(*prm), np.zeros((n, 6)), e, np.zeros((n, 7)), 0.5, True)
+    ref = O.update_ode23(prm, np.zeros((n, 6)), e, np.zeros((n, 6)), 0.5, tangent=True, kind=O.KIND_MICHEL_SUQUET,
+                         alpha_n=np.zeros(n))
+    assert np.all((st >> 16) & 1) and np.all(np.isfinite(C))
+    assert np.allclose(sig, ref[0], rtol=1e-10, atol=1e-16)
+    C2 = ref[3].reshape(-1, 36)
+    assert np.all(np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9)
+
+
 def test_michel_suquet_without_yield_and_hardening_is_norton(gsm):
     en, e, zn = synth.ode23_batch(2048, seed=8)
     s1, z1, st1 = run(gsm, gsm.norton(70.0, 0.3, 0.1, 1.0, 5.0), en, e, zn, 0.1)
@@ -168,5 +185,8 @@ def test_michel_suquet_is_refused_by_the_implicit_paths(gsm):
     t = torch.zeros(6, 8, dtype=torch.float64, device="cuda")
     with pytest.raises(gsm.GsmError):
         gsm.gsm_update(mat, t, t, 0.1, t.clone(), t.clone())
-    with pytest.raises(gsm.GsmError):
-        gsm.ms_create(torch.zeros(4, 4, 4, dtype=torch.uint8).cuda(), [mat])
+    # the basic scheme takes it with the ode23 integrator only
+    ctx = gsm.ms_create(torch.zeros(4, 4, 4, dtype=torch.uint8).cuda(), [mat])
+    out = gsm.ms_run(ctx, [[0.001, 0, 0, 0, 0, 0]], [0.1], check=False)
+    gsm.ms_destroy(ctx)
+    assert out["rc"] == gsm.GSM_ENOTSUP

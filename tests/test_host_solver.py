@@ -200,3 +200,22 @@ def test_host_ode23_michel_suquet_matches_oracle(hlib, tangent):
     assert tight.mean() >= 0.98
     assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))
     assert np.all(z[:, 6] >= alpha_n)  # alpha never decreases
+
+
+def test_host_ode23_michel_suquet_tangent_from_the_virgin_state(hlib):
+    """The first load step of a basic-scheme run starts the Michel-Suquet law
+    at eps = z = alpha = 0, where the force norm is 0 inside the elastic domain:
+    the tangent ODE must stay finite there and give the oracle's stress and
+    tangent, from uniaxial and shear strains, below and beyond yield."""
+    prm = synth.ALUMINIUM_MS
+    e = np.array([[0.0015, 0, 0, 0, 0, 0], [0.0002, 0, 0, 0, 0, 0], [0, 0, 0, 0.002, 0, 0],
+                  [0.001, -0.0004, -0.0004, 0, 0.0008, 0]])
+    n = e.shape[0]
+    en, zn = np.zeros((n, 6)), np.zeros((n, 7))
+    sig, z, C, st = _ode23_host(hlib, prm, en, e, zn, 0.5, 1e-8, 1e-11, True, kind=2)
+    out = O.update_ode23(prm, en, e, zn[:, :6], 0.5, rtol=1e-8, atol=1e-11, tangent=True, info=True,
+                         kind=O.KIND_MICHEL_SUQUET, alpha_n=np.zeros(n))
+    assert np.all((st >> 16) & 1) and np.all(np.isfinite(C))
+    assert np.allclose(sig, out[0], rtol=1e-10, atol=1e-16)
+    C2 = out[3].reshape(-1, 36)
+    assert np.all(np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9)

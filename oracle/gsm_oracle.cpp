@@ -837,6 +837,109 @@ void update_ode23(const Law& L, const double epsn[6], const double eps1[6], cons
   if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
 }
 
+// One material update by ode12, the pair of the explicit Euler scheme (order
+// 1) and Heun's method (order 2), Sec. 4.3.  Per attempt of length dt from
+// (t, y) with k1 = f(t, y):
+//   y_E = y + dt k1,  k2 = f(t + dt, y_E),  y_H = y + dt/2 (k1 + k2);
+// the substep continues with y_H (the higher order, as ode23 continues with
+// its order-3 solution); the error compares the stresses of y_H and y_E at
+// t + dt like ode23 compares those of its two solutions; the step control is
+// ode23's with exponent 1/2 (1/(q+1), q = 1 the lower order).  k1 of the next
+// substep is f(t + dt, y_H), evaluated after an acceptance.
+template <int NY>
+void update_ode12(const Law& L, const double epsn[6], const double eps1[6], const double zn[6], double alpha_n,
+                  double h, const Ode23Opts& o, double sig_out[6], double z_out[6], double* alpha_out,
+                  double (*Ct_out)[6], OdeInfo* info) {
+  double Gi[5][5];
+  g_inverse(L, Gi);
+  double y[NY];
+  y[0] = zn[0];
+  y[1] = zn[1];
+  y[2] = zn[3];
+  y[3] = zn[4];
+  y[4] = zn[5];
+  if (NY == 6) y[NY - 1] = alpha_n;
+  double Y[NY][6] = {};
+  const bool tan = o.tangent;
+  double k1[NY], K1[NY][6], k2[NY], K2[NY][6];
+  double t = 0.0, dt = h;
+  ode_rhs<NY>(L, Gi, epsn, eps1, h, 0.0, y, Y, k1, tan ? K1 : nullptr);
+  double sig_old[6], C_old[6][6];
+  stress_tangent<NY>(L, epsn, eps1, h, 0.0, y, Y, sig_old, tan ? C_old : nullptr);
+  info->accepted = info->rejected = 0;
+  info->flags = 0;
+  bool last_rejected = false;
+  while (t < h) {
+    if (info->accepted + info->rejected >= o.max_steps) {
+      info->flags |= F_CAP;
+      break;
+    }
+    const bool clip = t + dt >= h;
+    if (clip) dt = h - t;
+    const double tn1 = clip ? h : t + dt;
+    // Euler predictor and Heun corrector
+    double yE[NY], YE[NY][6], yH[NY], YH[NY][6];
+    for (int a = 0; a < NY; ++a) {
+      yE[a] = y[a] + dt * k1[a];
+      if (tan)
+        for (int c = 0; c < 6; ++c) YE[a][c] = Y[a][c] + dt * K1[a][c];
+    }
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, tn1, yE, YE, k2, tan ? K2 : nullptr);
+    for (int a = 0; a < NY; ++a) {
+      yH[a] = y[a] + 0.5 * dt * (k1[a] + k2[a]);
+      if (tan)
+        for (int c = 0; c < 6; ++c) YH[a][c] = Y[a][c] + 0.5 * dt * (K1[a][c] + K2[a][c]);
+    }
+    double sH[6], sE[6], CH[6][6], CE[6][6];
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, yH, YH, sH, tan ? CH : nullptr);
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, yE, YE, sE, tan ? CE : nullptr);
+    double sum = 0.0;
+    int m = 0;
+    auto sq_scaled = [](double d, double sc) {
+      const double q = sc > 0.0 ? d / sc : (d == 0.0 ? 0.0 : 1e300);
+      return q * q;
+    };
+    for (int i = 0; i < 6; ++i, ++m)
+      sum += sq_scaled(sH[i] - sE[i], o.atol + o.rtol * std::fmax(std::fabs(sig_old[i]), std::fabs(sH[i])));
+    if (tan)
+      for (int i = 0; i < 6; ++i)
+        for (int c = 0; c < 6; ++c, ++m)
+          sum += sq_scaled(CH[i][c] - CE[i][c], o.atol + o.rtol * std::fmax(std::fabs(C_old[i][c]), std::fabs(CH[i][c])));
+    const double err = std::isfinite(sum) ? std::sqrt(sum / m) : 1e300;
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    const double grow = err == 0.0 ? facmax : std::fmin(facmax, std::fmax(0.2, 0.9 / std::sqrt(err)));
+    if (err <= 1.0) {
+      t = tn1;
+      for (int a = 0; a < NY; ++a) {
+        y[a] = yH[a];
+        if (tan)
+          for (int c = 0; c < 6; ++c) Y[a][c] = YH[a][c];
+      }
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = sH[i];
+        if (tan)
+          for (int c = 0; c < 6; ++c) C_old[i][c] = CH[i][c];
+      }
+      ode_rhs<NY>(L, Gi, epsn, eps1, h, t, y, Y, k1, tan ? K1 : nullptr);
+      ++info->accepted;
+      last_rejected = false;
+    } else {
+      ++info->rejected;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+  if (t >= h && !(info->flags & (F_NONFINITE | F_CAP))) info->flags |= F_CONVERGED;
+  stress_tangent<NY>(L, epsn, eps1, h, h, y, Y, sig_out, Ct_out);
+  z_out[0] = y[0];
+  z_out[1] = y[1];
+  z_out[2] = -(y[0] + y[1]);
+  z_out[3] = y[2];
+  z_out[4] = y[3];
+  z_out[5] = y[4];
+  if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -940,15 +1043,16 @@ void ora_newton_matrix_batch(const double* params, int64_t n, const double* y, c
   }
 }
 
-// ode23 update (Sec. 4.3 with the stress-driven error control of Sec. 4.5):
+// ode23 / ode12 update (Sec. 4.3 with the stress-driven error control of Sec. 4.5):
 // kind 1 (Norton, params E, nu, sigma0, edot0, n) or 2 (Michel-Suquet, params
 // E, nu, sigma_Y, H, edot0, sigma_d, n); eps_n, eps, z_n [n][6]; alpha_n,
 // alpha [n] (kind 2; alpha_n may be NULL = 0); tangent [n][6][6] or NULL;
 // info [n][3] = accepted, rejected substeps, flags (1 converged, 4 substep cap).
-int ora_update_ode23(int kind, const double* params, int64_t n, const double* eps_n, const double* eps,
-                     const double* zn, const double* alpha_n, double h, double rtol, double atol, int max_steps,
-                     double* sigma, double* z, double* alpha, double* tangent, int32_t* info) {
-  if (kind != 1 && kind != 2) return -1;
+// method 0 = ode23 (Bogacki-Shampine 3(2)), 1 = ode12 (explicit Euler / Heun).
+int ora_update_ode(int kind, int method, const double* params, int64_t n, const double* eps_n, const double* eps,
+                   const double* zn, const double* alpha_n, double h, double rtol, double atol, int max_steps,
+                   double* sigma, double* z, double* alpha, double* tangent, int32_t* info) {
+  if ((kind != 1 && kind != 2) || (method != 0 && method != 1)) return -1;
   Law L;
   make_law(kind, params, &L);
   Ode23Opts o{rtol, atol, max_steps, tangent != nullptr};
@@ -957,12 +1061,17 @@ int ora_update_ode23(int kind, const double* params, int64_t n, const double* ep
     double(*Ct)[6] = tangent ? reinterpret_cast<double(*)[6]>(tangent + 36 * i) : nullptr;
     OdeInfo inf;
     double al = 0.0;
-    if (kind == 1)
+    const double a0 = alpha_n ? alpha_n[i] : 0.0;
+    if (kind == 1 && method == 0)
       update_ode23<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
                       &inf);
+    else if (kind == 1)
+      update_ode12<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
+                      &inf);
+    else if (method == 0)
+      update_ode23<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, a0, h, o, sigma + 6 * i, z + 6 * i, &al, Ct, &inf);
     else
-      update_ode23<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, alpha_n ? alpha_n[i] : 0.0, h, o, sigma + 6 * i,
-                      z + 6 * i, &al, Ct, &inf);
+      update_ode12<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, a0, h, o, sigma + 6 * i, z + 6 * i, &al, Ct, &inf);
     if (alpha) alpha[i] = al;
     if (info) {
       info[3 * i] = inf.accepted;

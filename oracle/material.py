@@ -62,9 +62,10 @@ def _load():
         lib.ora_Pi.restype = ctypes.c_double
         lib.ora_max_threads.restype = ctypes.c_int
         lib.ora_newton_matrix_batch.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, _dp]
-        lib.ora_update_ode23.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _ip]
-        lib.ora_update_ode23.restype = ctypes.c_int
+        lib.ora_update_ode.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
+                                       _dp, _ip]
+        lib.ora_update_ode.restype = ctypes.c_int
         lib.ora_psi_force_a.argtypes = [_dp, _dp, _dp, _dp]
         lib.ora_psi_force_ms.argtypes = [_dp, _dp, _dp, _dp]
         lib.ora_psi_force_ms.restype = ctypes.c_double
@@ -211,9 +212,13 @@ def newton_matrix_batch(params, y, y_n, h):
     return K, H
 
 
+ODE_METHODS = {"ode23": 0, "ode12": 1}
+
+
 def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100000, tangent=False, info=False,
-                 kind=KIND_NORTON, alpha_n=None):
-    """Material update by ode23 (Sec. 4.3, stress-driven error control Sec. 4.5).
+                 kind=KIND_NORTON, alpha_n=None, method="ode23"):
+    """Material update by ode23 (Sec. 4.3, stress-driven error control Sec. 4.5),
+    or by ode12 (explicit Euler / Heun pair, same control) with method="ode12".
 
     kind KIND_NORTON: params (E, nu, sigma0, edot0, n); KIND_MICHEL_SUQUET:
     params (E, nu, sigma_Y, H, edot0, sigma_d, n) with the equivalent plastic
@@ -233,10 +238,11 @@ def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100
     C = np.zeros((n, 6, 6)) if tangent else None
     inf = np.zeros((n, 3), dtype=np.int32)
     prm = _f64(list(params) + [0.0] * (7 - len(params)))
-    rc = lib.ora_update_ode23(int(kind), _ptr(prm), ctypes.c_int64(n), _ptr(eps_n), _ptr(eps), _ptr(z_n),
-                              _ptr(a_n) if a_n is not None else None, ctypes.c_double(h), ctypes.c_double(rtol),
-                              ctypes.c_double(atol), ctypes.c_int(max_steps), _ptr(sig), _ptr(z), _ptr(alpha),
-                              _ptr(C) if tangent else None, inf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    rc = lib.ora_update_ode(int(kind), ODE_METHODS[method], _ptr(prm), ctypes.c_int64(n), _ptr(eps_n), _ptr(eps),
+                            _ptr(z_n), _ptr(a_n) if a_n is not None else None, ctypes.c_double(h),
+                            ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(max_steps), _ptr(sig), _ptr(z),
+                            _ptr(alpha), _ptr(C) if tangent else None,
+                            inf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     if rc != 0:
         raise ValueError("update_ode23: unsupported law kind")
     out = [sig, z]

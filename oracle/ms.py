@@ -107,12 +107,13 @@ def equilibrium_error(sig_hat, mean_sig, N, floor):
     return num / den
 
 
-def material(eps, z_n, phase, laws, h, tangent=False, eps_n=None, ode=None):
+def material(eps, z_n, phase, laws, h, tangent=False, eps_n=None, ode=None, ode_method="ode23"):
     """One material evaluation of every voxel: laws[p] = (kind, params) for phase p.
 
     Implicit Euler (Sec. 4.1) unless ``ode`` = (rtol, atol): then the ode23
-    update of the force-potential form over the step (Sec. 4.3) from the
-    strain eps_n of the previous step; z_n has 7 columns there (z, alpha)."""
+    (or, with ode_method="ode12", the Euler/Heun) update of the force-potential
+    form over the step (Sec. 4.3) from the strain eps_n of the previous step;
+    z_n has 7 columns there (z, alpha)."""
     n = eps.shape[0]
     nz = z_n.shape[1]
     sig = np.empty((n, 6))
@@ -135,7 +136,7 @@ def material(eps, z_n, phase, laws, h, tangent=False, eps_n=None, ode=None):
         else:
             kw = {"alpha_n": z_n[idx, 6]} if kind == M.KIND_MICHEL_SUQUET else {}
             out = M.update_ode23(params, eps_n[idx], eps[idx], z_n[idx, :6], h, rtol=ode[0], atol=ode[1],
-                                 tangent=tangent, kind=kind, **kw)
+                                 tangent=tangent, kind=kind, method=ode_method, **kw)
             sig[idx] = out[0]
             z[idx, :6] = out[1]
             k = 2
@@ -181,7 +182,7 @@ def reference_stiffness(lam0, mu0):
 
 def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
           eps0=None, zn0=None, E_prev0=None, record=False, stress_mask=None, Sigma_target=None,
-          ref_update=False, ode=None):
+          ref_update=False, ode=None, ode_method="ode23"):
     """Load-history solve of the basic scheme.
 
     phase : (N, N, N) uint8 phase ids, voxel (i, j, k) with k fastest.
@@ -203,6 +204,7 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
                    force-potential form over each step by ode23 from the strain
                    of the previous step (Sec. 4.3); the internal variables then
                    have 7 columns (z, alpha) when a phase is a Michel-Suquet law.
+    ode_method   : "ode23" or "ode12" (explicit Euler / Heun pair).
 
     Returns dict with Sigma (n_steps, 6), iters (n_steps,), errors (list per
     step), eps and z (N^3, 6) at the end, and the per-step (eps, z) history if
@@ -230,7 +232,7 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
         eps = eps + (E_start - E_mean)[None, :]
         E_mean = E_start.copy()
         if ref_update:
-            _, _, Ct = material(eps, z_n, ph, laws, h, tangent=True, eps_n=eps_prev, ode=ode)
+            _, _, Ct = material(eps, z_n, ph, laws, h, tangent=True, eps_n=eps_prev, ode=ode, ode_method=ode_method)
             lam0, mu0 = reference_from_tangents(Ct)
         refs.append((lam0, mu0))
         floor = mu0 * 1e-6
@@ -239,7 +241,7 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
         errs = []
         n_eval = 0
         while True:
-            sig, z = material(eps, z_n, ph, laws, h, eps_n=eps_prev, ode=ode)
+            sig, z = material(eps, z_n, ph, laws, h, eps_n=eps_prev, ode=ode, ode_method=ode_method)
             n_eval += 1
             sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
             mean_sig = sig.mean(axis=0)

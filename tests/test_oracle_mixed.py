@@ -87,20 +87,21 @@ def test_updated_reference_with_a_flowing_matrix():
     assert np.all(b["reference"][1:, 1] < OMS.reference_medium(laws)[1])
 
 
+@pytest.mark.parametrize("method", ["ode23", "ode12"])
 @pytest.mark.parametrize("kind,prm", [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS)])
-def test_scheme_with_ode23_laws_on_a_homogeneous_grid(kind, prm):
+def test_scheme_with_ode23_laws_on_a_homogeneous_grid(kind, prm, method):
     """A homogeneous grid under prescribed macroscopic strains is the single
     voxel: the scheme with the ode23 law reproduces the material history
     integrated voxel-alone from eps_{k-1} to eps_k (z and, for Michel-Suquet,
     alpha)."""
     ph = np.zeros((4, 4, 4), dtype=np.uint8)
     loads = synth.ramp(3, [0.004, -0.001, 0.0, 0.0, 0.002, 0.0])
-    r = OMS.solve(ph, [(kind, prm)], loads, [0.1] * 3, tol=1e-12, ode=(1e-6, 1e-9))
+    r = OMS.solve(ph, [(kind, prm)], loads, [0.1] * 3, tol=1e-12, ode=(1e-6, 1e-9), ode_method=method)
     z = np.zeros((1, 6))
     a = np.zeros(1)
     e_prev = np.zeros((1, 6))
     for k in range(3):
-        out = O.update_ode23(prm, e_prev, loads[k][None], z, 0.1, rtol=1e-6, atol=1e-9, kind=kind,
+        out = O.update_ode23(prm, e_prev, loads[k][None], z, 0.1, rtol=1e-6, atol=1e-9, kind=kind, method=method,
                              **({"alpha_n": a} if kind == O.KIND_MICHEL_SUQUET else {}))
         z = out[1]
         if kind == O.KIND_MICHEL_SUQUET:

@@ -510,6 +510,27 @@ def bench_ode23(G, torch, args):
                                        "mean_accepted_substeps": float((s & 0xFFFF).mean()),
                                        "mean_rejected_substeps": float(((s >> 20) & 0x7FF).mean()),
                                        "converged_fraction": float(((s >> 16) & 1).mean())}
+    # ode12 (explicit Euler / Heun pair), same inputs; with the tangent on the first 2^20 voxels
+    for name, m, tan in (("ode12_no_tangent", n, None),
+                         ("ode12_tangent", 1 << 20, torch.empty(36, 1 << 20, dtype=torch.float64, device="cuda"))):
+        views = [t[:, :m].contiguous() for t in (E0, E1, Z0)]
+        sg, zz = torch.empty_like(views[1]), torch.empty_like(views[1])
+        st2 = torch.empty(m, dtype=torch.int32, device="cuda")
+        G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method="ode12")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method="ode12")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_ms = a.elapsed_time(b) / 3
+        s2 = st2.cpu().numpy()
+        out[name] = {"voxels": m, "voxel_updates_per_s": m / (t_ms * 1e-3), "ms_per_launch": t_ms,
+                     "mean_accepted_substeps": float((s2 & 0xFFFF).mean()),
+                     "mean_rejected_substeps": float(((s2 >> 20) & 0x7FF).mean()),
+                     "converged_fraction": float(((s2 >> 16) & 1).mean())}
+        del tan
     out["mmc_scheme"] = bench_mmc_scheme(G, torch)
     return out
 

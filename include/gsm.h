@@ -149,6 +149,22 @@ int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void*
                      double step_h, double rtol, double atol, int max_substeps, void* sigma, void* z, void* tangent,
                      int32_t* status, void* stream);
 
+/* Explicit Runge-Kutta pairs of Sec. 4.3. */
+#define GSM_ODE23 0              /* Bogacki-Shampine 3(2) (MATLAB's ode23)              */
+#define GSM_ODE12 1              /* explicit Euler (order 1) / Heun (order 2), continued
+                                    with Heun's solution; step exponent 1/2            */
+
+/*
+ * gsm_update_ode -- gsm_update_ode23 with the pair chosen by `method`
+ * (GSM_ODE23 or GSM_ODE12; anything else: GSM_EINVAL).  Same arguments,
+ * layouts, status word and errors; gsm_update_ode23 is method GSM_ODE23.
+ * ode12 evaluates the right-hand side twice per substep and needs about
+ * tol^(-1/2) substeps (ode23: tol^(-1/3)).
+ */
+int gsm_update_ode(gsm_handle h, int method, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n,
+                   int64_t ld, double step_h, double rtol, double atol, int max_substeps, void* sigma, void* z,
+                   void* tangent, int32_t* status, void* stream);
+
 /* gsm_strerror -- static message for a return code. */
 const char* gsm_strerror(int code);
 
@@ -212,8 +228,9 @@ typedef struct ms_load {
   int integrator;             /* 0: the implicit-Euler update (gsm_update) of every
                                  phase; 1: the force-potential form integrated over
                                  each load step by ode23 (gsm_update_ode23) from the
-                                 voxel's strain at t_n to the current iterate; needed
-                                 for GSM_PSI_ELASTIC_VP_KIN phases; FP64 only           */
+                                 voxel's strain at t_n to the current iterate; 2: the
+                                 same by ode12 (gsm_update_ode, GSM_ODE12); 1 or 2 are
+                                 needed for GSM_PSI_ELASTIC_VP_KIN phases; FP64 only  */
   double ode_rtol, ode_atol;  /* integrator 1: stress-error tolerances (rtol > 0,
                                  atol >= 0); keep them well below `tol`: an update
                                  that is not converged to better than the equilibrium
@@ -265,7 +282,7 @@ size_t ms_workspace_bytes(const ms_problem* prob);
  * A problem with GSM_PSI_ELASTIC_VP_KIN phases keeps its seventh internal
  * variable (the accumulated plastic strain) inside the context: it starts
  * fresh only (resume = 1 gives GSM_ENOTSUP).
- * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTSUP (integrator 1 with a precision
+ * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTSUP (integrator 1 or 2 with a precision
  * other than MS_PREC_FP64, a VP_KIN phase with integrator 0), GSM_ENOTCONV
  * (some step hit max_iter; the result is still filled in).
  */

@@ -23,6 +23,8 @@ GSM_PSI_ELASTIC, GSM_PSI_ELASTIC_VP_DEV, GSM_PSI_ELASTIC_VP_KIN = 0, 1, 2
 GSM_PHI_NONE, GSM_PHI_NORTON, GSM_PHI_MS_FORCE = 0, 1, 2
 GSM_FP64, GSM_FP32_FP64FIX, GSM_FP32 = 0, 1, 2
 MS_PREC_FP64, MS_PREC_FP32_BULK = 0, 1
+GSM_ODE23, GSM_ODE12 = 0, 1
+ODE_METHODS = {"ode23": GSM_ODE23, "ode12": GSM_ODE12}
 
 ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 << 19
 
@@ -30,7 +32,8 @@ ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 <<
 EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kernel_launches",
            "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc",
            "serve_create", "serve_destroy", "serve_submit", "serve_tick", "serve_job_state", "serve_fetch",
-           "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy", "gsm_update_ode23")
+           "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy", "gsm_update_ode23",
+           "gsm_update_ode")
 
 _lib = None
 
@@ -90,6 +93,8 @@ def load(path=None):
     lib.gsm_destroy.argtypes = [vp]
     lib.gsm_update.argtypes = [vp, i64, vp, vp, i64, dbl, vp, vp, vp, vp, vp]
     lib.gsm_update_ode23.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.gsm_update_ode.argtypes = [vp, ctypes.c_int, i64, vp, vp, vp, i64, dbl, dbl, dbl, ctypes.c_int, vp, vp, vp, vp,
+                                   vp]
     lib.gsm_strerror.restype = ctypes.c_char_p
     lib.gsm_strerror.argtypes = [ctypes.c_int]
     lib.gsm_kernel_launches.restype = i64
@@ -193,10 +198,11 @@ def gsm_destroy(mat):
 
 
 def gsm_update_ode23(mat, eps_n, eps, z_n, h, sigma, z, tangent=None, status=None, rtol=1e-3, atol=1e-6,
-                     max_substeps=100000, stream=None, n_vox=None):
-    """Material update by ode23 over the load step (FP64 tensors ``[6, ld]``;
-    internal variables ``[7, ld]`` (z, alpha) for the Michel-Suquet law; tangent
-    ``[36, ld]`` = full dsigma/deps_{n+1} row-major; status ``[ld]``)."""
+                     max_substeps=100000, stream=None, n_vox=None, method="ode23"):
+    """Material update by ode23 (or, method="ode12", the Euler/Heun pair) over the
+    load step (FP64 tensors ``[6, ld]``; internal variables ``[7, ld]`` (z,
+    alpha) for the Michel-Suquet law; tangent ``[36, ld]`` = full
+    dsigma/deps_{n+1} row-major; status ``[ld]``)."""
     lib = load()
     ld = eps.shape[1]
     n = ld if n_vox is None else int(n_vox)
@@ -204,8 +210,12 @@ def gsm_update_ode23(mat, eps_n, eps, z_n, h, sigma, z, tangent=None, status=Non
     for t, rows in ((eps_n, 6), (eps, 6), (z_n, nz), (sigma, 6), (z, nz), (tangent, 36)):
         if t is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != ld or not t.is_contiguous()):
             raise ValueError("fields must be contiguous [components, ld] tensors with a common ld")
-    rc = lib.gsm_update_ode23(mat.handle, n, _ptr(eps_n), _ptr(eps), _ptr(z_n), ld, float(h), float(rtol), float(atol),
-                              int(max_substeps), _ptr(sigma), _ptr(z), _ptr(tangent), _ptr(status), _stream_ptr(stream))
+    args = (n, _ptr(eps_n), _ptr(eps), _ptr(z_n), ld, float(h), float(rtol), float(atol), int(max_substeps),
+            _ptr(sigma), _ptr(z), _ptr(tangent), _ptr(status), _stream_ptr(stream))
+    if method == "ode23":
+        rc = lib.gsm_update_ode23(mat.handle, *args)
+    else:
+        rc = lib.gsm_update_ode(mat.handle, ODE_METHODS[method], *args)
     _check(rc, "gsm_update_ode23")
 
 
@@ -267,7 +277,7 @@ def _mask_bits(stress_mask):
 
 
 def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=None, Sigma=None, ref_update=False,
-                 ode=None):
+                 ode=None, ode_method="ode23"):
     E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
     hs = np.ascontiguousarray(np.asarray(hs, dtype=np.float64).reshape(-1))
     n = E.shape[0]
@@ -286,7 +296,7 @@ def _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask=Non
                  hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
                  f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if f is not None else None, float(switch_tol),
                  _mask_bits(stress_mask), S.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if S is not None else None,
-                 1 if ref_update else 0, 0 if ode is None else 1,
+                 1 if ref_update else 0, 0 if ode is None else 1 + ODE_METHODS[ode_method],
                  float(ode[0]) if ode is not None else 1e-3, float(ode[1]) if ode is not None else 1e-6,
                  int(ode[2]) if ode is not None and len(ode) > 2 else 100000)
     return ld, keep, n
@@ -303,14 +313,16 @@ def _result_struct(n):
 
 
 def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=None, resume=False,
-           E_prev=None, switch_tol=0.0, check=True, stress_mask=None, Sigma=None, ref_update=False, ode=None):
+           E_prev=None, switch_tol=0.0, check=True, stress_mask=None, Sigma=None, ref_update=False, ode=None,
+           ode_method="ode23"):
     """Solve a load history.  Returns dict(Sigma, iters, final_error, fp32_iters, total_iters, E,
     reference, rc).  stress_mask: 6 booleans (or bits) of the macroscopic components whose stress
     (Sigma, default 0) is prescribed; ref_update: per-step reference medium from tangents;
-    ode: None (implicit Euler) or (rtol, atol[, max_substeps]) for the ode23 update over each step."""
+    ode: None (implicit Euler) or (rtol, atol[, max_substeps]) for the update over each step by
+    ode_method ("ode23" or "ode12")."""
     lib = load()
     ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask, Sigma, ref_update,
-                               ode)
+                               ode, ode_method)
     res, out = _result_struct(n)
     st = None
     if eps is not None or z is not None:

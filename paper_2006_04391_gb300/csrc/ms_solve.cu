@@ -34,6 +34,7 @@
 #include "adjoint_kernels.cuh"
 #include "common.cuh"
 #include "ms_kernels.cuh"
+#include "ms_ode.h"
 
 namespace gsm {
 namespace {
@@ -101,7 +102,7 @@ struct Engine {
   Reduced* red_host = nullptr;
   int cap = 0;
   bool inited = false;
-  int per_sm_mat[4] = {1, 1, 1, 1};
+  int per_sm_mat[5] = {1, 1, 1, 1, 1};  // FP64, FP32-fix, FP32 laws; ode23, ode12 laws
   int per_sm_gam[2] = {1, 1};
 
   int init(cudaStream_t s, int capacity) {
@@ -125,8 +126,8 @@ struct Engine {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_batch_kernel<float, MODE_FP32>, kMatBlock, 0) ==
         cudaSuccess)
       per_sm_mat[2] = std::max(b, 1);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_ode_kernel, kMatBlock, 0) == cudaSuccess)
-      per_sm_mat[3] = std::max(b, 1);
+    per_sm_mat[3] = ms_ode_blocks_per_sm(0);
+    per_sm_mat[4] = ms_ode_blocks_per_sm(1);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<double>, kGamBlock, 0) == cudaSuccess)
       per_sm_gam[0] = std::max(b, 1);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<float>, kGamBlock, 0) == cudaSuccess)
@@ -200,11 +201,11 @@ struct Job {
   int stress_mask = 0;               // mixed boundary conditions: prescribed-stress components
   std::vector<double> S_target;      // [n_steps][6]
   bool ref_update = false;           // per-step reference medium from tangents
-  int integrator = 0;                // 0 implicit Euler, 1 ode23 (Sec. 4.3)
+  int integrator = 0;                // 0 implicit Euler, 1 ode23, 2 ode12 (Sec. 4.3)
   double ode_rtol = 1e-3, ode_atol = 1e-6;
   int ode_max = 100000;
-  bool has_kin = false;              // a Michel-Suquet phase: alpha, and ode23 only
-  double* eps_prev = nullptr;        // [6][nvox] strain at t_n (ode23)
+  bool has_kin = false;              // a Michel-Suquet phase: alpha, and an explicit pair only
+  double* eps_prev = nullptr;        // [6][nvox] strain at t_n (ode23, ode12)
   double* alpha_n = nullptr;         // [nvox] Michel-Suquet alpha at t_n
   double* alpha = nullptr;           // [nvox] and at t_{n+1}
   double C0ss_inv[36] = {};          // (C0 on the prescribed-stress components)^-1, n_s x n_s
@@ -243,7 +244,7 @@ int job_setup(Job& j, int N, const uint8_t* phase_dev, int n_phases, const gsm_h
   for (int p = 0; p < n_phases; ++p) {
     const Material* m = reinterpret_cast<const Material*>(laws[p]);
     if (!m) return GSM_EINVAL;
-    if (m->psi_kind == GSM_PSI_ELASTIC_VP_KIN) j.has_kin = true;  // runs with the ode23 integrator only
+    if (m->psi_kind == GSM_PSI_ELASTIC_VP_KIN) j.has_kin = true;  // runs with ode23 or ode12 only
     j.tab_host.kind[p] = m->psi_kind;
     j.tab_host.p64[p] = m->p64;
     j.tab_host.p32[p] = m->p32;
@@ -335,14 +336,14 @@ int job_load(Job& j, const ms_load* load) {
       if (load->forced_iters[k] < 1) return GSM_EINVAL;
   if (load->stress_mask < 0 || load->stress_mask > 63 || (load->ref_update != 0 && load->ref_update != 1))
     return GSM_EINVAL;
-  if (load->integrator != 0 && load->integrator != 1) return GSM_EINVAL;
-  if (load->integrator == 1 && (!(load->ode_rtol > 0.0) || !(load->ode_atol >= 0.0) || load->ode_max_substeps < 1))
+  if (load->integrator < 0 || load->integrator > 2) return GSM_EINVAL;
+  if (load->integrator >= 1 && (!(load->ode_rtol > 0.0) || !(load->ode_atol >= 0.0) || load->ode_max_substeps < 1))
     return GSM_EINVAL;
-  // the Michel-Suquet law integrates by ode23 only; ode23 runs in FP64
-  if (j.has_kin && load->integrator != 1) return GSM_ENOTSUP;
-  if (load->integrator == 1 && j.precision != MS_PREC_FP64) return GSM_ENOTSUP;
+  // the Michel-Suquet law integrates by an explicit pair only; those run in FP64
+  if (j.has_kin && load->integrator == 0) return GSM_ENOTSUP;
+  if (load->integrator >= 1 && j.precision != MS_PREC_FP64) return GSM_ENOTSUP;
   j.integrator = load->integrator;
-  if (j.integrator == 1) {
+  if (j.integrator >= 1) {
     j.ode_rtol = load->ode_rtol;
     j.ode_atol = load->ode_atol;
     j.ode_max = load->ode_max_substeps;
@@ -458,10 +459,9 @@ int reference_update(Engine& g, Job& j, const double (&dE)[6]) {
   const int grid = (int)std::min<int64_t>(j.n_vch, (int64_t)sm_count() * 2);
   const double inv_n3 = 1.0 / (double)j.nvox;
   const Step hs = make_step(j.h[j.step]);
-  if (j.integrator == 1)
-    ms_reference_ode_kernel<<<grid, kMatBlock, 0, g.stream>>>(
-        j.nvox, j.phase, j.tab_dev, hs, Ode23Ctl{j.ode_rtol, j.ode_atol, j.ode_max}, j.f64.eps_raw, j.eps_prev,
-        j.f64.zn, j.alpha_n, inv_n3, dE[0], dE[1], dE[2], dE[3], dE[4], dE[5], j.mat_part);
+  if (j.integrator >= 1)
+    ms_launch_reference_ode(j.integrator - 1, grid, g.stream, j.nvox, j.phase, j.tab_dev, hs.h, j.ode_rtol, j.ode_atol,
+                            j.ode_max, j.f64.eps_raw, j.eps_prev, j.f64.zn, j.alpha_n, inv_n3, dE, j.mat_part);
   else if (j.law_mode == MODE_FP64)
     ms_reference_kernel<MODE_FP64><<<grid, kMatBlock, 0, g.stream>>>(j.nvox, j.phase, j.tab_dev, hs, j.f64.eps_raw,
                                                                     j.f64.zn, inv_n3, dE[0], dE[1], dE[2], dE[3],
@@ -500,8 +500,8 @@ int step_start(Engine& g, Job& j) {
     dE[q] = E[q] - j.E_prev[q];
     j.E_cur[q] = E[q];
   }
-  // ode23 laws integrate over the step from each voxel's strain at t_n
-  if (j.integrator == 1) convert<double, double>(g.stream, j.f64.eps_raw, j.eps_prev, 6 * j.nvox, 1.0 / (double)j.nvox);
+  // ode23 / ode12 laws integrate over the step from each voxel's strain at t_n
+  if (j.integrator >= 1) convert<double, double>(g.stream, j.f64.eps_raw, j.eps_prev, 6 * j.nvox, 1.0 / (double)j.nvox);
   if (j.ref_update) {
     const int rc = reference_update(g, j, dE);
     if (rc != GSM_OK) return rc;
@@ -630,23 +630,27 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
       j->need_start = false;
     }
   // launch groups: FP64 fields + FP64 laws, FP64 fields + FP32-fix laws,
-  // FP64 fields + ode23 laws, FP32 fields (FP64 groups first: one Green launch)
+  // FP64 fields + ode23 laws, FP64 fields + ode12 laws, FP32 fields (FP64
+  // groups first: one Green launch)
+  constexpr int kGroups = 5, kF32 = 4;
   auto key = [](const Job* j) {
-    return j->fp32_phase ? 3 : (j->integrator == 1 ? 2 : (j->law_mode == MODE_FP32_FIX ? 1 : 0));
+    if (j->fp32_phase) return kF32;
+    if (j->integrator >= 1) return 1 + j->integrator;
+    return j->law_mode == MODE_FP32_FIX ? 1 : 0;
   };
   std::vector<Job*> order;
   order.reserve(n);
-  int gstart[5] = {0, 0, 0, 0, 0};
-  for (int k = 0; k < 4; ++k) {
+  int gstart[kGroups + 1] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < kGroups; ++k) {
     for (Job* j : jobs)
       if (key(j) == k) order.push_back(j);
     gstart[k + 1] = (int)order.size();
   }
-  int64_t vtot[4] = {0, 0, 0, 0}, mtot[2] = {0, 0};
+  int64_t vtot[kGroups] = {0, 0, 0, 0, 0}, mtot[2] = {0, 0};
   for (int i = 0; i < n; ++i) {
     Job& j = *order[i];
     const int k = key(&j);
-    const int pk = k == 3 ? 1 : 0;
+    const int pk = k == kF32 ? 1 : 0;
     const bool f = j.fp32_phase;
     JobView& v = g.views_host[i];
     v.phase = j.phase;
@@ -697,15 +701,16 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
                                                                               gstart[2] - gstart[1], vtot[1]);
     count_launch();
   }
-  if (gstart[3] > gstart[2]) {
-    const int grid = (int)std::min<int64_t>(vtot[2], sms * g.per_sm_mat[3]);
-    ms_material_ode_kernel<<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[2], gstart[3] - gstart[2], vtot[2]);
-    count_launch();
-  }
-  if (gstart[4] > gstart[3]) {
-    const int grid = (int)std::min<int64_t>(vtot[3], sms * g.per_sm_mat[2]);
-    ms_material_batch_kernel<float, MODE_FP32><<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[3],
-                                                                         gstart[4] - gstart[3], vtot[3]);
+  for (int k = 2; k <= 3; ++k)
+    if (gstart[k + 1] > gstart[k]) {
+      const int grid = (int)std::min<int64_t>(vtot[k], sms * g.per_sm_mat[k + 1]);
+      ms_launch_material_ode(k - 2, grid, s, g.views_dev + gstart[k], gstart[k + 1] - gstart[k], vtot[k]);
+      count_launch();
+    }
+  if (gstart[kF32 + 1] > gstart[kF32]) {
+    const int grid = (int)std::min<int64_t>(vtot[kF32], sms * g.per_sm_mat[2]);
+    ms_material_batch_kernel<float, MODE_FP32><<<grid, kMatBlock, 0, s>>>(g.views_dev + gstart[kF32],
+                                                                         gstart[kF32 + 1] - gstart[kF32], vtot[kF32]);
     count_launch();
   }
   for (Job* j : order) {
@@ -716,14 +721,16 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
         j->fp32_phase ? exec_r2c(*p, j->f32.sig, j->f32.sig_hat) : exec_r2c(*p, j->f64.sig, j->f64.sig_hat);
     if (fr != CUFFT_SUCCESS) return GSM_ECUDA;
   }
-  if (gstart[3] > gstart[0]) {
+  if (gstart[kF32] > gstart[0]) {
     const int grid = (int)std::min<int64_t>(mtot[0], sms * g.per_sm_gam[0]);
-    ms_gamma_batch_kernel<double><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[0], gstart[3] - gstart[0], mtot[0]);
+    ms_gamma_batch_kernel<double><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[0], gstart[kF32] - gstart[0],
+                                                             mtot[0]);
     count_launch();
   }
-  if (gstart[4] > gstart[3]) {
+  if (gstart[kF32 + 1] > gstart[kF32]) {
     const int grid = (int)std::min<int64_t>(mtot[1], sms * g.per_sm_gam[1]);
-    ms_gamma_batch_kernel<float><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[3], gstart[4] - gstart[3], mtot[1]);
+    ms_gamma_batch_kernel<float><<<grid, kGamBlock, 0, s>>>(g.views_dev + gstart[kF32],
+                                                            gstart[kF32 + 1] - gstart[kF32], mtot[1]);
     count_launch();
   }
   ms_finalize_batch_kernel<<<n, kFinBlock, 0, s>>>(g.views_dev, g.red_dev);
@@ -818,7 +825,7 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
   for (int q = 0; q < 6; ++q) j.E_prev[q] = 0.0;
   // alpha (the Michel-Suquet law's seventh internal variable) lives in the context only
   if (j.has_kin && state && state->resume) return GSM_ENOTSUP;
-  if (j.integrator == 1 && !j.eps_prev && cudaMallocAsync(&j.eps_prev, n6 * sizeof(double), s) != cudaSuccess)
+  if (j.integrator >= 1 && !j.eps_prev && cudaMallocAsync(&j.eps_prev, n6 * sizeof(double), s) != cudaSuccess)
     return GSM_ENOMEM;
   if (j.has_kin) {
     if (!j.alpha_n && cudaMallocAsync(&j.alpha_n, j.nvox * sizeof(double), s) != cudaSuccess) return GSM_ENOMEM;

@@ -1,9 +1,11 @@
-// gsm_update_ode23: the material update by adaptive explicit Runge-Kutta
+// gsm_update_ode / gsm_update_ode23: the material update by adaptive explicit Runge-Kutta
 // integration of the force-potential form (AutoMat, arXiv 2006.04391,
 // Sec. 4.3, Corollary 1, Sec. 4.5) on sm_103a.  One thread per voxel; fields
 // in HBM (or page-locked host memory) in structure-of-arrays layout; a
 // persistent grid-stride loop whose bound is uniform per block, so every lane
 // takes part in the warp votes of the substep loop.
+#include <type_traits>
+
 #include "common.cuh"
 #include "ode23.cuh"
 
@@ -18,7 +20,7 @@ constexpr int kOdeBlock = 128;
 // different substep counts, and with one voxel per lane per pass the finished
 // lanes would idle until the slowest voxel of their warp is done (measured:
 // 23.7 of 32 lanes busy; 28.7 -> 31.2 M voxel-updates/s).
-template <class Law, bool TAN>
+template <class Law, bool TAN, int PAIR>
 __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld, LawParams<double> p, Step hs,
                                                           Ode23Ctl ctl, const double* __restrict__ epsn,
                                                           const double* __restrict__ eps,
@@ -28,7 +30,7 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int NZ = stored_nz<Law>();
-  Ode23Voxel<Law, TAN> v;
+  ErkVoxel<Law, TAN, PAIR> v;
   auto start = [&](int64_t k) {
     double e0[6], e1[6], zi[NZ];
 #pragma unroll
@@ -102,10 +104,11 @@ template <auto Kernel> int ode_grid(int64_t n) {
 
 using namespace gsm;
 
-extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n,
-                                int64_t ld, double step_h, double rtol, double atol, int max_substeps, void* sigma,
-                                void* z, void* tangent, int32_t* status, void* stream) {
+extern "C" int gsm_update_ode(gsm_handle h, int method, int64_t n_vox, const void* eps_n, const void* eps,
+                              const void* z_n, int64_t ld, double step_h, double rtol, double atol, int max_substeps,
+                              void* sigma, void* z, void* tangent, int32_t* status, void* stream) {
   if (!h || n_vox < 0 || ld < n_vox) return GSM_EINVAL;
+  if (method != GSM_ODE23 && method != GSM_ODE12) return GSM_EINVAL;
   if (n_vox == 0) return GSM_OK;
   const Material& m = *reinterpret_cast<const Material*>(h);
   if (m.psi_kind != GSM_PSI_ELASTIC_VP_DEV && m.psi_kind != GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;
@@ -131,17 +134,33 @@ extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, 
   double* zo = static_cast<double*>(out[1]);
   double* to = static_cast<double*>(out[2]);
   int32_t* sto = static_cast<int32_t*>(out[3]);
-  auto launch = [&](auto law) {
+  auto launch = [&](auto law, auto pair) {
     using Law = decltype(law);
+    constexpr int PAIR = decltype(pair)::value;
     if (to)
-      ode23_kernel<Law, true><<<ode_grid<ode23_kernel<Law, true>>(n_vox), kOdeBlock, 0, s>>>(
+      ode23_kernel<Law, true, PAIR><<<ode_grid<ode23_kernel<Law, true, PAIR>>(n_vox), kOdeBlock, 0, s>>>(
           n_vox, ld, m.p64, hs, ctl, e0, e1, zi, so, zo, to, sto);
     else
-      ode23_kernel<Law, false><<<ode_grid<ode23_kernel<Law, false>>(n_vox), kOdeBlock, 0, s>>>(
+      ode23_kernel<Law, false, PAIR><<<ode_grid<ode23_kernel<Law, false, PAIR>>(n_vox), kOdeBlock, 0, s>>>(
           n_vox, ld, m.p64, hs, ctl, e0, e1, zi, so, zo, nullptr, sto);
   };
-  if (m.psi_kind == GSM_PSI_ELASTIC_VP_DEV) launch(NortonDev{});
-  else launch(MichelSuquet{});
+  using BS23 = std::integral_constant<int, ERK_BS23>;
+  using HEUN12 = std::integral_constant<int, ERK_HEUN12>;
+  const bool nor = m.psi_kind == GSM_PSI_ELASTIC_VP_DEV;
+  if (method == GSM_ODE23) {
+    if (nor) launch(NortonDev{}, BS23{});
+    else launch(MichelSuquet{}, BS23{});
+  } else {
+    if (nor) launch(NortonDev{}, HEUN12{});
+    else launch(MichelSuquet{}, HEUN12{});
+  }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? GSM_OK : GSM_ECUDA;
+}
+
+extern "C" int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n,
+                                int64_t ld, double step_h, double rtol, double atol, int max_substeps, void* sigma,
+                                void* z, void* tangent, int32_t* status, void* stream) {
+  return gsm_update_ode(h, GSM_ODE23, n_vox, eps_n, eps, z_n, ld, step_h, rtol, atol, max_substeps, sigma, z,
+                        tangent, status, stream);
 }

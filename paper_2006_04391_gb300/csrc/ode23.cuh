@@ -4,9 +4,11 @@
 // Sec. 2, Eq. gsm_internal: ydot = dPsi/dA (A), A = -d psi/dy (eps(t), y), with
 // the strain interpolated linearly over the load step,
 // eps(t) = eps_n + theta (eps_{n+1} - eps_n), theta = (t - t_n)/h.
-// Integrator: the Bogacki-Shampine 3(2) pair (MATLAB's ode23), first stage
-// = last stage of the previous step, step sizes after Hairer, Norsett and
-// Wanner (Solving ODEs I, II.4), whole interval as the first trial step.
+// Integrators (Sec. 4.3): the Bogacki-Shampine 3(2) pair (MATLAB's ode23),
+// first stage = last stage of the previous step, or ode12, the explicit Euler
+// (order 1) / Heun (order 2) pair continued with Heun's solution; step sizes
+// after Hairer, Norsett and Wanner (Solving ODEs I, II.4) with exponent
+// 1/(q+1), q the lower order; whole interval as the first trial step.
 // Error measure (Sec. 4.5, stress-driven): RMS over the stress pair the two
 // embedded solutions give at the end of the substep, scaled by atol + rtol
 // max(|sigma_old|, |sigma_new|); with the tangent also over the tangent pair.
@@ -24,6 +26,9 @@ struct Ode23Ctl {
   double rtol, atol;
   int max_steps;  // accepted + rejected substeps
 };
+
+// Embedded explicit Runge-Kutta pairs.
+enum : int { ERK_BS23 = 0, ERK_HEUN12 = 1 };
 
 // Status word of the ode23 update: bits 0-15 accepted substeps, bits 20-30
 // rejected substeps (both saturating), flags in bits 16-19 as elsewhere.
@@ -218,7 +223,7 @@ AD_HD double scaled_sq(double d, double sc) {
 // finish() for the outputs.  A kernel can therefore hand a lane its next voxel
 // as soon as its current one is done, instead of letting the lane wait for
 // the slowest voxel of its warp.
-template <class Law, bool TAN> struct Ode23Voxel {
+template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
   static constexpr int NY = Law::NY, NZ = stored_nz<Law>();
   using M56 = double[TAN ? NY : 1][TAN ? 6 : 1];
   using M66 = double[TAN ? 6 : 1][TAN ? 6 : 1];
@@ -265,6 +270,115 @@ template <class Law, bool TAN> struct Ode23Voxel {
   }
 
   AD_HD void attempt(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
+    if constexpr (PAIR == ERK_BS23) attempt_bs23(p, hs, ctl);
+    else attempt_heun12(p, hs, ctl);
+  }
+
+  // Error-norm entries of a stress (and tangent) pair against the last accepted
+  // stress (and tangent): returns the RMS-scaled error.
+  AD_HD double pair_error(const double (&s_hi)[6], const double (&s_lo)[6], const M66& C_hi, const M66& C_lo,
+                          const Ode23Ctl& ctl) const {
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
+    int m = 6;
+    if constexpr (TAN) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
+      m = 42;
+    }
+    // a trial step that overflows is rejected like one with a large error
+    return finite64(sum) ? sqrt(sum / m) : 1e300;
+  }
+
+  // Accept (err <= 1: move to the new state, its right-hand side and stress)
+  // or reject; next substep length after Hairer II.4 (fac 0.9, facmin 0.2,
+  // facmax 5, 1 right after a rejection).
+  AD_HD void conclude(double err, double tn1, bool clip, const OdeState<NY, TAN>& snew, const double (&knew)[NY],
+                      const M56& Knew, const double (&s_hi)[6], const M66& C_hi) {
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    double f;
+    if constexpr (PAIR == ERK_BS23) f = err == 0.0 ? 1e300 : 0.9 * fpow::pow_pos(err, -1.0 / 3.0);
+    else f = err == 0.0 ? 1e300 : 0.9 / sqrt(err);
+    const double grow = fmin(facmax, fmax(0.2, f));
+    if (err <= 1.0) {
+      t = tn1;
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        s.y[a] = snew.y[a];
+        k1[a] = knew[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            s.Y[a][c] = snew.Y[a][c];
+            K1[a][c] = Knew[a][c];
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = s_hi[i];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
+      }
+      ++n_acc;
+      last_rejected = false;
+      if (clip) done = true;
+    } else {
+      ++n_rej;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+
+  // ode12: y_E = y + dt k1, k2 = f(t + dt, y_E), y_H = y + dt/2 (k1 + k2); the
+  // error compares the stresses of y_H and y_E; the right-hand side at y_H
+  // (k1 of the next substep) is evaluated before the decision so that the
+  // lanes of a warp stay together.
+  AD_HD void attempt_heun12(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
+    const double h = hs.h, inv_h = hs.inv_h;
+    if (n_acc + n_rej >= ctl.max_steps) {
+      flags |= ST_CAP;
+      done = true;
+      return;
+    }
+    const bool clip = t + dt >= h;
+    if (clip) dt = h - t;
+    const double tn1 = clip ? h : t + dt;
+    const double th1 = clip ? 1.0 : tn1 * inv_h;
+    OdeState<NY, TAN> sE, sH;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      sE.y[a] = fma(dt, k1[a], s.y[a]);
+      if constexpr (TAN)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sE.Y[a][c] = fma(dt, K1[a][c], s.Y[a][c]);
+    }
+    double k[NY];
+    M56 Kc;
+    ode_rhs<Law, TAN>(p, epsn, de, th1, sE, k, Kc);
+    const double hd = 0.5 * dt;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      sH.y[a] = fma(hd, k1[a] + k[a], s.y[a]);
+      if constexpr (TAN)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sH.Y[a][c] = fma(hd, K1[a][c] + Kc[a][c], s.Y[a][c]);
+    }
+    double s_hi[6], s_lo[6];
+    M66 C_hi, C_lo;
+    ode_stress<Law, TAN>(p, epsn, de, th1, sH, s_hi, C_hi);
+    ode_stress<Law, TAN>(p, epsn, de, th1, sE, s_lo, C_lo);
+    const double err = pair_error(s_hi, s_lo, C_hi, C_lo, ctl);
+    ode_rhs<Law, TAN>(p, epsn, de, th1, sH, k, Kc);
+    conclude(err, tn1, clip, sH, k, Kc, s_hi, C_hi);
+  }
+
+  AD_HD void attempt_bs23(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
     // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1), order-3 weights (2/9, 1/3, 4/9),
     // order-2 weights (7/24, 1/4, 1/3, 1/8) on k1..k4 with k4 = f(t + dt, y3).
     constexpr double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
@@ -356,52 +470,7 @@ template <class Law, bool TAN> struct Ode23Voxel {
         for (int c = 0; c < 6; ++c) s2.Y[a][c] = Y3[a][c] - E[a][c];
     }
     ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
-    double sum = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-      sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
-    int m = 6;
-    if constexpr (TAN) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-          sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
-      m = 42;
-    }
-    // a trial step that overflows is rejected like one with a large error
-    const double err = finite64(sum) ? sqrt(sum / m) : 1e300;
-    // Hairer II.4: fac 0.9, facmin 0.2, facmax 5 (1 right after a rejection), exponent 1/3
-    const double facmax = last_rejected ? 1.0 : 5.0;
-    const double grow = err == 0.0 ? facmax : fmin(facmax, fmax(0.2, 0.9 * fpow::pow_pos(err, -1.0 / 3.0)));
-    if (err <= 1.0) {
-      t = tn1;
-#pragma unroll
-      for (int a = 0; a < NY; ++a) {
-        s.y[a] = y3[a];
-        k1[a] = k4[a];
-        if constexpr (TAN)
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            s.Y[a][c] = Y3[a][c];
-            K1[a][c] = K4[a][c];
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        sig_old[i] = s_hi[i];
-        if constexpr (TAN)
-#pragma unroll
-          for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
-      }
-      ++n_acc;
-      last_rejected = false;
-      if (clip) done = true;
-    } else {
-      ++n_rej;
-      last_rejected = true;
-    }
-    dt *= grow;
+    conclude(pair_error(s_hi, s_lo, C_hi, C_lo, ctl), tn1, clip, s3, k4, K4, s_hi, C_hi);
   }
 
   // outputs at the end of the step (sig_old is the stress of the last accepted
@@ -434,13 +503,15 @@ template <class Law, bool TAN> struct Ode23Voxel {
   }
 };
 
-// One voxel, start to end (single thread; the kernel schedules Ode23Voxel
+template <class Law, bool TAN> using Ode23Voxel = ErkVoxel<Law, TAN, ERK_BS23>;
+
+// One voxel, start to end (single thread; the kernel schedules ErkVoxel
 // states per lane itself).
-template <class Law, bool TAN>
+template <class Law, bool TAN, int PAIR = ERK_BS23>
 AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
                            const double (&zn)[stored_nz<Law>()], const Step& hs, const Ode23Ctl& ctl,
                            double (&sig)[6], double (&z)[stored_nz<Law>()], double* C36) {
-  Ode23Voxel<Law, TAN> v;
+  ErkVoxel<Law, TAN, PAIR> v;
   v.init(p, epsn, eps1, zn, hs.h);
   while (!v.done) v.attempt(p, hs, ctl);
   return v.finish(hs.h, sig, z, C36);

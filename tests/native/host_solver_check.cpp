@@ -12,7 +12,7 @@ using namespace gsm;
 // ode23 update, kind 1 (Norton, params E, nu, sigma0, edot0, n) or 2
 // (Michel-Suquet, params E, nu, sigma_Y, H, edot0, sigma_d, n); AoS eps_n,
 // eps [n][6], z_n and z [n][nz] (nz = 6 or 7); tangent [n][36] or NULL.
-template <class Law>
+template <class Law, int PAIR>
 void run_ode23(const LawParams<double>& p, int64_t n, const double* eps_n, const double* eps, const double* zn,
                const Step& hs, const Ode23Ctl& ctl, double* sig, double* z, double* tan, int32_t* status) {
   constexpr int NZ = stored_nz<Law>();
@@ -23,8 +23,8 @@ void run_ode23(const LawParams<double>& p, int64_t n, const double* eps_n, const
       e1[c] = eps[6 * i + c];
     }
     for (int c = 0; c < NZ; ++c) zi[c] = zn[NZ * i + c];
-    unsigned st = tan ? voxel_ode23<Law, true>(p, e0, e1, zi, hs, ctl, s, zo, tan + 36 * i)
-                      : voxel_ode23<Law, false>(p, e0, e1, zi, hs, ctl, s, zo, nullptr);
+    unsigned st = tan ? voxel_ode23<Law, true, PAIR>(p, e0, e1, zi, hs, ctl, s, zo, tan + 36 * i)
+                      : voxel_ode23<Law, false, PAIR>(p, e0, e1, zi, hs, ctl, s, zo, nullptr);
     for (int c = 0; c < 6; ++c) sig[6 * i + c] = s[c];
     for (int c = 0; c < NZ; ++c) z[NZ * i + c] = zo[c];
     status[i] = (int32_t)st;
@@ -59,8 +59,20 @@ int host_update_ode23(int kind, const double* prm, int64_t n, const double* eps_
   const LawParams<double> p = make_params(prm, kind);
   const Step hs = make_step(h);
   const Ode23Ctl ctl{rtol, atol, max_steps};
-  if (kind == 1) run_ode23<NortonDev>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
-  else run_ode23<MichelSuquet>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  if (kind == 1) run_ode23<NortonDev, ERK_BS23>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  else run_ode23<MichelSuquet, ERK_BS23>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  return 0;
+}
+
+// The same with the ode12 (explicit Euler / Heun) pair.
+int host_update_ode12(int kind, const double* prm, int64_t n, const double* eps_n, const double* eps,
+                      const double* zn, double h, double rtol, double atol, int max_steps, double* sig, double* z,
+                      double* tan, int32_t* status) {
+  const LawParams<double> p = make_params(prm, kind);
+  const Step hs = make_step(h);
+  const Ode23Ctl ctl{rtol, atol, max_steps};
+  if (kind == 1) run_ode23<NortonDev, ERK_HEUN12>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  else run_ode23<MichelSuquet, ERK_HEUN12>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
   return 0;
 }
 

@@ -232,18 +232,19 @@ def test_taped_run_rejects_mixed_conditions(gsm):
 ODE = (1e-8, 1e-11)
 
 
+@pytest.mark.parametrize("method", ["ode23", "ode12"])
 @pytest.mark.parametrize("kind,prm", [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS)])
-def test_ode23_scheme_homogeneous_grid(gsm, kind, prm):
+def test_ode23_scheme_homogeneous_grid(gsm, kind, prm, method):
     """A homogeneous grid is one voxel integrated from eps_{k-1} to eps_k by
     ode23 each step: the GPU scheme gives the oracle's history."""
     import torch
     ph = np.zeros((6, 6, 6), dtype=np.uint8)
     loads = synth.ramp(3, [0.004, -0.001, 0.0, 0.0, 0.002, 0.0])
-    ref = OMS.solve(ph, [(kind, prm)], loads, [0.1] * 3, tol=1e-12, ode=(1e-6, 1e-9))
+    ref = OMS.solve(ph, [(kind, prm)], loads, [0.1] * 3, tol=1e-12, ode=(1e-6, 1e-9), ode_method=method)
     z = torch.zeros(6, 216, dtype=torch.float64, device="cuda")
     eps = torch.zeros(6, 216, dtype=torch.float64, device="cuda")
     out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, [(kind, prm)]), loads, [0.1] * 3, tol=1e-12,
-                       ode=(1e-6, 1e-9), eps=eps, z=z)
+                       ode=(1e-6, 1e-9), ode_method=method, eps=eps, z=z)
     assert out["rc"] == 0 and np.all(out["iters"] == ref["iters"])
     assert rel(out["Sigma"], ref["Sigma"]) < 1e-10
     assert np.allclose(z.cpu().numpy().T, ref["z"][:, :6], rtol=1e-9, atol=1e-14)
@@ -270,6 +271,23 @@ def test_ode23_norton_composite_iteration_matched(gsm):
     assert rel(out["Sigma"], ref["Sigma"]) < 1e-9
     assert rel(eps.cpu().numpy().T, ref["eps"]) < 1e-8
     assert rel(z.cpu().numpy().T, ref["z"][:, :6]) < 1e-7
+
+
+def test_ode12_michel_suquet_composite_mixed_iteration_matched(gsm):
+    """The MMC with the ode12 pair (rtol 1e-6: the pair's substep count grows as
+    tol^(-1/2)), uniaxial stress, updated reference, the oracle's evaluation
+    counts."""
+    import torch
+    ph = synth.sphere_phase(8, 0.2)
+    laws = [(O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS), (O.KIND_ELASTIC, synth.ALUMINA)]
+    loads = synth.ramp(2, [0.003, 0, 0, 0, 0, 0])
+    forced = [12, 12]
+    kw = dict(forced_iters=forced, stress_mask=UNIAXIAL, ref_update=True, ode=(1e-6, 1e-9), ode_method="ode12")
+    ref = OMS.solve(ph, laws, loads, [0.5, 0.5], **kw)
+    out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.5, 0.5], **kw)
+    assert rel(out["Sigma"], ref["Sigma"]) < 1e-9
+    assert rel(out["E"], ref["E"]) < 1e-9
+    assert np.allclose(out["reference"], ref["reference"], rtol=1e-9, atol=0)
 
 
 def test_ode23_michel_suquet_composite_mixed_iteration_matched(gsm):

@@ -23,7 +23,7 @@ def soa(a, ld):
     return torch.from_numpy(out).cuda()
 
 
-def run(G, mat, en, e, zn, h, rtol=1e-3, atol=1e-6, tangent=False, ld=None, max_substeps=100000):
+def run(G, mat, en, e, zn, h, rtol=1e-3, atol=1e-6, tangent=False, ld=None, max_substeps=100000, method="ode23"):
     import torch
     n = e.shape[0]
     ld = ld or n
@@ -32,7 +32,8 @@ def run(G, mat, en, e, zn, h, rtol=1e-3, atol=1e-6, tangent=False, ld=None, max_
     z = torch.full_like(E1, float("nan"))
     tan = torch.full((36, ld), float("nan"), dtype=torch.float64, device="cuda") if tangent else None
     st = torch.zeros(ld, dtype=torch.int32, device="cuda")
-    G.gsm_update_ode23(mat, E0, E1, Z0, h, sig, z, tan, st, rtol=rtol, atol=atol, max_substeps=max_substeps, n_vox=n)
+    G.gsm_update_ode23(mat, E0, E1, Z0, h, sig, z, tan, st, rtol=rtol, atol=atol, max_substeps=max_substeps, n_vox=n,
+                       method=method)
     torch.cuda.synchronize()
     out = [sig.cpu().numpy()[:, :n].T, z.cpu().numpy()[:, :n].T, st.cpu().numpy()[:n]]
     if tangent:
@@ -190,3 +191,52 @@ def test_michel_suquet_is_refused_by_the_implicit_paths(gsm):
     out = gsm.ms_run(ctx, [[0.001, 0, 0, 0, 0, 0]], [0.1], check=False)
     gsm.ms_destroy(ctx)
     assert out["rc"] == gsm.GSM_ENOTSUP
+
+
+# ------------------------------------------------------------ ode12 (Sec. 4.3)
+
+@pytest.mark.parametrize("tangent", [False, True])
+@pytest.mark.parametrize("n_exp", [1.0, 5.0])
+def test_ode12_matches_oracle(gsm, tangent, n_exp):
+    """The explicit Euler / Heun pair (gsm_update_ode, GSM_ODE12) against the
+    oracle's ode12, several blocks and a ragged tail."""
+    prm = synth.MATRIX_16[:4] + (n_exp,)
+    n = 2 * 4096 + 37 if not tangent else 2048 + 37
+    en, e, zn = synth.ode23_batch(n, seed=int(n_exp * 3) + 70 + int(tangent))
+    res = run(gsm, gsm.norton(*prm), en, e, zn, 0.1, tangent=tangent, ld=n + 3, method="ode12")
+    ref = O.update_ode23(prm, en, e, zn, 0.1, tangent=tangent, info=True, method="ode12")
+    check(res, ref, zn, 1e-3, 1e-6, tangent)
+
+
+def test_ode12_michel_suquet_matches_oracle(gsm):
+    prm = synth.ALUMINIUM_MS
+    n = 4096 + 11
+    en, e, zn6 = synth.ode23_batch(n, seed=77)
+    alpha_n = np.random.default_rng(9).uniform(0.0, 0.01, n)
+    zn7 = np.concatenate([zn6, alpha_n[:, None]], axis=1)
+    import torch
+    E0, E1, Z0 = soa(en, n), soa(e, n), soa(zn7, n)
+    sig = torch.empty_like(E1)
+    z = torch.empty(7, n, dtype=torch.float64, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    gsm.gsm_update_ode23(gsm.michel_suquet(*prm), E0, E1, Z0, 0.1, sig, z, None, st, method="ode12")
+    ref = O.update_ode23(prm, en, e, zn6, 0.1, info=True, kind=O.KIND_MICHEL_SUQUET, alpha_n=alpha_n, method="ode12")
+    s, zz, stt = sig.cpu().numpy().T, z.cpu().numpy().T, st.cpu().numpy()
+    assert np.all((stt >> 16) & 1)
+    rel = np.abs(s - ref[0]).max(1) / np.abs(ref[0]).max(1)
+    da = np.abs(zz[:, 6] - ref[2])
+    tight = (rel < 1e-10) & (da <= 1e-10 * np.maximum(ref[2] - alpha_n, 1e-300) + 1e-18)
+    assert tight.mean() >= 0.98
+    assert np.all(np.abs(s - ref[0]) <= 10 * (1e-3 * np.abs(ref[0]).max(1, keepdims=True) + 1e-6))
+
+
+def test_ode_method_is_checked(gsm):
+    import ctypes
+    import torch
+    t = torch.zeros(6, 4, dtype=torch.float64, device="cuda")
+    mat = gsm.norton(*synth.MATRIX_16)
+    lib = gsm.load()
+    rc = lib.gsm_update_ode(mat.handle, 7, 4, t.data_ptr(), t.data_ptr(), t.data_ptr(), 4, ctypes.c_double(0.1),
+                            ctypes.c_double(1e-3), ctypes.c_double(1e-6), 100, t.clone().data_ptr(),
+                            t.clone().data_ptr(), None, None, None)
+    assert rc == gsm.GSM_EINVAL

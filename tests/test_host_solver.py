@@ -139,16 +139,17 @@ def test_host_solver_small_trial_states(hlib, case, mode):
             assert np.all(np.abs(z - z2).max(1) <= bound)
 
 
-def _ode23_host(hlib, prm, en, e, zn, h, rtol, atol, tangent, kind=1):
+def _ode23_host(hlib, prm, en, e, zn, h, rtol, atol, tangent, kind=1, method="ode23"):
     n = e.shape[0]
     nz = zn.shape[1]
     sig, z = np.empty((n, 6)), np.empty((n, nz))
     st = np.empty(n, dtype=np.int32)
     C = np.empty((n, 36)) if tangent else None
     prm = np.asarray(list(prm) + [0.0] * (7 - len(prm)), dtype=float)
-    hlib.host_update_ode23(kind, P(prm), ctypes.c_int64(n), P(en), P(e), P(np.ascontiguousarray(zn)),
-                           ctypes.c_double(h), ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(100000),
-                           P(sig), P(z), P(C) if tangent else None, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    fn = hlib.host_update_ode23 if method == "ode23" else hlib.host_update_ode12
+    fn(kind, P(prm), ctypes.c_int64(n), P(en), P(e), P(np.ascontiguousarray(zn)),
+       ctypes.c_double(h), ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(100000),
+       P(sig), P(z), P(C) if tangent else None, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return sig, z, C, st
 
 
@@ -219,3 +220,28 @@ def test_host_ode23_michel_suquet_tangent_from_the_virgin_state(hlib):
     assert np.allclose(sig, out[0], rtol=1e-10, atol=1e-16)
     C2 = out[3].reshape(-1, 36)
     assert np.all(np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9)
+
+
+@pytest.mark.parametrize("tangent", [False, True])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_host_ode12_matches_oracle(hlib, tangent, kind):
+    """The AD-driven ode12 (Euler/Heun pair) against the oracle's hand-derived
+    one, Norton and Michel-Suquet, under the same flip-tolerant criterion as
+    ode23."""
+    prm = synth.MATRIX_16 if kind == 1 else synth.ALUMINIUM_MS
+    en, e, zn6 = synth.ode23_batch(300, seed=61 + kind + int(tangent))
+    alpha_n = np.random.default_rng(7).uniform(0.0, 0.01, 300) if kind == 2 else None
+    zn = zn6 if kind == 1 else np.concatenate([zn6, alpha_n[:, None]], axis=1)
+    sig, z, C, st = _ode23_host(hlib, prm, en, e, zn, 0.1, 1e-3, 1e-6, tangent, kind=kind, method="ode12")
+    kw = {"alpha_n": alpha_n} if kind == 2 else {}
+    out = O.update_ode23(prm, en, e, zn6, 0.1, tangent=tangent, info=True, kind=kind, method="ode12", **kw)
+    assert np.all((st >> 16) & 1) and np.all(out[-1][:, 2] == 1)
+    rel = np.abs(sig - out[0]).max(1) / np.abs(out[0]).max(1)
+    relz = np.abs(z[:, :6] - out[1]).max(1) / np.maximum(np.abs(out[1] - zn6).max(1), 1e-300)
+    tight = (rel < 1e-10) & (relz < 1e-10)
+    same = ((st & 0xFFFF) == out[-1][:, 0]) & (((st >> 20) & 0x7FF) == out[-1][:, 1])
+    if tangent:
+        C2 = out[3 if kind == 2 else 2].reshape(-1, 36)
+        tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98 and same.mean() >= 0.98
+    assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))

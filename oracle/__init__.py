@@ -23,5 +23,5 @@ closed forms, finite differences, invariants and special cases instead.
 from .material import (  # noqa: F401
     KIND_ELASTIC, KIND_NORTON, lame, update, radial_return, psi, psi_y, psi_yy,
     phi, phi_v, phi_vv, residual, newton_matrix, incremental_potential, stress,
-    max_threads, P_MATRIX, G_MATRIX, update_ode23, psi_force_a, psi_force_ms, gen_stress_ms, KIND_MICHEL_SUQUET,
+    max_threads, P_MATRIX, G_MATRIX, update_ode23, psi_force_a, psi_force_ms, psi_force_aaa, gen_stress_ms, KIND_MICHEL_SUQUET,
 )

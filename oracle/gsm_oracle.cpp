@@ -940,6 +940,359 @@ void update_ode12(const Law& L, const double epsn[6], const double eps1[6], cons
   if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
 }
 
+// Dense solve of W x = b (W general, n <= 6) by Gaussian elimination with
+// partial pivoting; false if W is singular.
+bool gauss_solve(int n, const double* W, const double* b, double* x) {
+  double M[6][7];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) M[i][j] = W[i * n + j];
+    M[i][n] = b[i];
+  }
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j <= n; ++j) std::swap(M[c][j], M[piv][j]);
+    for (int r = c + 1; r < n; ++r) {
+      const double f = M[r][c] / M[c][c];
+      for (int j = c; j <= n; ++j) M[r][j] -= f * M[c][j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = M[i][n];
+    for (int j = i + 1; j < n; ++j) t -= M[i][j] * x[j];
+    x[i] = t / M[i][i];
+  }
+  return true;
+}
+
+// Third derivative of the force potential contracted with two directions u,
+// v (NY entries each): out = Psi_AAA[u, v].  Both laws have the form Psi =
+// sigma0 edot0/(n+1) (x^+/sigma0)^(n+1) with x = s (Norton) or s + A_alpha
+// (Michel-Suquet), s^2 = A_z^T G^-1 A_z.  With m = G^-1 A_z / s, Q = G^-1 - m
+// m^T and r(x) = edot0 (x/sigma0)^n the Hessian is H_zz = r' m m^T + r Q/s,
+// H_za = r' m, H_aa = r'; its derivative along u, with dx = m.u_z + u_a,
+// ds = m.u_z, dm = Q u_z/s:
+//   dH_zz = r'' dx m m^T + (r' - r/s)(dm m^T + m dm^T) + (r' dx - r ds/s) Q/s,
+//   dH_za = r'' dx m + r' dm,  dH_aa = r'' dx.
+// Zero where the potential is inactive (x <= 0) or s = 0.
+template <int NY>
+void psi_force_aaa(const Law& L, const double Gi[5][5], const double A[NY], const double u[NY], const double v[NY],
+                   double out[NY]) {
+  for (int a = 0; a < NY; ++a) out[a] = 0.0;
+  double GA[5], s2 = 0.0;
+  for (int a = 0; a < 5; ++a) {
+    double t = 0.0;
+    for (int b = 0; b < 5; ++b) t += Gi[a][b] * A[b];
+    GA[a] = t;
+    s2 += A[a] * t;
+  }
+  const double s = std::sqrt(s2);
+  const double x = NY == 6 ? s + A[5] : s;
+  if (!(x > 0.0) || s == 0.0) return;
+  const double n = L.n, sg = L.sigma0, e0 = L.edot0;
+  const double r = e0 * std::pow(x / sg, n);
+  const double r1 = n * e0 / sg * std::pow(x / sg, n - 1.0);
+  const double r2 = n * (n - 1.0) * e0 / (sg * sg) * std::pow(x / sg, n - 2.0);
+  double m[5], Q[5][5], dm[5];
+  for (int a = 0; a < 5; ++a) m[a] = GA[a] / s;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) Q[a][b] = Gi[a][b] - m[a] * m[b];
+  double ds = 0.0;
+  for (int a = 0; a < 5; ++a) ds += m[a] * u[a];
+  const double dx = ds + (NY == 6 ? u[5] : 0.0);
+  for (int a = 0; a < 5; ++a) {
+    double t = 0.0;
+    for (int b = 0; b < 5; ++b) t += Q[a][b] * u[b];
+    dm[a] = t / s;
+  }
+  double mv = 0.0, dmv = 0.0;
+  for (int a = 0; a < 5; ++a) {
+    mv += m[a] * v[a];
+    dmv += dm[a] * v[a];
+  }
+  const double va = NY == 6 ? v[5] : 0.0;
+  for (int a = 0; a < 5; ++a) {
+    double Qv = 0.0;
+    for (int b = 0; b < 5; ++b) Qv += Q[a][b] * v[b];
+    out[a] = r2 * dx * m[a] * mv + (r1 - r / s) * (dm[a] * mv + m[a] * dmv) + (r1 * dx - r * ds / s) * Qv / s +
+             (r2 * dx * m[a] + r1 * dm[a]) * va;
+  }
+  if (NY == 6) out[5] = r2 * dx * mv + r1 * dmv + r2 * dx * va;
+}
+
+// Generalized-stress sensitivities of the force-potential ODE: dA/dy (NY x
+// NY; dA_z/dz = -P^T (C + 2/3 Hv) P, zero for alpha) and dA/dt (NY; dA_z/dt
+// = P^T C (eps_{n+1} - eps_n)/h).
+template <int NY>
+void gen_stress_sens(const Law& L, const double epsn[6], const double eps1[6], double h, double dAdy[NY][NY],
+                     double dAdt[NY]) {
+  for (int a = 0; a < NY; ++a) {
+    dAdt[a] = 0.0;
+    for (int b = 0; b < NY; ++b) dAdy[a][b] = 0.0;
+  }
+  for (int a = 0; a < 5; ++a) {
+    for (int b = 0; b < 5; ++b) {
+      double t = 0.0;
+      for (int i = 0; i < 6; ++i) {
+        const double hv = i < 3 ? L.Hkin : 0.5 * L.Hkin;
+        for (int j = 0; j < 6; ++j) t += P[i][a] * (L.C[i][j] + (i == j ? (2.0 / 3.0) * hv : 0.0)) * P[j][b];
+      }
+      dAdy[a][b] = -t;
+    }
+    double t = 0.0;
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) t += P[i][a] * L.C[i][j] * (eps1[j] - epsn[j]);
+    dAdt[a] = t / h;
+  }
+}
+
+// Psi_AA at the generalized stress of (t, y).
+template <int NY>
+void force_hessian_at(const Law& L, const double Gi[5][5], const double epsn[6], const double eps1[6], double h,
+                      double t, const double y[NY], double A[NY], double H[NY][NY]) {
+  const double th = t / h;
+  double et[6];
+  for (int i = 0; i < 6; ++i) et[i] = epsn[i] + th * (eps1[i] - epsn[i]);
+  gen_stress<NY>(L, et, y, A);
+  double g[6];
+  if (NY == 5) {
+    double H5[5][5];
+    psi_force_a(L, Gi, A, g, H5);
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) H[a][b] = H5[a][b];
+  } else {
+    double H6[6][6];
+    psi_force_ms(L, Gi, A, g, H6);
+    for (int a = 0; a < NY; ++a)
+      for (int b = 0; b < NY; ++b) H[a][b] = H6[a][b];
+  }
+}
+
+// One material update by ode23s, the modified Rosenbrock triple of Shampine
+// and Reichelt (SIAM J. Sci. Comput. 18 (1997) 1-22; MATLAB's ode23s), Sec.
+// 4.3.  With d = 1/(2 + sqrt 2), e32 = 6 + sqrt 2, J = df/dy and T = df/dt
+// at the start (t, y) of a substep of length dt and W = I - dt d J:
+//   k1 = W^-1 (F0 + dt d T),          F0 = f(t, y)
+//   F1 = f(t + dt/2, y + dt/2 k1),   k2 = W^-1 (F1 - k1) + k1
+//   y_new = y + dt k2,               F2 = f(t + dt, y_new)
+//   k3 = W^-1 (F2 - e32 (k2 - F1) - 2 (k1 - F0) + dt d T)
+//   error estimate dt/6 (k1 - 2 k2 + k3)
+// The error compares the stresses of y_new and y_new minus the estimate (as
+// ode23 compares its two solutions); step control as ode23's (exponent 1/3);
+// F2 is F0 of the next substep, J and T are re-evaluated at the accepted point.
+// Tangent (Corollary 1, the Rosenbrock form of the stage derivatives): for
+// each column k of Y = dy/deps_{n+1}, with dA_k the total derivative of A,
+//   J~_k w = Psi_AAA[dA_k, dA/dy w],  T~_k = Psi_AAA[dA_k, dA/dt] + Psi_AA d2A_k,
+//   d2A_k = d(dA/dt)/deps_k = P^T C e_k / h,
+//   k1~ = W^-1 (F0~ + dt d T~ + dt d J~ k1)
+//   k2~ = k1~ + W^-1 (F1~ - k1~ + dt d J~ (k2 - k1))
+//   k3~ = W^-1 (F2~ - e32 (k2~ - F1~) - 2 (k1~ - F0~) + dt d T~ + dt d J~ k3)
+// with Fi~ the tangent right-hand sides (ode_rhs) at the stage states.
+template <int NY>
+void update_ode23s(const Law& L, const double epsn[6], const double eps1[6], const double zn[6], double alpha_n,
+                   double h, const Ode23Opts& o, double sig_out[6], double z_out[6], double* alpha_out,
+                   double (*Ct_out)[6], OdeInfo* info) {
+  const double d = 1.0 / (2.0 + std::sqrt(2.0)), e32 = 6.0 + std::sqrt(2.0);
+  double Gi[5][5];
+  g_inverse(L, Gi);
+  double dAdy[NY][NY], dAdt[NY];
+  gen_stress_sens<NY>(L, epsn, eps1, h, dAdy, dAdt);
+  double y[NY];
+  y[0] = zn[0];
+  y[1] = zn[1];
+  y[2] = zn[3];
+  y[3] = zn[4];
+  y[4] = zn[5];
+  if (NY == 6) y[NY - 1] = alpha_n;
+  double Y[NY][6] = {};
+  const bool tan = o.tangent;
+  double F0[NY], G0[NY][6];
+  ode_rhs<NY>(L, Gi, epsn, eps1, h, 0.0, y, Y, F0, tan ? G0 : nullptr);
+  double sig_old[6], C_old[6][6];
+  stress_tangent<NY>(L, epsn, eps1, h, 0.0, y, Y, sig_old, tan ? C_old : nullptr);
+  // J, T (and Psi_AA, A for the tangent) at the start of the substep
+  double A0[NY], H0[NY][NY], J[NY][NY], T[NY];
+  auto refresh = [&](double t) {
+    force_hessian_at<NY>(L, Gi, epsn, eps1, h, t, y, A0, H0);
+    for (int a = 0; a < NY; ++a) {
+      double tt = 0.0;
+      for (int b = 0; b < NY; ++b) tt += H0[a][b] * dAdt[b];
+      T[a] = tt;
+      for (int b = 0; b < NY; ++b) {
+        double jj = 0.0;
+        for (int c = 0; c < NY; ++c) jj += H0[a][c] * dAdy[c][b];
+        J[a][b] = jj;
+      }
+    }
+  };
+  refresh(0.0);
+  info->accepted = info->rejected = 0;
+  info->flags = 0;
+  bool last_rejected = false;
+  double t = 0.0, dt = h;
+  while (t < h) {
+    if (info->accepted + info->rejected >= o.max_steps) {
+      info->flags |= F_CAP;
+      break;
+    }
+    const bool clip = t + dt >= h;
+    if (clip) dt = h - t;
+    const double tn1 = clip ? h : t + dt;
+    double W[NY * NY];
+    for (int a = 0; a < NY; ++a)
+      for (int b = 0; b < NY; ++b) W[a * NY + b] = (a == b ? 1.0 : 0.0) - dt * d * J[a][b];
+    bool ok = true;
+    double rhs[NY], k1[NY], k2[NY], k3[NY], F1[NY], F2[NY], ys[NY], yn1[NY], e[NY];
+    for (int a = 0; a < NY; ++a) rhs[a] = F0[a] + dt * d * T[a];
+    ok &= gauss_solve(NY, W, rhs, k1);
+    for (int a = 0; a < NY; ++a) ys[a] = y[a] + 0.5 * dt * k1[a];
+    double Ys[NY][6], G1[NY][6], G2[NY][6], K1[NY][6], K2[NY][6], K3[NY][6], Yn1[NY][6], E[NY][6];
+    // the tangent stages need F1~ at y + dt/2 k1 with Y + dt/2 k1~: k1~ first
+    double dA[6][NY];  // total dA/deps_k at (t, y, Y), column k
+    if (tan) {
+      for (int k = 0; k < 6; ++k) {
+        double th = t / h;
+        for (int a = 0; a < NY; ++a) {
+          double v = 0.0;
+          for (int b = 0; b < NY; ++b) v += dAdy[a][b] * Y[b][k];
+          if (a < 5)
+            for (int i = 0; i < 6; ++i) v += th * P[i][a] * L.C[i][k];
+          dA[k][a] = v;
+        }
+      }
+    }
+    // J~_k w for the k-th column
+    auto Jt = [&](int k, const double w[NY], double out[NY]) {
+      double v[NY];
+      for (int a = 0; a < NY; ++a) {
+        double tt = 0.0;
+        for (int b = 0; b < NY; ++b) tt += dAdy[a][b] * w[b];
+        v[a] = tt;
+      }
+      psi_force_aaa<NY>(L, Gi, A0, dA[k], v, out);
+    };
+    double Tt[6][NY];
+    if (tan)
+      for (int k = 0; k < 6; ++k) {
+        psi_force_aaa<NY>(L, Gi, A0, dA[k], dAdt, Tt[k]);
+        for (int a = 0; a < NY; ++a) {
+          double tt = 0.0;
+          for (int b = 0; b < 5; ++b) {
+            double d2 = 0.0;
+            for (int i = 0; i < 6; ++i) d2 += P[i][b] * L.C[i][k];
+            tt += H0[a][b] * d2 / h;
+          }
+          Tt[k][a] += tt;
+        }
+        double jk[NY], r2[NY], col[NY];
+        Jt(k, k1, jk);
+        for (int a = 0; a < NY; ++a) r2[a] = G0[a][k] + dt * d * Tt[k][a] + dt * d * jk[a];
+        ok &= gauss_solve(NY, W, r2, col);
+        for (int a = 0; a < NY; ++a) {
+          K1[a][k] = col[a];
+          Ys[a][k] = Y[a][k] + 0.5 * dt * col[a];
+        }
+      }
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, t + 0.5 * dt, ys, Ys, F1, tan ? G1 : nullptr);
+    for (int a = 0; a < NY; ++a) rhs[a] = F1[a] - k1[a];
+    double w2[NY];
+    ok &= gauss_solve(NY, W, rhs, w2);
+    for (int a = 0; a < NY; ++a) {
+      k2[a] = w2[a] + k1[a];
+      yn1[a] = y[a] + dt * k2[a];
+    }
+    if (tan)
+      for (int k = 0; k < 6; ++k) {
+        double dk[NY], jk[NY], r2[NY], col[NY];
+        for (int a = 0; a < NY; ++a) dk[a] = k2[a] - k1[a];
+        Jt(k, dk, jk);
+        for (int a = 0; a < NY; ++a) r2[a] = G1[a][k] - K1[a][k] + dt * d * jk[a];
+        ok &= gauss_solve(NY, W, r2, col);
+        for (int a = 0; a < NY; ++a) {
+          K2[a][k] = K1[a][k] + col[a];
+          Yn1[a][k] = Y[a][k] + dt * K2[a][k];
+        }
+      }
+    ode_rhs<NY>(L, Gi, epsn, eps1, h, tn1, yn1, Yn1, F2, tan ? G2 : nullptr);
+    for (int a = 0; a < NY; ++a) rhs[a] = F2[a] - e32 * (k2[a] - F1[a]) - 2.0 * (k1[a] - F0[a]) + dt * d * T[a];
+    ok &= gauss_solve(NY, W, rhs, k3);
+    for (int a = 0; a < NY; ++a) e[a] = dt / 6.0 * (k1[a] - 2.0 * k2[a] + k3[a]);
+    if (tan)
+      for (int k = 0; k < 6; ++k) {
+        double jk[NY], r2[NY], col[NY];
+        Jt(k, k3, jk);
+        for (int a = 0; a < NY; ++a)
+          r2[a] = G2[a][k] - e32 * (K2[a][k] - G1[a][k]) - 2.0 * (K1[a][k] - G0[a][k]) + dt * d * Tt[k][a] +
+                  dt * d * jk[a];
+        ok &= gauss_solve(NY, W, r2, col);
+        for (int a = 0; a < NY; ++a) {
+          K3[a][k] = col[a];
+          E[a][k] = dt / 6.0 * (K1[a][k] - 2.0 * K2[a][k] + K3[a][k]);
+        }
+      }
+    double y2[NY], Y2[NY][6], s3[6], s2[6], C3[6][6], C2[6][6];
+    for (int a = 0; a < NY; ++a) {
+      y2[a] = yn1[a] - e[a];
+      if (tan)
+        for (int c = 0; c < 6; ++c) Y2[a][c] = Yn1[a][c] - E[a][c];
+    }
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, yn1, Yn1, s3, tan ? C3 : nullptr);
+    stress_tangent<NY>(L, epsn, eps1, h, tn1, y2, Y2, s2, tan ? C2 : nullptr);
+    double sum = 0.0;
+    int m = 0;
+    auto sq_scaled = [](double dd, double sc) {
+      const double q = sc > 0.0 ? dd / sc : (dd == 0.0 ? 0.0 : 1e300);
+      return q * q;
+    };
+    for (int i = 0; i < 6; ++i, ++m)
+      sum += sq_scaled(s3[i] - s2[i], o.atol + o.rtol * std::fmax(std::fabs(sig_old[i]), std::fabs(s3[i])));
+    if (tan)
+      for (int i = 0; i < 6; ++i)
+        for (int c = 0; c < 6; ++c, ++m)
+          sum += sq_scaled(C3[i][c] - C2[i][c], o.atol + o.rtol * std::fmax(std::fabs(C_old[i][c]), std::fabs(C3[i][c])));
+    // a singular W or an overflow rejects the trial step
+    const double err = ok && std::isfinite(sum) ? std::sqrt(sum / m) : 1e300;
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    const double grow = err == 0.0 ? facmax : std::fmin(facmax, std::fmax(0.2, 0.9 * std::pow(err, -1.0 / 3.0)));
+    if (err <= 1.0) {
+      t = tn1;
+      for (int a = 0; a < NY; ++a) {
+        y[a] = yn1[a];
+        F0[a] = F2[a];
+        if (tan)
+          for (int c = 0; c < 6; ++c) {
+            Y[a][c] = Yn1[a][c];
+            G0[a][c] = G2[a][c];
+          }
+      }
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = s3[i];
+        if (tan)
+          for (int c = 0; c < 6; ++c) C_old[i][c] = C3[i][c];
+      }
+      refresh(t);
+      ++info->accepted;
+      last_rejected = false;
+    } else {
+      ++info->rejected;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+  if (t >= h && !(info->flags & (F_NONFINITE | F_CAP))) info->flags |= F_CONVERGED;
+  stress_tangent<NY>(L, epsn, eps1, h, h, y, Y, sig_out, Ct_out);
+  z_out[0] = y[0];
+  z_out[1] = y[1];
+  z_out[2] = -(y[0] + y[1]);
+  z_out[3] = y[2];
+  z_out[4] = y[3];
+  z_out[5] = y[4];
+  if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -1048,11 +1401,12 @@ void ora_newton_matrix_batch(const double* params, int64_t n, const double* y, c
 // E, nu, sigma_Y, H, edot0, sigma_d, n); eps_n, eps, z_n [n][6]; alpha_n,
 // alpha [n] (kind 2; alpha_n may be NULL = 0); tangent [n][6][6] or NULL;
 // info [n][3] = accepted, rejected substeps, flags (1 converged, 4 substep cap).
-// method 0 = ode23 (Bogacki-Shampine 3(2)), 1 = ode12 (explicit Euler / Heun).
+// method 0 = ode23 (Bogacki-Shampine 3(2)), 1 = ode12 (explicit Euler / Heun),
+// 2 = ode23s (Shampine-Reichelt Rosenbrock triple).
 int ora_update_ode(int kind, int method, const double* params, int64_t n, const double* eps_n, const double* eps,
                    const double* zn, const double* alpha_n, double h, double rtol, double atol, int max_steps,
                    double* sigma, double* z, double* alpha, double* tangent, int32_t* info) {
-  if ((kind != 1 && kind != 2) || (method != 0 && method != 1)) return -1;
+  if ((kind != 1 && kind != 2) || method < 0 || method > 2) return -1;
   Law L;
   make_law(kind, params, &L);
   Ode23Opts o{rtol, atol, max_steps, tangent != nullptr};
@@ -1065,13 +1419,18 @@ int ora_update_ode(int kind, int method, const double* params, int64_t n, const 
     if (kind == 1 && method == 0)
       update_ode23<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
                       &inf);
-    else if (kind == 1)
+    else if (kind == 1 && method == 1)
       update_ode12<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
                       &inf);
+    else if (kind == 1)
+      update_ode23s<5>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, 0.0, h, o, sigma + 6 * i, z + 6 * i, nullptr, Ct,
+                       &inf);
     else if (method == 0)
       update_ode23<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, a0, h, o, sigma + 6 * i, z + 6 * i, &al, Ct, &inf);
-    else
+    else if (method == 1)
       update_ode12<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, a0, h, o, sigma + 6 * i, z + 6 * i, &al, Ct, &inf);
+    else
+      update_ode23s<6>(L, eps_n + 6 * i, eps + 6 * i, zn + 6 * i, a0, h, o, sigma + 6 * i, z + 6 * i, &al, Ct, &inf);
     if (alpha) alpha[i] = al;
     if (info) {
       info[3 * i] = inf.accepted;
@@ -1080,6 +1439,17 @@ int ora_update_ode(int kind, int method, const double* params, int64_t n, const 
     }
   }
   return 0;
+}
+
+// Psi_AAA[u, v] of the Norton (kind 1, NY = 5) or Michel-Suquet (kind 2, NY = 6) force potential.
+void ora_psi_force_aaa(int kind, const double* params, const double* A, const double* u, const double* v,
+                       double* out) {
+  Law L;
+  make_law(kind, params, &L);
+  double Gi[5][5];
+  g_inverse(L, Gi);
+  if (kind == 1) psi_force_aaa<5>(L, Gi, A, u, v, out);
+  else psi_force_aaa<6>(L, Gi, A, u, v, out);
 }
 
 // Michel-Suquet force potential Psi(A) at A [6] = (A_y, A_alpha); g [6], H [6][6] or NULL.

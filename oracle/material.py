@@ -68,6 +68,7 @@ def _load():
         lib.ora_update_ode.restype = ctypes.c_int
         lib.ora_psi_force_a.argtypes = [_dp, _dp, _dp, _dp]
         lib.ora_psi_force_ms.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_psi_force_aaa.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
         lib.ora_psi_force_ms.restype = ctypes.c_double
         lib.ora_gen_stress_ms.argtypes = [_dp, _dp, _dp, _dp]
         _lib = lib
@@ -212,13 +213,14 @@ def newton_matrix_batch(params, y, y_n, h):
     return K, H
 
 
-ODE_METHODS = {"ode23": 0, "ode12": 1}
+ODE_METHODS = {"ode23": 0, "ode12": 1, "ode23s": 2}
 
 
 def update_ode23(params, eps_n, eps, z_n, h, rtol=1e-3, atol=1e-6, max_steps=100000, tangent=False, info=False,
                  kind=KIND_NORTON, alpha_n=None, method="ode23"):
     """Material update by ode23 (Sec. 4.3, stress-driven error control Sec. 4.5),
-    or by ode12 (explicit Euler / Heun pair, same control) with method="ode12".
+    or by ode12 (explicit Euler / Heun pair, same control) with method="ode12",
+    or by ode23s (Shampine-Reichelt Rosenbrock triple) with method="ode23s".
 
     kind KIND_NORTON: params (E, nu, sigma0, edot0, n); KIND_MICHEL_SUQUET:
     params (E, nu, sigma_Y, H, edot0, sigma_d, n) with the equivalent plastic
@@ -281,3 +283,14 @@ def psi_force_a(params, A):
     H = np.zeros((5, 5))
     lib.ora_psi_force_a(_ptr(_params(params)), _ptr(A), _ptr(g), _ptr(H))
     return g, H
+
+
+def psi_force_aaa(params, A, u, v, kind=KIND_NORTON):
+    """Psi_AAA[u, v] of the force potential (Norton: 5 entries; Michel-Suquet: 6)."""
+    lib = _load()
+    k = 5 if kind == KIND_NORTON else 6
+    out = np.zeros(k)
+    prm = _f64(list(params) + [0.0] * (7 - len(params)))
+    lib.ora_psi_force_aaa(int(kind), _ptr(prm), _ptr(_f64(A).reshape(k)), _ptr(_f64(u).reshape(k)),
+                          _ptr(_f64(v).reshape(k)), _ptr(out))
+    return out

@@ -204,7 +204,8 @@ def solve(phase, laws, loads, hs, tol=1e-8, max_iter=10000, forced_iters=None,
                    force-potential form over each step by ode23 from the strain
                    of the previous step (Sec. 4.3); the internal variables then
                    have 7 columns (z, alpha) when a phase is a Michel-Suquet law.
-    ode_method   : "ode23" or "ode12" (explicit Euler / Heun pair).
+    ode_method   : "ode23", "ode12" (explicit Euler / Heun pair) or "ode23s"
+                   (Shampine-Reichelt Rosenbrock triple).
 
     Returns dict with Sigma (n_steps, 6), iters (n_steps,), errors (list per
     step), eps and z (N^3, 6) at the end, and the per-step (eps, z) history if

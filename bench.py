@@ -510,18 +510,22 @@ def bench_ode23(G, torch, args):
                                        "mean_accepted_substeps": float((s & 0xFFFF).mean()),
                                        "mean_rejected_substeps": float(((s >> 20) & 0x7FF).mean()),
                                        "converged_fraction": float(((s >> 16) & 1).mean())}
-    # ode12 (explicit Euler / Heun pair), same inputs; with the tangent on the first 2^20 voxels
-    for name, m, tan in (("ode12_no_tangent", n, None),
-                         ("ode12_tangent", 1 << 20, torch.empty(36, 1 << 20, dtype=torch.float64, device="cuda"))):
+    # ode12 (explicit Euler / Heun pair) and ode23s (Rosenbrock triple), same inputs; with
+    # the tangent on the first 2^20 (ode12) or 2^18 (ode23s) voxels
+    for name, meth, m, tan in (
+            ("ode12_no_tangent", "ode12", n, None),
+            ("ode12_tangent", "ode12", 1 << 20, torch.empty(36, 1 << 20, dtype=torch.float64, device="cuda")),
+            ("ode23s_no_tangent", "ode23s", n, None),
+            ("ode23s_tangent", "ode23s", 1 << 18, torch.empty(36, 1 << 18, dtype=torch.float64, device="cuda"))):
         views = [t[:, :m].contiguous() for t in (E0, E1, Z0)]
         sg, zz = torch.empty_like(views[1]), torch.empty_like(views[1])
         st2 = torch.empty(m, dtype=torch.int32, device="cuda")
-        G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method="ode12")
+        G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method=meth)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(3):
-            G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method="ode12")
+            G.gsm_update_ode23(mat, *views, 0.1, sg, zz, tan, st2, method=meth)
         b.record(stream)
         torch.cuda.synchronize()
         t_ms = a.elapsed_time(b) / 3

@@ -153,13 +153,18 @@ int gsm_update_ode23(gsm_handle h, int64_t n_vox, const void* eps_n, const void*
 #define GSM_ODE23 0              /* Bogacki-Shampine 3(2) (MATLAB's ode23)              */
 #define GSM_ODE12 1              /* explicit Euler (order 1) / Heun (order 2), continued
                                     with Heun's solution; step exponent 1/2            */
+#define GSM_ODE23S 2             /* Shampine-Reichelt modified Rosenbrock triple
+                                    (MATLAB's ode23s): linearly implicit, for stiff
+                                    steps; its tangent uses a hand third derivative
+                                    of the force potential (Sec. 4.3)                  */
 
 /*
- * gsm_update_ode -- gsm_update_ode23 with the pair chosen by `method`
- * (GSM_ODE23 or GSM_ODE12; anything else: GSM_EINVAL).  Same arguments,
- * layouts, status word and errors; gsm_update_ode23 is method GSM_ODE23.
- * ode12 evaluates the right-hand side twice per substep and needs about
- * tol^(-1/2) substeps (ode23: tol^(-1/3)).
+ * gsm_update_ode -- gsm_update_ode23 with the integrator chosen by `method`
+ * (GSM_ODE23, GSM_ODE12 or GSM_ODE23S; anything else: GSM_EINVAL).  Same
+ * arguments, layouts, status word and errors; gsm_update_ode23 is method
+ * GSM_ODE23.  ode12 evaluates the right-hand side twice per substep and needs
+ * about tol^(-1/2) substeps (ode23: tol^(-1/3)); ode23s solves three NY x NY
+ * linear systems per substep and is not limited by stiffness.
  */
 int gsm_update_ode(gsm_handle h, int method, int64_t n_vox, const void* eps_n, const void* eps, const void* z_n,
                    int64_t ld, double step_h, double rtol, double atol, int max_substeps, void* sigma, void* z,
@@ -229,13 +234,14 @@ typedef struct ms_load {
                                  phase; 1: the force-potential form integrated over
                                  each load step by ode23 (gsm_update_ode23) from the
                                  voxel's strain at t_n to the current iterate; 2: the
-                                 same by ode12 (gsm_update_ode, GSM_ODE12); 1 or 2 are
-                                 needed for GSM_PSI_ELASTIC_VP_KIN phases; FP64 only  */
-  double ode_rtol, ode_atol;  /* integrator 1: stress-error tolerances (rtol > 0,
+                                 same by ode12 (gsm_update_ode, GSM_ODE12); 3: by
+                                 ode23s (GSM_ODE23S); 1, 2 or 3 are needed for
+                                 GSM_PSI_ELASTIC_VP_KIN phases; FP64 only             */
+  double ode_rtol, ode_atol;  /* integrator >= 1: stress-error tolerances (rtol > 0,
                                  atol >= 0); keep them well below `tol`: an update
                                  that is not converged to better than the equilibrium
                                  tolerance stalls the fixed point                      */
-  int ode_max_substeps;       /* integrator 1: attempts per voxel and step (>= 1)     */
+  int ode_max_substeps;       /* integrator >= 1: attempts per voxel and step (>= 1)  */
 } ms_load;
 
 typedef struct ms_state {
@@ -282,7 +288,7 @@ size_t ms_workspace_bytes(const ms_problem* prob);
  * A problem with GSM_PSI_ELASTIC_VP_KIN phases keeps its seventh internal
  * variable (the accumulated plastic strain) inside the context: it starts
  * fresh only (resume = 1 gives GSM_ENOTSUP).
- * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTSUP (integrator 1 or 2 with a precision
+ * Errors: GSM_EINVAL, GSM_ECUDA, GSM_ENOTSUP (integrator 1, 2 or 3 with a precision
  * other than MS_PREC_FP64, a VP_KIN phase with integrator 0), GSM_ENOTCONV
  * (some step hit max_iter; the result is still filled in).
  */

@@ -23,8 +23,8 @@ GSM_PSI_ELASTIC, GSM_PSI_ELASTIC_VP_DEV, GSM_PSI_ELASTIC_VP_KIN = 0, 1, 2
 GSM_PHI_NONE, GSM_PHI_NORTON, GSM_PHI_MS_FORCE = 0, 1, 2
 GSM_FP64, GSM_FP32_FP64FIX, GSM_FP32 = 0, 1, 2
 MS_PREC_FP64, MS_PREC_FP32_BULK = 0, 1
-GSM_ODE23, GSM_ODE12 = 0, 1
-ODE_METHODS = {"ode23": GSM_ODE23, "ode12": GSM_ODE12}
+GSM_ODE23, GSM_ODE12, GSM_ODE23S = 0, 1, 2
+ODE_METHODS = {"ode23": GSM_ODE23, "ode12": GSM_ODE12, "ode23s": GSM_ODE23S}
 
 ST_CONVERGED, ST_NONFINITE, ST_CAP, ST_NOT_SPD = 1 << 16, 1 << 17, 1 << 18, 1 << 19
 
@@ -199,7 +199,8 @@ def gsm_destroy(mat):
 
 def gsm_update_ode23(mat, eps_n, eps, z_n, h, sigma, z, tangent=None, status=None, rtol=1e-3, atol=1e-6,
                      max_substeps=100000, stream=None, n_vox=None, method="ode23"):
-    """Material update by ode23 (or, method="ode12", the Euler/Heun pair) over the
+    """Material update by ode23 (or, method="ode12", the Euler/Heun pair; method="ode23s",
+    the Shampine-Reichelt Rosenbrock triple) over the
     load step (FP64 tensors ``[6, ld]``; internal variables ``[7, ld]`` (z,
     alpha) for the Michel-Suquet law; tangent ``[36, ld]`` = full
     dsigma/deps_{n+1} row-major; status ``[ld]``)."""
@@ -319,7 +320,7 @@ def ms_run(ctx, E, hs, tol=1e-8, max_iter=10000, forced_iters=None, eps=None, z=
     reference, rc).  stress_mask: 6 booleans (or bits) of the macroscopic components whose stress
     (Sigma, default 0) is prescribed; ref_update: per-step reference medium from tangents;
     ode: None (implicit Euler) or (rtol, atol[, max_substeps]) for the update over each step by
-    ode_method ("ode23" or "ode12")."""
+    ode_method ("ode23", "ode12" or "ode23s")."""
     lib = load()
     ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, switch_tol, stress_mask, Sigma, ref_update,
                                ode, ode_method)

@@ -96,6 +96,9 @@ struct NortonDev {
     auto s2 = (sq(a0) + sq(a1) - a0 * a1) + S(3) * (sq(a2) + sq(a3) + sq(a4));
     return p.c_Psi * pow(s2, p.b_Psi);
   }
+  // Psi = c_Psi x^beta with x = s_A (for the hand third derivative of ode23s)
+  static constexpr bool kYield = false;
+  AD_HD static double Psi_beta(const LawParams<double>& p) { return 2.0 * p.b_Psi; }
 
   // psi depends on (eps, y) only through tr(eps) and dev(eps) - P y (P y is
   // traceless, C isotropic).  With the trial strain e_s = dev(eps) - P y_n:
@@ -175,6 +178,9 @@ struct MichelSuquet {
     auto s2 = (sq(a0) + sq(a1) - a0 * a1) + S(3) * (sq(a2) + sq(a3) + sq(a4));
     return p.c_Psi * pospow(sqrt0(s2) + a5, p.b_Psi);
   }
+  // Psi = c_Psi (x^+)^beta with x = s_A + A_alpha (for the hand third derivative of ode23s)
+  static constexpr bool kYield = true;
+  AD_HD static double Psi_beta(const LawParams<double>& p) { return p.b_Psi; }
 };
 
 }  // namespace gsm

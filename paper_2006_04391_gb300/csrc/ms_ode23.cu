@@ -1,0 +1,6 @@
+// Basic-scheme material kernel for laws integrated by ode23; see ms_ode_impl.cuh.
+#include "ms_ode_impl.cuh"
+
+namespace gsm {
+GSM_MS_ODE_INSTANTIATE_MATERIAL(0)
+}  // namespace gsm

@@ -1,13 +1,18 @@
-// Basic-scheme kernels for laws integrated over the load step by an explicit
-// Runge-Kutta pair (AutoMat, arXiv 2006.04391, Sec. 4.3: ode23 or ode12;
-// tangent ODE of Corollary 1), with their host launchers.  A translation unit
-// of its own: the integrator instantiations dominate the compile time.
+// Basic-scheme kernels for laws integrated over the load step by an ODE
+// integrator (AutoMat, arXiv 2006.04391, Sec. 4.3: ode23, ode12 or ode23s;
+// tangent ODE of Corollary 1) and their host launchers, instantiated per
+// integrator in ms_ode{23,12,23s}.cu (material kernels) and
+// ms_ode{23,12,23s}_ref.cu (reference kernels, with the tangent): the
+// integrator instantiations dominate the compile time, one unit each.
+#pragma once
+
 #include "ms_kernels.cuh"
 #include "ms_ode.h"
 #include "ode23.cuh"
 
 namespace gsm {
 namespace {
+
 
 // Material evaluation of voxel i with the ode23 laws (Sec. 4.3): Norton and
 // Michel-Suquet voxels integrate the force-potential form from the strain of
@@ -36,7 +41,7 @@ __device__ __forceinline__ void material_voxel_ode(int64_t i, bool in, const Job
   for (int c = 0; c < 7; ++c) zo[c] = 0.0;
   const bool nor = in && kind == GSM_PSI_ELASTIC_VP_DEV;
   if (any_lane(nor)) {
-    ErkVoxel<NortonDev, false, PAIR> w;
+    OdeVoxel<NortonDev, false, PAIR> w;
     double zi[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) zi[c] = nor ? __ldg(zn + c * nvox + i) : 0.0;
@@ -55,7 +60,7 @@ __device__ __forceinline__ void material_voxel_ode(int64_t i, bool in, const Job
   }
   const bool kin = in && kind == GSM_PSI_ELASTIC_VP_KIN;
   if (any_lane(kin)) {
-    ErkVoxel<MichelSuquet, false, PAIR> w;
+    OdeVoxel<MichelSuquet, false, PAIR> w;
     double zi[7];
 #pragma unroll
     for (int c = 0; c < 6; ++c) zi[c] = kin ? __ldg(zn + c * nvox + i) : 0.0;
@@ -195,37 +200,36 @@ __global__ void __launch_bounds__(kMatBlock) ms_reference_ode_kernel(int64_t nvo
 
 }  // namespace
 
-int ms_ode_blocks_per_sm(int pair) {
+template <int PAIR> int ms_ode_blocks_per_sm_p() {
   int b = 0;
-  const cudaError_t e = pair == ERK_BS23
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_ode_kernel<ERK_BS23>,
-                                                                            kMatBlock, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_ode_kernel<ERK_HEUN12>,
-                                                                            kMatBlock, 0);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_ode_kernel<PAIR>, kMatBlock, 0);
   return e == cudaSuccess && b > 0 ? b : 1;
 }
 
-void ms_launch_material_ode(int pair, int grid, cudaStream_t s, const void* views, int n_jobs, int64_t total_chunks) {
-  const JobView* v = static_cast<const JobView*>(views);
-  if (pair == ERK_BS23) ms_material_ode_kernel<ERK_BS23><<<grid, kMatBlock, 0, s>>>(v, n_jobs, total_chunks);
-  else ms_material_ode_kernel<ERK_HEUN12><<<grid, kMatBlock, 0, s>>>(v, n_jobs, total_chunks);
+template <int PAIR>
+void ms_launch_material_ode_p(int grid, cudaStream_t s, const void* views, int n_jobs, int64_t total_chunks) {
+  ms_material_ode_kernel<PAIR><<<grid, kMatBlock, 0, s>>>(static_cast<const JobView*>(views), n_jobs, total_chunks);
 }
 
-void ms_launch_reference_ode(int pair, int grid, cudaStream_t s, int64_t nvox, const uint8_t* phase, const void* tab,
-                             double h, double rtol, double atol, int max_steps, const double* eps_raw,
-                             const double* eps_prev, const double* zn, const double* alpha_n, double inv_n3,
-                             const double (&dE)[6], double* part) {
-  const PhaseTable* t = static_cast<const PhaseTable*>(tab);
-  const Step hs = make_step(h);
-  const Ode23Ctl ctl{rtol, atol, max_steps};
-  if (pair == ERK_BS23)
-    ms_reference_ode_kernel<ERK_BS23><<<grid, kMatBlock, 0, s>>>(nvox, phase, t, hs, ctl, eps_raw, eps_prev, zn,
-                                                                 alpha_n, inv_n3, dE[0], dE[1], dE[2], dE[3], dE[4],
-                                                                 dE[5], part);
-  else
-    ms_reference_ode_kernel<ERK_HEUN12><<<grid, kMatBlock, 0, s>>>(nvox, phase, t, hs, ctl, eps_raw, eps_prev, zn,
-                                                                   alpha_n, inv_n3, dE[0], dE[1], dE[2], dE[3],
-                                                                   dE[4], dE[5], part);
+template <int PAIR>
+void ms_launch_reference_ode_p(int grid, cudaStream_t s, int64_t nvox, const uint8_t* phase, const void* tab, double h,
+                               double rtol, double atol, int max_steps, const double* eps_raw, const double* eps_prev,
+                               const double* zn, const double* alpha_n, double inv_n3, const double (&dE)[6],
+                               double* part) {
+  ms_reference_ode_kernel<PAIR><<<grid, kMatBlock, 0, s>>>(
+      nvox, phase, static_cast<const PhaseTable*>(tab), make_step(h), Ode23Ctl{rtol, atol, max_steps}, eps_raw,
+      eps_prev, zn, alpha_n, inv_n3, dE[0], dE[1], dE[2], dE[3], dE[4], dE[5], part);
 }
+
+// explicit instantiations: the material kernel and the (tangent-heavy)
+// reference kernel of an integrator go to separate translation units
+#define GSM_MS_ODE_INSTANTIATE_MATERIAL(PAIR)                                                                    \
+  template int ms_ode_blocks_per_sm_p<PAIR>();                                                                \
+  template void ms_launch_material_ode_p<PAIR>(int, cudaStream_t, const void*, int, int64_t);
+#define GSM_MS_ODE_INSTANTIATE_REFERENCE(PAIR)                                                                   \
+  template void ms_launch_reference_ode_p<PAIR>(int, cudaStream_t, int64_t, const uint8_t*, const void*, double, \
+                                                double, double, int, const double*, const double*,          \
+                                                const double*, const double*, double, const double (&)[6],  \
+                                                double*);
 
 }  // namespace gsm

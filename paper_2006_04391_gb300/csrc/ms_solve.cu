@@ -102,7 +102,7 @@ struct Engine {
   Reduced* red_host = nullptr;
   int cap = 0;
   bool inited = false;
-  int per_sm_mat[5] = {1, 1, 1, 1, 1};  // FP64, FP32-fix, FP32 laws; ode23, ode12 laws
+  int per_sm_mat[6] = {1, 1, 1, 1, 1, 1};  // FP64, FP32-fix, FP32 laws; ode23, ode12, ode23s laws
   int per_sm_gam[2] = {1, 1};
 
   int init(cudaStream_t s, int capacity) {
@@ -126,8 +126,7 @@ struct Engine {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_batch_kernel<float, MODE_FP32>, kMatBlock, 0) ==
         cudaSuccess)
       per_sm_mat[2] = std::max(b, 1);
-    per_sm_mat[3] = ms_ode_blocks_per_sm(0);
-    per_sm_mat[4] = ms_ode_blocks_per_sm(1);
+    for (int q = 0; q < 3; ++q) per_sm_mat[3 + q] = ms_ode_blocks_per_sm(q);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<double>, kGamBlock, 0) == cudaSuccess)
       per_sm_gam[0] = std::max(b, 1);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_gamma_batch_kernel<float>, kGamBlock, 0) == cudaSuccess)
@@ -201,7 +200,7 @@ struct Job {
   int stress_mask = 0;               // mixed boundary conditions: prescribed-stress components
   std::vector<double> S_target;      // [n_steps][6]
   bool ref_update = false;           // per-step reference medium from tangents
-  int integrator = 0;                // 0 implicit Euler, 1 ode23, 2 ode12 (Sec. 4.3)
+  int integrator = 0;                // 0 implicit Euler, 1 ode23, 2 ode12, 3 ode23s (Sec. 4.3)
   double ode_rtol = 1e-3, ode_atol = 1e-6;
   int ode_max = 100000;
   bool has_kin = false;              // a Michel-Suquet phase: alpha, and an explicit pair only
@@ -336,7 +335,7 @@ int job_load(Job& j, const ms_load* load) {
       if (load->forced_iters[k] < 1) return GSM_EINVAL;
   if (load->stress_mask < 0 || load->stress_mask > 63 || (load->ref_update != 0 && load->ref_update != 1))
     return GSM_EINVAL;
-  if (load->integrator < 0 || load->integrator > 2) return GSM_EINVAL;
+  if (load->integrator < 0 || load->integrator > 3) return GSM_EINVAL;
   if (load->integrator >= 1 && (!(load->ode_rtol > 0.0) || !(load->ode_atol >= 0.0) || load->ode_max_substeps < 1))
     return GSM_EINVAL;
   // the Michel-Suquet law integrates by an explicit pair only; those run in FP64
@@ -500,7 +499,7 @@ int step_start(Engine& g, Job& j) {
     dE[q] = E[q] - j.E_prev[q];
     j.E_cur[q] = E[q];
   }
-  // ode23 / ode12 laws integrate over the step from each voxel's strain at t_n
+  // ODE-integrated laws integrate over the step from each voxel's strain at t_n
   if (j.integrator >= 1) convert<double, double>(g.stream, j.f64.eps_raw, j.eps_prev, 6 * j.nvox, 1.0 / (double)j.nvox);
   if (j.ref_update) {
     const int rc = reference_update(g, j, dE);
@@ -630,9 +629,9 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
       j->need_start = false;
     }
   // launch groups: FP64 fields + FP64 laws, FP64 fields + FP32-fix laws,
-  // FP64 fields + ode23 laws, FP64 fields + ode12 laws, FP32 fields (FP64
-  // groups first: one Green launch)
-  constexpr int kGroups = 5, kF32 = 4;
+  // FP64 fields + ode23 / ode12 / ode23s laws, FP32 fields (FP64 groups
+  // first: one Green launch)
+  constexpr int kGroups = 6, kF32 = 5;
   auto key = [](const Job* j) {
     if (j->fp32_phase) return kF32;
     if (j->integrator >= 1) return 1 + j->integrator;
@@ -640,13 +639,13 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
   };
   std::vector<Job*> order;
   order.reserve(n);
-  int gstart[kGroups + 1] = {0, 0, 0, 0, 0, 0};
+  int gstart[kGroups + 1] = {0, 0, 0, 0, 0, 0, 0};
   for (int k = 0; k < kGroups; ++k) {
     for (Job* j : jobs)
       if (key(j) == k) order.push_back(j);
     gstart[k + 1] = (int)order.size();
   }
-  int64_t vtot[kGroups] = {0, 0, 0, 0, 0}, mtot[2] = {0, 0};
+  int64_t vtot[kGroups] = {0, 0, 0, 0, 0, 0}, mtot[2] = {0, 0};
   for (int i = 0; i < n; ++i) {
     Job& j = *order[i];
     const int k = key(&j);
@@ -701,7 +700,7 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
                                                                               gstart[2] - gstart[1], vtot[1]);
     count_launch();
   }
-  for (int k = 2; k <= 3; ++k)
+  for (int k = 2; k <= 4; ++k)
     if (gstart[k + 1] > gstart[k]) {
       const int grid = (int)std::min<int64_t>(vtot[k], sms * g.per_sm_mat[k + 1]);
       ms_launch_material_ode(k - 2, grid, s, g.views_dev + gstart[k], gstart[k + 1] - gstart[k], vtot[k]);

@@ -18,6 +18,8 @@
 // All derivatives of psi and Psi come from the AD sweeps; FP64 throughout.
 #pragma once
 
+#include <type_traits>
+
 #include "solver.cuh"
 
 namespace gsm {
@@ -27,8 +29,8 @@ struct Ode23Ctl {
   int max_steps;  // accepted + rejected substeps
 };
 
-// Embedded explicit Runge-Kutta pairs.
-enum : int { ERK_BS23 = 0, ERK_HEUN12 = 1 };
+// Embedded explicit Runge-Kutta pairs, and the Rosenbrock triple of ode23s.
+enum : int { ERK_BS23 = 0, ERK_HEUN12 = 1, ROS_23S = 2 };
 
 // Status word of the ode23 update: bits 0-15 accepted substeps, bits 20-30
 // rejected substeps (both saturating), flags in bits 16-19 as elsewhere.
@@ -505,13 +507,493 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
 
 template <class Law, bool TAN> using Ode23Voxel = ErkVoxel<Law, TAN, ERK_BS23>;
 
+// ------------------------------------------------------------------ ode23s
+//
+// Third derivative of the force potential contracted with two directions,
+// out = Psi_AAA[u, v]: the hand partial the Rosenbrock tangent needs (the
+// paper's semi-automatic strategy: the AD here stops at second order).  Both
+// laws have Psi = c (x^+)^beta with x = s (Norton) or s + A_alpha
+// (Michel-Suquet), s^2 = A_z^T M A_z, M = [[1, -1/2], [-1/2, 1]] + 3 I_3 (von
+// Mises).  With m = M A_z / s, Q = M - m m^T and r(x) = dPsi/dx:
+//   H_zz = r' m m^T + r Q/s,  H_za = r' m,  H_aa = r',
+// and along u (dx = m.u_z + u_a, ds = m.u_z, dm = Q u_z / s):
+//   dH_zz = r'' dx m m^T + (r' - r/s)(dm m^T + m dm^T) + (r' dx - r ds/s) Q/s,
+//   dH_za = r'' dx m + r' dm,  dH_aa = r'' dx;  zero where x <= 0 or s = 0.
+template <class Law>
+AD_HD void force_aaa(const LawParams<double>& p, const double (&A)[Law::NY], const double (&u)[Law::NY],
+                     const double (&v)[Law::NY], double (&out)[Law::NY]) {
+  constexpr int NY = Law::NY;
+#pragma unroll
+  for (int a = 0; a < NY; ++a) out[a] = 0.0;
+  double MA[5];
+  MA[0] = A[0] - 0.5 * A[1];
+  MA[1] = A[1] - 0.5 * A[0];
+  MA[2] = 3.0 * A[2];
+  MA[3] = 3.0 * A[3];
+  MA[4] = 3.0 * A[4];
+  double s2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) s2 = fma(A[a], MA[a], s2);
+  const double s = sqrt(s2);
+  double x = s;
+  if constexpr (Law::kYield) x += A[5];
+  if (!(x > 0.0) || !(s > 0.0)) return;
+  const double beta = Law::Psi_beta(p);
+  const double px = fpow::pow_pos(x, beta - 3.0);
+  const double r2 = p.c_Psi * beta * (beta - 1.0) * (beta - 2.0) * px;
+  const double r1 = p.c_Psi * beta * (beta - 1.0) * px * x;
+  const double r0 = p.c_Psi * beta * px * x * x;
+  const double inv_s = 1.0 / s;
+  double m[5], Mu[5], Mv[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) m[a] = MA[a] * inv_s;
+  Mu[0] = u[0] - 0.5 * u[1];
+  Mu[1] = u[1] - 0.5 * u[0];
+  Mv[0] = v[0] - 0.5 * v[1];
+  Mv[1] = v[1] - 0.5 * v[0];
+#pragma unroll
+  for (int a = 2; a < 5; ++a) {
+    Mu[a] = 3.0 * u[a];
+    Mv[a] = 3.0 * v[a];
+  }
+  double ds = 0.0, mv = 0.0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    ds = fma(m[a], u[a], ds);
+    mv = fma(m[a], v[a], mv);
+  }
+  double dx = ds;
+  double va = 0.0;
+  if constexpr (Law::kYield) {
+    dx += u[5];
+    va = v[5];
+  }
+  // dm = Q u / s = (M u - m ds)/s;  dm.v;  Q v = M v - m mv
+  double dm[5], dmv = 0.0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    dm[a] = (Mu[a] - m[a] * ds) * inv_s;
+    dmv = fma(dm[a], v[a], dmv);
+  }
+  const double c1 = r1 - r0 * inv_s, c2 = (r1 * dx - r0 * ds * inv_s) * inv_s;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    const double Qv = Mv[a] - m[a] * mv;
+    out[a] = r2 * dx * m[a] * mv + c1 * (dm[a] * mv + m[a] * dmv) + c2 * Qv + (r2 * dx * m[a] + r1 * dm[a]) * va;
+  }
+  if constexpr (Law::kYield) out[5] = r2 * dx * mv + r1 * dmv + r2 * dx * va;
+}
+
+// W x = b for the NY x NY matrix of a Rosenbrock stage: Gaussian elimination
+// with partial pivoting, factor once (multipliers below, U on and above the
+// diagonal, row swaps in piv), solve many by replaying swap and elimination
+// column by column; everything in registers (the row swaps are selects over
+// compile-time indices).
+template <int NY> struct StageLU {
+  double w[NY][NY];
+  int piv[NY];
+  bool ok;
+
+  AD_HD void factor() {
+    ok = true;
+#pragma unroll
+    for (int c = 0; c < NY; ++c) {
+      int pr = c;
+      double best = fabs(w[c][c]);
+#pragma unroll
+      for (int r = c + 1; r < NY; ++r)
+        if (fabs(w[r][c]) > best) {
+          best = fabs(w[r][c]);
+          pr = r;
+        }
+      piv[c] = pr;
+#pragma unroll
+      for (int r = c + 1; r < NY; ++r)
+        if (r == pr)
+#pragma unroll
+          for (int j = c; j < NY; ++j) {  // (the multipliers left of c stay with their elimination step)
+            const double t = w[c][j];
+            w[c][j] = w[r][j];
+            w[r][j] = t;
+          }
+      if (!(best > 0.0)) {
+        ok = false;
+        w[c][c] = 1.0;  // keep the arithmetic finite; the substep is rejected
+      }
+      const double inv = 1.0 / w[c][c];
+#pragma unroll
+      for (int r = c + 1; r < NY; ++r) {
+        const double f = w[r][c] * inv;
+        w[r][c] = f;
+#pragma unroll
+        for (int j = c + 1; j < NY; ++j) w[r][j] = fma(-f, w[c][j], w[r][j]);
+      }
+    }
+  }
+
+  AD_HD void solve(const double (&b)[NY], double (&x)[NY]) const {
+    double y[NY];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) y[i] = b[i];
+#pragma unroll
+    for (int c = 0; c < NY; ++c) {
+#pragma unroll
+      for (int r = c + 1; r < NY; ++r)
+        if (r == piv[c]) {
+          const double t = y[c];
+          y[c] = y[r];
+          y[r] = t;
+        }
+#pragma unroll
+      for (int r = c + 1; r < NY; ++r) y[r] = fma(-w[r][c], y[c], y[r]);
+    }
+#pragma unroll
+    for (int i = NY - 1; i >= 0; --i) {
+      double t = y[i];
+#pragma unroll
+      for (int j = i + 1; j < NY; ++j) t = fma(-w[i][j], x[j], t);
+      x[i] = t / w[i][i];
+    }
+  }
+};
+
+// ode23s as a resumable voxel state (same interface as ErkVoxel): the modified
+// Rosenbrock triple of Shampine and Reichelt (SIAM J. Sci. Comput. 18 (1997)
+// 1-22), d = 1/(2 + sqrt 2), e32 = 6 + sqrt 2, J = df/dy = Psi_AA dA/dy and
+// T = df/dt = Psi_AA dA/dt at the start (t, y) of a substep, W = I - dt d J:
+//   k1 = W^-1 (F0 + dt d T),  F1 = f(t + dt/2, y + dt/2 k1),
+//   k2 = W^-1 (F1 - k1) + k1,  y_new = y + dt k2,  F2 = f(t + dt, y_new),
+//   k3 = W^-1 (F2 - e32 (k2 - F1) - 2 (k1 - F0) + dt d T),
+//   error estimate dt/6 (k1 - 2 k2 + k3), compared through the stresses of
+//   y_new and y_new minus the estimate; step control as ode23's (exponent
+//   1/3); F2 is F0 of the next substep; J, T re-evaluated after an acceptance.
+// dA/dy = -psi_yy and dA/dt = -psi_ye (eps_{n+1} - eps_n)/h are constant for
+// both laws (psi is quadratic in (eps, y)).  With TAN, each column k of Y =
+// dy/deps_{n+1} follows the differentiated stages (Corollary 1, Rosenbrock
+// form), with dA_k = -(theta psi_ye e_k + psi_yy Y e_k):
+//   J~_k w = Psi_AAA[dA_k, dA/dy w],  T~_k = Psi_AAA[dA_k, dA/dt] - Psi_AA psi_ye e_k / h,
+//   k1~ = W^-1 (F0~ + dt d (T~ + J~ k1)),
+//   k2~ = k1~ + W^-1 (F1~ - k1~ + dt d J~ (k2 - k1)),
+//   k3~ = W^-1 (F2~ - e32 (k2~ - F1~) - 2 (k1~ - F0~) + dt d (T~ + J~ k3)).
+template <class Law, bool TAN> struct RosVoxel {
+  static constexpr int NY = Law::NY, NZ = stored_nz<Law>();
+  using M56 = double[TAN ? NY : 1][TAN ? 6 : 1];
+  using M66 = double[TAN ? 6 : 1][TAN ? 6 : 1];
+  double epsn[6], de[6];
+  OdeState<NY, TAN> s;
+  double F0[NY];
+  M56 G0;
+  double J[NY][NY], T[NY];
+  double dAdy[NY][NY], dAdt[NY];
+  // with TAN: Psi_AA and A at the substep start, psi_ye
+  double H0[TAN ? NY : 1][TAN ? NY : 1], A0[TAN ? NY : 1], Hye[TAN ? NY : 1][TAN ? 6 : 1];
+  double sig_old[6];
+  M66 C_old;
+  double t, dt;
+  int n_acc, n_rej;
+  unsigned flags;
+  bool last_rejected, done;
+
+  // Psi_AA at (theta, y): J, T (and, with TAN, H0, A0).
+  AD_HD void refresh(const LawParams<double>& p, double theta, double inv_h) {
+    double et[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
+    double g[NY], hye[NY][6], hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
+    ode_blocks<Law, false>(p, et, s.y, g, hye, hyy, sig_, Cee_, Cey_);
+    double A[NY], f[NY], H[NY][NY];
+#pragma unroll
+    for (int a = 0; a < NY; ++a) A[a] = -g[a];
+    force_a_aa<Law>(p, A, f, H);
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+#pragma unroll
+      for (int b = 0; b < NY; ++b) dAdy[a][b] = -hyy[a][b];
+      double tt = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) tt = fma(hye[a][k], de[k], tt);
+      dAdt[a] = -tt * inv_h;
+    }
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      double tt = 0.0;
+#pragma unroll
+      for (int b = 0; b < NY; ++b) tt = fma(H[a][b], dAdt[b], tt);
+      T[a] = tt;
+#pragma unroll
+      for (int b = 0; b < NY; ++b) {
+        double jj = 0.0;
+#pragma unroll
+        for (int c = 0; c < NY; ++c) jj = fma(H[a][c], dAdy[c][b], jj);
+        J[a][b] = jj;
+      }
+    }
+    if constexpr (TAN) {
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        A0[a] = A[a];
+#pragma unroll
+        for (int b = 0; b < NY; ++b) H0[a][b] = H[a][b];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Hye[a][k] = hye[a][k];
+      }
+    }
+  }
+
+  AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[NZ],
+                  double h) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      epsn[i] = e0[i];
+      de[i] = e1[i] - e0[i];
+    }
+    s.y[0] = zn[0];
+    s.y[1] = zn[1];
+    s.y[2] = zn[3];
+    s.y[3] = zn[4];
+    s.y[4] = zn[5];
+#pragma unroll
+    for (int a = 5; a < NY; ++a) s.y[a] = zn[a + 1];
+    if constexpr (TAN) {
+#pragma unroll
+      for (int a = 0; a < NY; ++a)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, F0, G0);
+    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+    refresh(p, 0.0, 1.0 / h);
+    t = 0.0;
+    dt = h;
+    n_acc = n_rej = 0;
+    flags = 0;
+    last_rejected = false;
+    done = false;
+  }
+
+  // J~_k w (column k of the tangent) into out.
+  AD_HD void jtil(const LawParams<double>& p, const double (&dAk)[NY], const double (&w)[NY],
+                  double (&out)[NY]) const {
+    double v[NY];
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      double tt = 0.0;
+#pragma unroll
+      for (int b = 0; b < NY; ++b) tt = fma(dAdy[a][b], w[b], tt);
+      v[a] = tt;
+    }
+    const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
+    force_aaa<Law>(p, A, dAk, v, out);
+  }
+
+  AD_HD void attempt(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
+    constexpr double d = 0.29289321881345247560;   // 1/(2 + sqrt 2)
+    constexpr double e32 = 7.4142135623730950488;  // 6 + sqrt 2
+    const double h = hs.h, inv_h = hs.inv_h;
+    if (n_acc + n_rej >= ctl.max_steps) {
+      flags |= ST_CAP;
+      done = true;
+      return;
+    }
+    const bool clip = t + dt >= h;
+    if (clip) dt = h - t;
+    const double tn1 = clip ? h : t + dt;
+    const double th1 = clip ? 1.0 : tn1 * inv_h;
+    const double th0 = t * inv_h;
+    const double hd = dt * d;
+    StageLU<NY> W;
+#pragma unroll
+    for (int a = 0; a < NY; ++a)
+#pragma unroll
+      for (int b = 0; b < NY; ++b) W.w[a][b] = (a == b ? 1.0 : 0.0) - hd * J[a][b];
+    W.factor();
+    double rhs[NY], k1[NY], k2[NY], k3[NY], F1[NY], F2[NY];
+    M56 G1, G2, K1, K2;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) rhs[a] = fma(hd, T[a], F0[a]);
+    W.solve(rhs, k1);
+    OdeState<NY, TAN> st;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) st.y[a] = fma(0.5 * dt, k1[a], s.y[a]);
+    // tangent: the total dA/deps_k at the substep start, T~_k and k1~
+    double dA[TAN ? 6 : 1][TAN ? NY : 1], Tt[TAN ? 6 : 1][TAN ? NY : 1];
+    if constexpr (TAN) {
+      // (columns one at a time: the tangent state lives in local memory anyway,
+      // and unrolling the six columns multiplies the code and the compile time)
+#pragma unroll 1
+      for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int a = 0; a < NY; ++a) {
+          double v = th0 * Hye[a][k];
+#pragma unroll
+          for (int b = 0; b < NY; ++b) v = fma(-dAdy[a][b], s.Y[b][k], v);  // psi_yy = -dA/dy
+          dA[k][a] = -v;
+        }
+        double dAt[NY];
+        const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
+        force_aaa<Law>(p, A, dA[k], dAdt, dAt);
+        double jk[NY], r[NY], col[NY];
+        jtil(p, dA[k], k1, jk);
+#pragma unroll
+        for (int a = 0; a < NY; ++a) {
+          double hh = 0.0;
+#pragma unroll
+          for (int b = 0; b < NY; ++b) hh = fma(H0[a][b], Hye[b][k], hh);
+          Tt[k][a] = dAt[a] - hh * inv_h;
+          r[a] = G0[a][k] + hd * Tt[k][a] + hd * jk[a];
+        }
+        W.solve(r, col);
+#pragma unroll
+        for (int a = 0; a < NY; ++a) {
+          K1[a][k] = col[a];
+          st.Y[a][k] = fma(0.5 * dt, col[a], s.Y[a][k]);
+        }
+      }
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, F1, G1);
+    double w2[NY];
+#pragma unroll
+    for (int a = 0; a < NY; ++a) rhs[a] = F1[a] - k1[a];
+    W.solve(rhs, w2);
+    OdeState<NY, TAN> s3;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      k2[a] = w2[a] + k1[a];
+      s3.y[a] = fma(dt, k2[a], s.y[a]);
+    }
+    if constexpr (TAN) {
+      // (columns one at a time: the tangent state lives in local memory anyway,
+      // and unrolling the six columns multiplies the code and the compile time)
+#pragma unroll 1
+      for (int k = 0; k < 6; ++k) {
+        double dk[NY], jk[NY], r[NY], col[NY];
+#pragma unroll
+        for (int a = 0; a < NY; ++a) dk[a] = k2[a] - k1[a];
+        jtil(p, dA[k], dk, jk);
+#pragma unroll
+        for (int a = 0; a < NY; ++a) r[a] = G1[a][k] - K1[a][k] + hd * jk[a];
+        W.solve(r, col);
+#pragma unroll
+        for (int a = 0; a < NY; ++a) {
+          K2[a][k] = K1[a][k] + col[a];
+          s3.Y[a][k] = fma(dt, K2[a][k], s.Y[a][k]);
+        }
+      }
+    }
+    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, F2, G2);
+#pragma unroll
+    for (int a = 0; a < NY; ++a) rhs[a] = F2[a] - e32 * (k2[a] - F1[a]) - 2.0 * (k1[a] - F0[a]) + hd * T[a];
+    W.solve(rhs, k3);
+    OdeState<NY, TAN> s2;
+    const double dt6 = dt * (1.0 / 6.0);
+#pragma unroll
+    for (int a = 0; a < NY; ++a) s2.y[a] = s3.y[a] - dt6 * (k1[a] - 2.0 * k2[a] + k3[a]);
+    if constexpr (TAN) {
+      // (columns one at a time: the tangent state lives in local memory anyway,
+      // and unrolling the six columns multiplies the code and the compile time)
+#pragma unroll 1
+      for (int k = 0; k < 6; ++k) {
+        double jk[NY], r[NY], col[NY];
+        jtil(p, dA[k], k3, jk);
+#pragma unroll
+        for (int a = 0; a < NY; ++a)
+          r[a] = G2[a][k] - e32 * (K2[a][k] - G1[a][k]) - 2.0 * (K1[a][k] - G0[a][k]) + hd * Tt[k][a] + hd * jk[a];
+        W.solve(r, col);
+#pragma unroll
+        for (int a = 0; a < NY; ++a) s2.Y[a][k] = s3.Y[a][k] - dt6 * (K1[a][k] - 2.0 * K2[a][k] + col[a]);
+      }
+    }
+    double s_hi[6], s_lo[6];
+    M66 C_hi, C_lo;
+    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
+    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      sum += scaled_sq(s_hi[i] - s_lo[i], fma(ctl.rtol, fmax_(fabs(sig_old[i]), fabs(s_hi[i])), ctl.atol));
+    int m = 6;
+    if constexpr (TAN) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          sum += scaled_sq(C_hi[i][c] - C_lo[i][c], fma(ctl.rtol, fmax_(fabs(C_old[i][c]), fabs(C_hi[i][c])), ctl.atol));
+      m = 42;
+    }
+    // a singular stage matrix or an overflow rejects the trial step
+    const double err = W.ok && finite64(sum) ? sqrt(sum / m) : 1e300;
+    const double facmax = last_rejected ? 1.0 : 5.0;
+    const double f = err == 0.0 ? 1e300 : 0.9 * fpow::pow_pos(err, -1.0 / 3.0);
+    const double grow = fmin(facmax, fmax(0.2, f));
+    if (err <= 1.0) {
+      t = tn1;
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        s.y[a] = s3.y[a];
+        F0[a] = F2[a];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            s.Y[a][c] = s3.Y[a][c];
+            G0[a][c] = G2[a][c];
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        sig_old[i] = s_hi[i];
+        if constexpr (TAN)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) C_old[i][c] = C_hi[i][c];
+      }
+      ++n_acc;
+      last_rejected = false;
+      if (clip) done = true;
+      else refresh(p, th1, inv_h);
+    } else {
+      ++n_rej;
+      last_rejected = true;
+    }
+    dt *= grow;
+  }
+
+  AD_HD unsigned finish(double h, double (&sig)[6], double (&z)[NZ], double* C36) const {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sig[i] = sig_old[i];
+    if constexpr (TAN) {
+      if (C36)
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) C36[6 * i + c] = C_old[i][c];
+    }
+    z[0] = s.y[0];
+    z[1] = s.y[1];
+    z[2] = -(s.y[0] + s.y[1]);
+    z[3] = s.y[2];
+    z[4] = s.y[3];
+    z[5] = s.y[4];
+#pragma unroll
+    for (int a = 5; a < NY; ++a) z[a + 1] = s.y[a];
+    unsigned st = flags;
+    if (t >= h && !(flags & ST_CAP)) st |= ST_CONVERGED;
+    if (!finite64(sig[0]) || !finite64(z[0])) st |= ST_NONFINITE;
+    st |= (unsigned)(n_acc < 0xffff ? n_acc : 0xffff);
+    st |= (unsigned)(n_rej < 0x7ff ? n_rej : 0x7ff) << ST_ODE_REJ_SHIFT;
+    return st;
+  }
+};
+
+// The voxel state of integrator PAIR.
+template <class Law, bool TAN, int PAIR>
+using OdeVoxel = std::conditional_t<PAIR == ROS_23S, RosVoxel<Law, TAN>, ErkVoxel<Law, TAN, PAIR == ROS_23S ? 0 : PAIR>>;
+
 // One voxel, start to end (single thread; the kernel schedules ErkVoxel
 // states per lane itself).
 template <class Law, bool TAN, int PAIR = ERK_BS23>
 AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], const double (&eps1)[6],
                            const double (&zn)[stored_nz<Law>()], const Step& hs, const Ode23Ctl& ctl,
                            double (&sig)[6], double (&z)[stored_nz<Law>()], double* C36) {
-  ErkVoxel<Law, TAN, PAIR> v;
+  OdeVoxel<Law, TAN, PAIR> v;
   v.init(p, epsn, eps1, zn, hs.h);
   while (!v.done) v.attempt(p, hs, ctl);
   return v.finish(hs.h, sig, z, C36);

@@ -64,6 +64,52 @@ int host_update_ode23(int kind, const double* prm, int64_t n, const double* eps_
   return 0;
 }
 
+// The same with the ode23s (Rosenbrock) triple.
+int host_update_ode23s(int kind, const double* prm, int64_t n, const double* eps_n, const double* eps,
+                       const double* zn, double h, double rtol, double atol, int max_steps, double* sig, double* z,
+                       double* tan, int32_t* status) {
+  const LawParams<double> p = make_params(prm, kind);
+  const Step hs = make_step(h);
+  const Ode23Ctl ctl{rtol, atol, max_steps};
+  if (kind == 1) run_ode23<NortonDev, ROS_23S>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  else run_ode23<MichelSuquet, ROS_23S>(p, n, eps_n, eps, zn, hs, ctl, sig, z, tan, status);
+  return 0;
+}
+
+// W x = b by the register LU of the Rosenbrock stages (n = 5 or 6, W row-major).
+int host_stage_solve(int n, const double* W, const double* b, double* x) {
+  auto run = [&](auto tag) {
+    constexpr int N = decltype(tag)::value;
+    StageLU<N> lu;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) lu.w[i][j] = W[i * N + j];
+    lu.factor();
+    double bb[N], xx[N];
+    for (int i = 0; i < N; ++i) bb[i] = b[i];
+    lu.solve(bb, xx);
+    for (int i = 0; i < N; ++i) x[i] = xx[i];
+    return lu.ok ? 0 : -1;
+  };
+  if (n == 5) return run(std::integral_constant<int, 5>{});
+  return run(std::integral_constant<int, 6>{});
+}
+
+// Psi_AAA[u, v] of the hand partial used by the ode23s tangent.
+void host_force_aaa(int kind, const double* prm, const double* A, const double* u, const double* v, double* out) {
+  const LawParams<double> p = make_params(prm, kind);
+  if (kind == 1) {
+    double a[5], uu[5], vv[5], o[5];
+    for (int i = 0; i < 5; ++i) { a[i] = A[i]; uu[i] = u[i]; vv[i] = v[i]; }
+    force_aaa<NortonDev>(p, a, uu, vv, o);
+    for (int i = 0; i < 5; ++i) out[i] = o[i];
+  } else {
+    double a[6], uu[6], vv[6], o[6];
+    for (int i = 0; i < 6; ++i) { a[i] = A[i]; uu[i] = u[i]; vv[i] = v[i]; }
+    force_aaa<MichelSuquet>(p, a, uu, vv, o);
+    for (int i = 0; i < 6; ++i) out[i] = o[i];
+  }
+}
+
 // The same with the ode12 (explicit Euler / Heun) pair.
 int host_update_ode12(int kind, const double* prm, int64_t n, const double* eps_n, const double* eps,
                       const double* zn, double h, double rtol, double atol, int max_steps, double* sig, double* z,

@@ -232,7 +232,7 @@ def test_taped_run_rejects_mixed_conditions(gsm):
 ODE = (1e-8, 1e-11)
 
 
-@pytest.mark.parametrize("method", ["ode23", "ode12"])
+@pytest.mark.parametrize("method", ["ode23", "ode12", "ode23s"])
 @pytest.mark.parametrize("kind,prm", [(O.KIND_NORTON, synth.MATRIX_16), (O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS)])
 def test_ode23_scheme_homogeneous_grid(gsm, kind, prm, method):
     """A homogeneous grid is one voxel integrated from eps_{k-1} to eps_k by
@@ -273,16 +273,18 @@ def test_ode23_norton_composite_iteration_matched(gsm):
     assert rel(z.cpu().numpy().T, ref["z"][:, :6]) < 1e-7
 
 
-def test_ode12_michel_suquet_composite_mixed_iteration_matched(gsm):
+@pytest.mark.parametrize("method", ["ode12", "ode23s"])
+def test_ode12_ode23s_michel_suquet_composite_mixed_iteration_matched(gsm, method):
     """The MMC with the ode12 pair (rtol 1e-6: the pair's substep count grows as
-    tol^(-1/2)), uniaxial stress, updated reference, the oracle's evaluation
+    tol^(-1/2)) or the ode23s triple (reference medium from its Rosenbrock
+    tangent), uniaxial stress, updated reference, the oracle's evaluation
     counts."""
     import torch
     ph = synth.sphere_phase(8, 0.2)
     laws = [(O.KIND_MICHEL_SUQUET, synth.ALUMINIUM_MS), (O.KIND_ELASTIC, synth.ALUMINA)]
     loads = synth.ramp(2, [0.003, 0, 0, 0, 0, 0])
     forced = [12, 12]
-    kw = dict(forced_iters=forced, stress_mask=UNIAXIAL, ref_update=True, ode=(1e-6, 1e-9), ode_method="ode12")
+    kw = dict(forced_iters=forced, stress_mask=UNIAXIAL, ref_update=True, ode=(1e-6, 1e-9), ode_method=method)
     ref = OMS.solve(ph, laws, loads, [0.5, 0.5], **kw)
     out = gsm.ms_solve(torch.from_numpy(ph).cuda(), gpu_laws(gsm, laws), loads, [0.5, 0.5], **kw)
     assert rel(out["Sigma"], ref["Sigma"]) < 1e-9

@@ -240,3 +240,59 @@ def test_ode_method_is_checked(gsm):
                             ctypes.c_double(1e-3), ctypes.c_double(1e-6), 100, t.clone().data_ptr(),
                             t.clone().data_ptr(), None, None, None)
     assert rc == gsm.GSM_EINVAL
+
+
+# ------------------------------------------------------- ode23s (Sec. 4.3)
+
+@pytest.mark.parametrize("tangent", [False, True])
+@pytest.mark.parametrize("kind", [O.KIND_NORTON, O.KIND_MICHEL_SUQUET])
+def test_ode23s_matches_oracle(gsm, tangent, kind):
+    """The Rosenbrock triple (gsm_update_ode, GSM_ODE23S; tangent with the hand
+    third derivative) against the oracle's ode23s."""
+    import torch
+    prm = synth.MATRIX_16 if kind == O.KIND_NORTON else synth.ALUMINIUM_MS
+    n = 4096 + 37 if not tangent else 1024 + 37
+    en, e, zn6 = synth.ode23_batch(n, seed=90 + int(tangent) + 2 * kind)
+    if kind == O.KIND_NORTON:
+        mat, zn, nz, kw = gsm.norton(*prm), zn6, 6, {}
+    else:
+        alpha_n = np.random.default_rng(12).uniform(0.0, 0.01, n)
+        mat, zn, nz = gsm.michel_suquet(*prm), np.concatenate([zn6, alpha_n[:, None]], axis=1), 7
+        kw = {"alpha_n": alpha_n}
+    ld = n + 3
+    E0, E1, Z0 = soa(en, ld), soa(e, ld), soa(zn, ld)
+    sig = torch.full_like(E1, float("nan"))
+    z = torch.full((nz, ld), float("nan"), dtype=torch.float64, device="cuda")
+    tan = torch.full((36, ld), float("nan"), dtype=torch.float64, device="cuda") if tangent else None
+    st = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    gsm.gsm_update_ode23(mat, E0, E1, Z0, 0.1, sig, z, tan, st, n_vox=n, method="ode23s")
+    torch.cuda.synchronize()
+    ref = O.update_ode23(prm, en, e, zn6, 0.1, tangent=tangent, info=True, kind=kind, method="ode23s", **kw)
+    s_, z_, st_ = sig.cpu().numpy()[:, :n].T, z.cpu().numpy()[:, :n].T, st.cpu().numpy()[:n]
+    assert np.all((st_ >> 16) & 1)
+    rel = np.abs(s_ - ref[0]).max(1) / np.abs(ref[0]).max(1)
+    relz = np.abs(z_[:, :6] - ref[1]).max(1) / np.maximum(np.abs(ref[1] - zn6).max(1), 1e-300)
+    tight = (rel < 1e-10) & (relz < 1e-10)
+    if tangent:
+        C2 = ref[-2].reshape(-1, 36)
+        tight &= np.abs(tan.cpu().numpy()[:, :n].T - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98, tight.mean()
+    assert np.all(np.abs(s_ - ref[0]) <= 10 * (1e-3 * np.abs(ref[0]).max(1, keepdims=True) + 1e-6))
+
+
+def test_ode23s_stiff_step(gsm):
+    """A long deviatoric ramp (amplitude 0.05 over h = 10): the Rosenbrock triple
+    takes far fewer substeps than ode23 on the GPU too, and the oracle's result."""
+    rng = np.random.default_rng(0)
+    n = 512
+    d = rng.normal(size=(n, 6))
+    d[:, :3] -= d[:, :3].mean(1, keepdims=True)
+    eps = 0.05 * d / np.abs(d).max(1, keepdims=True)
+    zero = np.zeros((n, 6))
+    r23 = run(gsm, gsm.norton(*synth.MATRIX_16), zero, eps, zero, 10.0)
+    r3s = run(gsm, gsm.norton(*synth.MATRIX_16), zero, eps, zero, 10.0, method="ode23s")
+    steps = lambda st: ((st & 0xFFFF) + ((st >> 20) & 0x7FF)).sum()
+    assert steps(r3s[2]) * 5 < steps(r23[2])
+    ref = O.update_ode23(synth.MATRIX_16, zero, eps, zero, 10.0, info=True, method="ode23s")
+    rel = np.abs(r3s[0] - ref[0]).max(1) / np.abs(ref[0]).max(1)
+    assert np.mean(rel < 1e-10) >= 0.98

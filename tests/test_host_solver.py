@@ -146,7 +146,7 @@ def _ode23_host(hlib, prm, en, e, zn, h, rtol, atol, tangent, kind=1, method="od
     st = np.empty(n, dtype=np.int32)
     C = np.empty((n, 36)) if tangent else None
     prm = np.asarray(list(prm) + [0.0] * (7 - len(prm)), dtype=float)
-    fn = hlib.host_update_ode23 if method == "ode23" else hlib.host_update_ode12
+    fn = {"ode23": hlib.host_update_ode23, "ode12": hlib.host_update_ode12, "ode23s": hlib.host_update_ode23s}[method]
     fn(kind, P(prm), ctypes.c_int64(n), P(en), P(e), P(np.ascontiguousarray(zn)),
        ctypes.c_double(h), ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(100000),
        P(sig), P(z), P(C) if tangent else None, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
@@ -244,4 +244,67 @@ def test_host_ode12_matches_oracle(hlib, tangent, kind):
         C2 = out[3 if kind == 2 else 2].reshape(-1, 36)
         tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
     assert tight.mean() >= 0.98 and same.mean() >= 0.98
+    assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))
+
+
+def test_host_stage_lu_solves_with_pivoting(hlib):
+    """The register LU of the Rosenbrock stages against numpy's solve, on
+    matrices that need row exchanges (small or zero leading pivots) and on
+    I - c J with J like the law Jacobians; a singular matrix is reported."""
+    rng = np.random.default_rng(17)
+    for n in (5, 6):
+        for trial in range(40):
+            W = rng.normal(size=(n, n))
+            if trial % 3 == 0:
+                W[0, 0] = 0.0                     # forces a swap at the first column
+            if trial % 3 == 1:
+                W[:, :2] = W[:, :2] * 1e-3        # small pivots in the first columns
+            b = rng.normal(size=n)
+            x = np.zeros(n)
+            assert hlib.host_stage_solve(n, P(np.ascontiguousarray(W)), P(b), P(x)) == 0
+            assert np.allclose(x, np.linalg.solve(W, b), rtol=1e-9, atol=1e-12 * np.abs(x).max())
+        S = np.zeros((n, n))
+        S[:, 0] = 1.0
+        x = np.zeros(n)
+        assert hlib.host_stage_solve(n, P(S), P(np.ones(n)), P(x)) == -1
+
+
+def test_host_force_aaa_matches_oracle(hlib):
+    """The hand third derivative of the GPU laws (the ode23s tangent's partial)
+    against the oracle's, Norton and Michel-Suquet, active states."""
+    rng = np.random.default_rng(5)
+    for kind, prm, k in ((1, synth.MATRIX_16, 5), (2, synth.ALUMINIUM_MS, 6)):
+        pv = np.asarray(list(prm) + [0.0] * (7 - len(prm)), dtype=float)
+        for _ in range(20):
+            A = rng.normal(size=k) * 0.2
+            if k == 6:
+                A[5] = -prm[2]
+            u, v = rng.normal(size=(2, k))
+            out = np.zeros(k)
+            hlib.host_force_aaa(kind, P(pv), P(A), P(u), P(v), P(out))
+            ref = O.psi_force_aaa(prm, A, u, v, kind=kind)
+            assert np.allclose(out, ref, rtol=1e-11, atol=1e-13 * max(np.abs(ref).max(), 1e-300))
+
+
+@pytest.mark.parametrize("tangent", [False, True])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_host_ode23s_matches_oracle(hlib, tangent, kind):
+    """The Rosenbrock update built from the AD second derivatives and the hand
+    third derivative against the oracle's hand-derived one."""
+    prm = synth.MATRIX_16 if kind == 1 else synth.ALUMINIUM_MS
+    n = 300 if not tangent else 120
+    en, e, zn6 = synth.ode23_batch(n, seed=81 + kind + int(tangent))
+    alpha_n = np.random.default_rng(8).uniform(0.0, 0.01, n) if kind == 2 else None
+    zn = zn6 if kind == 1 else np.concatenate([zn6, alpha_n[:, None]], axis=1)
+    sig, z, C, st = _ode23_host(hlib, prm, en, e, zn, 0.1, 1e-3, 1e-6, tangent, kind=kind, method="ode23s")
+    kw = {"alpha_n": alpha_n} if kind == 2 else {}
+    out = O.update_ode23(prm, en, e, zn6, 0.1, tangent=tangent, info=True, kind=kind, method="ode23s", **kw)
+    assert np.all((st >> 16) & 1) and np.all(out[-1][:, 2] == 1)
+    rel = np.abs(sig - out[0]).max(1) / np.abs(out[0]).max(1)
+    relz = np.abs(z[:, :6] - out[1]).max(1) / np.maximum(np.abs(out[1] - zn6).max(1), 1e-300)
+    tight = (rel < 1e-10) & (relz < 1e-10)
+    if tangent:
+        C2 = out[3 if kind == 2 else 2].reshape(-1, 36)
+        tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
+    assert tight.mean() >= 0.98
     assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))

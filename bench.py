@@ -66,7 +66,10 @@ def parse():
     ap.add_argument("--voxels", type=int, default=N_VOX, help="batch size (profiling runs use a small batch)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
-    ap.add_argument("--no-ode23", action="store_true", help="skip the ode23 material-update measurement")
+    ap.add_argument("--no-ode23", action="store_true", help="skip the ODE material-update measurements")
+    ap.add_argument("--ode-voxels", type=int, default=1 << 22,
+                    help="voxels of the ODE measurements (profiling runs use a small batch)")
+    ap.add_argument("--no-mmc", action="store_true", help="skip the MMC scheme run of the ODE measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving sample")
     ap.add_argument("--serve-full", action="store_true",
@@ -454,12 +457,12 @@ def bench_mixed(G, torch):
 
 def bench_ode23(G, torch, args):
     """Adaptive ode23 material update (force-potential form, stress-driven error
-    control, MATLAB's default tolerances rtol 1e-3, atol 1e-6) on 2^22 voxels of
+    control, MATLAB's default tolerances rtol 1e-3, atol 1e-6) on 2^22 (--ode-voxels) voxels of
     load-step-like inputs (synth.ode23_batch, Norton n = 5, h = 0.1), without and
     with the tangent ODE; FP64."""
     import numpy as np
     import synth
-    n = 1 << 22
+    n = args.ode_voxels
     en, e, zn = synth.ode23_batch(n, seed=2024)
     E0 = torch.from_numpy(np.ascontiguousarray(en.T)).cuda()
     E1 = torch.from_numpy(np.ascontiguousarray(e.T)).cuda()
@@ -468,7 +471,7 @@ def bench_ode23(G, torch, args):
     z = torch.empty_like(E1)
     st = torch.empty(n, dtype=torch.int32, device="cuda")
     mat = G.norton(*PARAMS)
-    out = {"workload": "2^22 voxels, synth.ode23_batch (z_n as the material batch, eps_n = z_n + U[-0.002,0.002]^6, "
+    out = {"workload": f"{n} voxels, synth.ode23_batch (z_n as the material batch, eps_n = z_n + U[-0.002,0.002]^6, "
                        "eps = eps_n + U[-0.001,0.001]^6), Norton n=5, h=0.1, rtol 1e-3, atol 1e-6, FP64"}
     stream = torch.cuda.current_stream()
     for name, tan in (("no_tangent", None), ("tangent", torch.empty(36, n, dtype=torch.float64, device="cuda"))):
@@ -514,9 +517,11 @@ def bench_ode23(G, torch, args):
     # the tangent on the first 2^20 (ode12) or 2^18 (ode23s) voxels
     for name, meth, m, tan in (
             ("ode12_no_tangent", "ode12", n, None),
-            ("ode12_tangent", "ode12", 1 << 20, torch.empty(36, 1 << 20, dtype=torch.float64, device="cuda")),
+            ("ode12_tangent", "ode12", min(n, 1 << 20),
+             torch.empty(36, min(n, 1 << 20), dtype=torch.float64, device="cuda")),
             ("ode23s_no_tangent", "ode23s", n, None),
-            ("ode23s_tangent", "ode23s", 1 << 18, torch.empty(36, 1 << 18, dtype=torch.float64, device="cuda"))):
+            ("ode23s_tangent", "ode23s", min(n, 1 << 18),
+             torch.empty(36, min(n, 1 << 18), dtype=torch.float64, device="cuda"))):
         views = [t[:, :m].contiguous() for t in (E0, E1, Z0)]
         sg, zz = torch.empty_like(views[1]), torch.empty_like(views[1])
         st2 = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -535,7 +540,8 @@ def bench_ode23(G, torch, args):
                      "mean_rejected_substeps": float(((s2 >> 20) & 0x7FF).mean()),
                      "converged_fraction": float(((s2 >> 16) & 1).mean())}
         del tan
-    out["mmc_scheme"] = bench_mmc_scheme(G, torch)
+    if not args.no_mmc:
+        out["mmc_scheme"] = bench_mmc_scheme(G, torch)
     return out
 
 

@@ -119,6 +119,23 @@ int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, in
                void* sigma, void* z, void* tangent, int32_t* status, void* stream);
 
 /*
+ * gsm_update_host -- gsm_update for arrays that live in page-locked host memory,
+ * streamed through the device in chunks of `chunk` voxels (0: 2^20): the
+ * host->device copies of chunk i+1 and the device->host copies of chunk i-1
+ * (two internal streams, the copy engines of both directions of the host link)
+ * overlap the update of chunk i (on `stream`).  Same arguments, layouts and
+ * results as gsm_update (bit-identical to it on device copies of the arrays);
+ * every non-NULL array must be page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister), else GSM_EINVAL.  Device staging buffers for three
+ * chunks come from the stream-ordered allocator of the current device and go
+ * back to it on `stream`.  Asynchronous on `stream`: the results are in host
+ * memory once `stream` has passed this call.  Errors: GSM_EINVAL, GSM_ENOMEM,
+ * GSM_ENOTSUP, GSM_ECUDA.
+ */
+int gsm_update_host(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, int64_t ld, double step_h,
+                    void* sigma, void* z, void* tangent, int32_t* status, int64_t chunk, void* stream);
+
+/*
  * gsm_update_ode23 -- material update by adaptive explicit Runge-Kutta
  * integration of the force-potential form ydot = dPsi/dA(-d psi/dy) over the
  * load step (Sec. 4.3: the Bogacki-Shampine 3(2) pair of MATLAB's ode23, step

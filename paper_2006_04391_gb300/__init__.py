@@ -33,7 +33,7 @@ EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kerne
            "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc",
            "serve_create", "serve_destroy", "serve_submit", "serve_tick", "serve_job_state", "serve_fetch",
            "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy", "gsm_update_ode23",
-           "gsm_update_ode")
+           "gsm_update_ode", "gsm_update_host")
 
 _lib = None
 
@@ -93,6 +93,7 @@ def load(path=None):
     lib.gsm_destroy.argtypes = [vp]
     lib.gsm_update.argtypes = [vp, i64, vp, vp, i64, dbl, vp, vp, vp, vp, vp]
     lib.gsm_update_ode23.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.gsm_update_host.argtypes = [vp, i64, vp, vp, i64, dbl, vp, vp, vp, vp, i64, vp]
     lib.gsm_update_ode.argtypes = [vp, ctypes.c_int, i64, vp, vp, vp, i64, dbl, dbl, dbl, ctypes.c_int, vp, vp, vp, vp,
                                    vp]
     lib.gsm_strerror.restype = ctypes.c_char_p
@@ -231,6 +232,21 @@ def gsm_update(mat, eps, z_n, h, sigma, z, tangent=None, status=None, stream=Non
     rc = lib.gsm_update(mat.handle, n, _ptr(eps), _ptr(z_n), ld, float(h), _ptr(sigma), _ptr(z),
                         _ptr(tangent), _ptr(status), _stream_ptr(stream))
     _check(rc, "gsm_update")
+
+
+def gsm_update_host(mat, eps, z_n, h, sigma, z, tangent=None, status=None, chunk=0, stream=None, n_vox=None):
+    """gsm_update on pinned CPU tensors (``[6, ld]``, tangent ``[21, ld]``, status
+    ``[ld]``), streamed through the device in chunks with copies overlapping the
+    updates; asynchronous on ``stream``."""
+    lib = load()
+    ld = eps.shape[1]
+    n = ld if n_vox is None else int(n_vox)
+    for t, rows in ((eps, 6), (z_n, 6), (sigma, 6), (z, 6), (tangent, 21)):
+        if t is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != ld or not t.is_contiguous()):
+            raise ValueError("fields must be contiguous [components, ld] tensors with a common ld")
+    rc = lib.gsm_update_host(mat.handle, n, _ptr(eps), _ptr(z_n), ld, float(h), _ptr(sigma), _ptr(z), _ptr(tangent),
+                             _ptr(status), int(chunk), _stream_ptr(stream))
+    _check(rc, "gsm_update_host")
 
 
 # -------------------------------------------------------------- basic scheme

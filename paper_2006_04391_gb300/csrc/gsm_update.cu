@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "voxel.cuh"
 
@@ -267,6 +269,130 @@ int gsm_update(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, in
   }
   return material_update(m, n_vox, in[0], in[1], ld, step_h, out[0], out[1], out[2], static_cast<int32_t*>(out[3]),
                          static_cast<cudaStream_t>(stream));
+}
+
+// Chunked host <-> device streaming of gsm_update: three slots of device
+// staging buffers; host->device copies on one stream, the updates on the
+// caller's stream, device->host copies on a third, ordered by events so that
+// the copies of chunks i + 1 and i - 1 overlap the update of chunk i.
+int gsm_update_host(gsm_handle h, int64_t n_vox, const void* eps, const void* z_n, int64_t ld, double step_h,
+                    void* sigma, void* z, void* tangent, int32_t* status, int64_t chunk, void* stream) {
+  if (!h || n_vox < 0 || ld < n_vox || chunk < 0) return GSM_EINVAL;
+  if (n_vox == 0) return GSM_OK;
+  const Material& m = *reinterpret_cast<const Material*>(h);
+  if (!eps || !sigma) return GSM_EINVAL;
+  if (m.psi_kind == GSM_PSI_ELASTIC_VP_KIN) return GSM_ENOTSUP;
+  const bool vp = m.psi_kind == GSM_PSI_ELASTIC_VP_DEV;
+  if (vp && (!z_n || !z)) return GSM_EINVAL;
+  if (!(std::isfinite(step_h) && step_h > 0.0)) return GSM_EINVAL;
+  // every array must be page-locked host memory (the copy engines read and write it)
+  const void* all[6] = {eps, z_n, sigma, z, tangent, status};
+  for (const void* p : all) {
+    if (!p) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return GSM_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeHost) return GSM_EINVAL;
+  }
+  const int64_t C = std::min<int64_t>(chunk > 0 ? chunk : (int64_t)1 << 20, n_vox);
+  const size_t es = m.precision == GSM_FP32 ? sizeof(float) : sizeof(double);
+  const bool use_z = z_n && z;  // (the elastic law copies z_n into z when both are given)
+  // per slot: eps, z_n, sigma, z [6][C]; tangent [21][C]; status [C]
+  const size_t f6 = 6 * C * es, f21 = tangent ? 21 * C * es : 0, fst = status ? C * sizeof(int32_t) : 0;
+  const size_t slot = 2 * f6 + (use_z ? 2 * f6 : 0) + f21 + fst;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  constexpr int kSlots = 3;
+  char* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, kSlots * slot, cs) != cudaSuccess) {
+    cudaGetLastError();
+    return GSM_ENOMEM;
+  }
+  cudaStream_t in_s = nullptr, out_s = nullptr;
+  cudaEvent_t start = nullptr, end = nullptr, in_done[kSlots] = {}, comp_done[kSlots] = {}, out_done[kSlots] = {};
+  bool ok = cudaStreamCreateWithFlags(&in_s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&out_s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&end, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < kSlots; ++k)
+    ok = cudaEventCreateWithFlags(&in_done[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&comp_done[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&out_done[k], cudaEventDisableTiming) == cudaSuccess;
+  int rc = ok ? GSM_OK : GSM_ECUDA;
+  if (ok) {
+    // the copies start after the work already queued on the caller's stream
+    ok = cudaEventRecord(start, cs) == cudaSuccess && cudaStreamWaitEvent(in_s, start, 0) == cudaSuccess;
+    const size_t hp = ld * es;  // host row pitch
+    const int64_t n_chunks = (n_vox + C - 1) / C;
+    for (int64_t i = 0; ok && i < n_chunks; ++i) {
+      const int k = (int)(i % kSlots);
+      const int64_t c0 = i * C, len = std::min<int64_t>(C, n_vox - c0);
+      char* sb = buf + k * slot;
+      char* d_eps = sb;
+      char* d_zn = use_z ? sb + f6 : nullptr;
+      char* d_sig = sb + (use_z ? 2 * f6 : f6);
+      char* d_z = use_z ? sb + 3 * f6 : nullptr;
+      char* d_tan = tangent ? sb + (use_z ? 4 * f6 : 2 * f6) : nullptr;
+      int32_t* d_st = status ? reinterpret_cast<int32_t*>(sb + (use_z ? 4 * f6 : 2 * f6) + f21) : nullptr;
+      const size_t dp = C * es, w = len * es, off = c0 * es;
+      // host -> device, once the update of the slot's previous chunk has read its inputs
+      if (i >= kSlots) ok = ok && cudaStreamWaitEvent(in_s, comp_done[k], 0) == cudaSuccess;
+      ok = ok && cudaMemcpy2DAsync(d_eps, dp, static_cast<const char*>(eps) + off, hp, w, 6,
+                                   cudaMemcpyHostToDevice, in_s) == cudaSuccess;
+      if (use_z)
+        ok = ok && cudaMemcpy2DAsync(d_zn, dp, static_cast<const char*>(z_n) + off, hp, w, 6,
+                                     cudaMemcpyHostToDevice, in_s) == cudaSuccess;
+      ok = ok && cudaEventRecord(in_done[k], in_s) == cudaSuccess;
+      // the update, once the inputs are in and the slot's previous outputs are out
+      ok = ok && cudaStreamWaitEvent(cs, in_done[k], 0) == cudaSuccess;
+      if (i >= kSlots) ok = ok && cudaStreamWaitEvent(cs, out_done[k], 0) == cudaSuccess;
+      if (ok) {
+        const int r = material_update(m, len, d_eps, d_zn, C, step_h, d_sig, d_z, d_tan, d_st, cs);
+        if (r != GSM_OK) {
+          rc = r;
+          ok = false;
+        }
+      }
+      ok = ok && cudaEventRecord(comp_done[k], cs) == cudaSuccess;
+      // device -> host
+      ok = ok && cudaStreamWaitEvent(out_s, comp_done[k], 0) == cudaSuccess;
+      ok = ok && cudaMemcpy2DAsync(static_cast<char*>(sigma) + off, hp, d_sig, dp, w, 6, cudaMemcpyDeviceToHost,
+                                   out_s) == cudaSuccess;
+      if (use_z)
+        ok = ok && cudaMemcpy2DAsync(static_cast<char*>(z) + off, hp, d_z, dp, w, 6, cudaMemcpyDeviceToHost,
+                                     out_s) == cudaSuccess;
+      if (tangent)
+        ok = ok && cudaMemcpy2DAsync(static_cast<char*>(tangent) + off, hp, d_tan, dp, w, 21,
+                                     cudaMemcpyDeviceToHost, out_s) == cudaSuccess;
+      if (status)
+        ok = ok && cudaMemcpyAsync(status + c0, d_st, len * sizeof(int32_t), cudaMemcpyDeviceToHost, out_s) ==
+                       cudaSuccess;
+      ok = ok && cudaEventRecord(out_done[k], out_s) == cudaSuccess;
+    }
+    // the caller's stream continues once every result is in host memory
+    ok = ok && cudaEventRecord(end, out_s) == cudaSuccess && cudaStreamWaitEvent(cs, end, 0) == cudaSuccess;
+    if (!ok && rc == GSM_OK) rc = GSM_ECUDA;
+    if (!ok) {
+      // make sure nothing queued still uses the buffers before they go back
+      cudaStreamSynchronize(in_s);
+      cudaStreamSynchronize(out_s);
+      cudaStreamSynchronize(cs);
+    }
+  }
+  cudaFreeAsync(buf, cs);
+  // (streams and events are released once their queued work has completed)
+  for (int k = 0; k < kSlots; ++k) {
+    if (in_done[k]) cudaEventDestroy(in_done[k]);
+    if (comp_done[k]) cudaEventDestroy(comp_done[k]);
+    if (out_done[k]) cudaEventDestroy(out_done[k]);
+  }
+  if (start) cudaEventDestroy(start);
+  if (end) cudaEventDestroy(end);
+  if (in_s) cudaStreamDestroy(in_s);
+  if (out_s) cudaStreamDestroy(out_s);
+  if (rc != GSM_OK) cudaGetLastError();
+  return rc;
 }
 
 const char* gsm_strerror(int code) {

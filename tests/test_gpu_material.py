@@ -187,3 +187,43 @@ def test_pinned_host_arrays_zero_copy(gsm, precision):
     plain = torch.from_numpy(np.ascontiguousarray(eps.T))  # pageable, not registered
     with pytest.raises(gsm.GsmError):
         gsm.gsm_update(mat, plain, h_z0, 0.01, h_s, h_z, None, None)
+
+
+@pytest.mark.parametrize("precision,chunk", [(0, 1000), (1, 0), (2, 1537)])
+def test_host_streamed_update(gsm, precision, chunk):
+    """gsm_update_host (pinned host arrays streamed through the device in chunks,
+    copies overlapping the updates) gives gsm_update's results bit for bit: a
+    ragged last chunk, slots reused several times (chunk 1000 over 9 chunks),
+    ld > n, with tangent and status.  Device or unregistered arrays are refused."""
+    import torch
+    n, ld = 8 * 1000 + 123, 8 * 1000 + 130
+    eps, zn = synth.material_batch(n, seed=37)
+    mat = gsm.norton(*synth.MATRIX_16, precision=precision)
+    dt = torch.float32 if precision == 2 else torch.float64
+
+    def soa_pad(a):
+        out = torch.zeros(a.shape[1], ld, dtype=dt)
+        out[:, :n] = torch.from_numpy(np.ascontiguousarray(a.T)).to(dt)
+        return out
+
+    d_e, d_z0 = soa_pad(eps).cuda(), soa_pad(zn).cuda()
+    d_s, d_z = torch.zeros_like(d_e), torch.zeros_like(d_e)
+    d_t = torch.zeros(21, ld, dtype=dt, device="cuda")
+    d_st = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    gsm.gsm_update(mat, d_e, d_z0, 0.01, d_s, d_z, d_t, d_st, n_vox=n)
+    h_e, h_z0 = soa_pad(eps).pin_memory(), soa_pad(zn).pin_memory()
+    h_s = torch.full_like(h_e, float("nan")).pin_memory()
+    h_z = torch.full_like(h_e, float("nan")).pin_memory()
+    h_t = torch.full((21, ld), float("nan"), dtype=dt).pin_memory()
+    h_st = torch.zeros(ld, dtype=torch.int32).pin_memory()
+    gsm.gsm_update_host(mat, h_e, h_z0, 0.01, h_s, h_z, h_t, h_st, chunk=chunk, n_vox=n)
+    torch.cuda.synchronize()
+    assert torch.equal(h_s[:, :n], d_s[:, :n].cpu())
+    assert torch.equal(h_z[:, :n], d_z[:, :n].cpu())
+    assert torch.equal(h_t[:, :n], d_t[:, :n].cpu())
+    assert torch.equal(h_st[:n], d_st[:n].cpu())
+    assert torch.isnan(h_s[:, n:]).all()  # the padding columns are not touched
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update_host(mat, d_e, h_z0, 0.01, h_s, h_z, None, None, n_vox=n)
+    with pytest.raises(gsm.GsmError):
+        gsm.gsm_update_host(mat, soa_pad(eps), h_z0, 0.01, h_s, h_z, None, None, n_vox=n)

@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--ode-voxels", type=int, default=1 << 22,
                     help="voxels of the ODE measurements (profiling runs use a small batch)")
     ap.add_argument("--no-mmc", action="store_true", help="skip the MMC scheme run of the ODE measurements")
+    ap.add_argument("--ms-n", type=int, default=256, help="grid of the basic-scheme measurement (profiling: 128)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the homogenization-setting scheme runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving sample")
     ap.add_argument("--serve-full", action="store_true",
@@ -258,7 +260,7 @@ def run_ours(args):
 
     ms_block = None
     if not args.no_ms and rank == 0:
-        ms_block = bench_ms(G, torch)
+        ms_block = bench_ms(G, torch, args)
     serve_block = None
     if not args.no_serve and rank == 0:
         serve_block = bench_serve(G, args)
@@ -405,16 +407,17 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_b
     print(json.dumps(out))
 
 
-def bench_ms(G, torch):
-    """Basic-scheme iterations/s at 256^3 (fibre composite), FP64 and FP32 bulk."""
+def bench_ms(G, torch, args):
+    """Basic-scheme iterations/s at 256^3 (--ms-n) (fibre composite), FP64 and FP32 bulk."""
     if not hasattr(G.load(), "ms_create"):
         return None
     import numpy as np
     import synth
-    ph, frac, nf = synth.fibre_composite(256, seed=0)
+    N = args.ms_n
+    ph, frac, nf = synth.fibre_composite(N, seed=0)
     phase = torch.from_numpy(ph).cuda()
-    res = {"workload": f"256^3 RSA cylinders r=6 L=180, 15 percent (achieved {frac:.4f}, {nf} fibres), "
-                       "n=10, shear+tension"}
+    res = {"workload": f"{N}^3 RSA cylinders r=6 L={min(180.0, 0.7 * N):g}, 15 percent (achieved {frac:.4f}, "
+                       f"{nf} fibres), n=10, shear+tension"}
     loads, hs = synth.shear_tension_load(20, 0.02)
     # FP64: FP64 fields, FFTs and laws.  FP32 bulk: FP32 fields, FFTs and law
     # iterations, FP64 reductions; its FP64 iterations evaluate the law as FP32
@@ -435,7 +438,8 @@ def bench_ms(G, torch):
                      "final_error": float(out["final_error"][0]),
                      "law": "FP64" if law_prec == G.GSM_FP64 else "FP32 Newton + FP64 correction"}
         G.ms_destroy(ctx)
-    res["homogenization_setting"] = bench_mixed(G, torch)
+    if not args.no_mixed:
+        res["homogenization_setting"] = bench_mixed(G, torch)
     return res
 
 

@@ -109,18 +109,21 @@ template <int NV> __device__ void block_sum(double (&v)[NV], double* out, int64_
 }
 
 // Material evaluation of voxel i.  Every lane of a warp must call this (the
-// Newton loops vote warp-wide); lanes with in = false only vote.
+// Newton loops vote warp-wide); lanes with in = false only vote.  The field
+// precision T is also that of the 1/N^3 scaling and of the lane's partial
+// stress sums (FP32 fields: no FP64 work, a sixty-fourth of the FP32 rate on
+// GB300, outside the law; the block sums are FP64).
 template <class T, int MODE>
 __device__ __forceinline__ void material_voxel(int64_t i, bool in, int64_t nvox, const uint8_t* __restrict__ phase,
-                                               const PhaseTable& tab, const Step& hs, double inv_n3,
+                                               const PhaseTable& tab, const Step& hs, T inv_n3,
                                                const T* __restrict__ eps_raw, const T* __restrict__ zn,
-                                               T* __restrict__ sig, T* __restrict__ z, double (&acc)[6]) {
+                                               T* __restrict__ sig, T* __restrict__ z, T (&acc)[6]) {
   const int ph = in ? (int)phase[i] : 0;
   const bool vp = in && tab.kind[ph] == GSM_PSI_ELASTIC_VP_DEV;
   T e[6], zi[6], s[6], zo[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    e[c] = in ? (T)((double)__ldg(eps_raw + c * nvox + i) * inv_n3) : T(0);
+    e[c] = in ? __ldg(eps_raw + c * nvox + i) * inv_n3 : T(0);
     zi[c] = vp ? __ldg(zn + c * nvox + i) : T(0);
   }
   if constexpr (MODE == MODE_FP64) {
@@ -141,7 +144,7 @@ __device__ __forceinline__ void material_voxel(int64_t i, bool in, int64_t nvox,
     for (int c = 0; c < 6; ++c) {
       sig[c * nvox + i] = s[c];
       z[c * nvox + i] = zo[c];
-      acc[c] += (double)s[c];
+      acc[c] += s[c];
     }
   }
 }
@@ -221,13 +224,16 @@ __global__ void __launch_bounds__(kMatBlock) ms_material_kernel(int64_t nvox, co
                                                                 const T* __restrict__ eps_raw,
                                                                 const T* __restrict__ zn, T* __restrict__ sig,
                                                                 T* __restrict__ z, double* __restrict__ partials) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  T acc[6] = {0, 0, 0, 0, 0, 0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nvox; base += stride) {
     const int64_t i = base + threadIdx.x;
-    material_voxel<T, MODE>(i, i < nvox, nvox, phase, tab, hs, inv_n3, eps_raw, zn, sig, z, acc);
+    material_voxel<T, MODE>(i, i < nvox, nvox, phase, tab, hs, (T)inv_n3, eps_raw, zn, sig, z, acc);
   }
-  block_sum<6>(acc, partials, gridDim.x);
+  double accd[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) accd[c] = (double)acc[c];
+  block_sum<6>(accd, partials, gridDim.x);
 }
 
 // Index of the job owning global chunk c (starts ascending, starts[0] = 0).
@@ -251,15 +257,18 @@ __global__ void __launch_bounds__(kMatBlock) ms_material_batch_kernel(const JobV
     const JobView& v = views[owner(starts, n_jobs, gc)];
     const int64_t lc = gc - v.vchunk0;
     const Step hs{v.h, v.inv_h, (float)v.h, (float)v.inv_h};
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll 1
     for (int sweep = 0; sweep < kVChunk / kMatBlock; ++sweep) {
       const int64_t i = lc * kVChunk + sweep * kMatBlock + threadIdx.x;
-      material_voxel<T, MODE>(i, i < v.nvox, v.nvox, v.phase, *v.tab, hs, v.inv_n3,
+      material_voxel<T, MODE>(i, i < v.nvox, v.nvox, v.phase, *v.tab, hs, (T)v.inv_n3,
                               static_cast<const T*>(v.eps_raw), static_cast<const T*>(v.zn),
                               static_cast<T*>(v.sig), static_cast<T*>(v.z), acc);
     }
-    block_sum_at<6>(acc, v.mat_part, v.n_vch, lc);
+    double accd[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) accd[c] = (double)acc[c];
+    block_sum_at<6>(accd, v.mat_part, v.n_vch, lc);
   }
 }
 

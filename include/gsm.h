@@ -371,6 +371,11 @@ typedef struct serve_job {
   double tol;
   int max_iter;
   double switch_tol;          /* <= 0: 1e-5                                   */
+  int integrator;             /* as ms_load.integrator: 0 implicit Euler, 1 ode23,
+                                 2 ode12, 3 ode23s (1-3 with MS_PREC_FP64 only;
+                                 needed for GSM_PSI_ELASTIC_VP_KIN phases)     */
+  double ode_rtol, ode_atol;  /* integrator >= 1, as in ms_load                */
+  int ode_max_substeps;       /* integrator >= 1, as in ms_load                */
 } serve_job;
 
 typedef struct serve_server* serve_handle;
@@ -382,8 +387,12 @@ int serve_create(serve_handle* out, size_t hbm_budget_bytes, int max_active, voi
 int serve_destroy(serve_handle h);
 
 /* serve_submit -- queue a job (host copies of all inputs; the caller's arrays
- * may be freed on return) and return its id.  GSM_ENOMEM if the job alone
- * exceeds the budget, GSM_EINVAL on bad input. */
+ * may be freed on return) and return its id.  Jobs with ODE-integrated laws
+ * are batched with the others (their own launch group per integrator) and
+ * also take the ODE work arrays from the budget (8 N^3 doubles: the strain at
+ * t_n, and alpha twice for Michel-Suquet phases).  GSM_ENOMEM if the job alone
+ * exceeds the budget, GSM_EINVAL on bad input, GSM_ENOTSUP for combinations
+ * ms_run refuses. */
 int serve_submit(serve_handle h, const serve_job* job, int64_t* id);
 
 /* serve_tick -- admit queued jobs, run one iteration of every active job,
@@ -401,7 +410,8 @@ int serve_job_state(serve_handle h, int64_t id, int32_t* state, int32_t* step, i
 int serve_fetch(serve_handle h, int64_t id, double* Sigma, int32_t* iters, double* final_error);
 
 /* serve_job_bytes -- device bytes a job of this size takes from the budget
- * (fields, work areas, and its cuFFT plans if none of that size exist yet). */
+ * (fields, work areas, and its cuFFT plans if none of that size exist yet;
+ * jobs with ODE-integrated laws add their ODE work arrays). */
 size_t serve_job_bytes(int N, int precision);
 
 /*

@@ -68,7 +68,9 @@ class serve_job(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int),
                 ("laws", ctypes.POINTER(ctypes.c_void_p)), ("precision", ctypes.c_int), ("n_steps", ctypes.c_int),
                 ("E", ctypes.POINTER(ctypes.c_double)), ("h", ctypes.POINTER(ctypes.c_double)),
-                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("switch_tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("switch_tol", ctypes.c_double),
+                ("integrator", ctypes.c_int), ("ode_rtol", ctypes.c_double), ("ode_atol", ctypes.c_double),
+                ("ode_max_substeps", ctypes.c_int)]
 
 
 class ms_result(ctypes.Structure):
@@ -440,8 +442,11 @@ class Server:
                                 _stream_ptr(stream)), "serve_create")
         self.n_steps = {}
 
-    def submit(self, phase, laws, E, hs, tol=1e-6, max_iter=20000, precision=MS_PREC_FP32_BULK, switch_tol=0.0):
-        """Queue a job; ``phase`` is a host uint8 array (N, N, N).  Returns the job id."""
+    def submit(self, phase, laws, E, hs, tol=1e-6, max_iter=20000, precision=MS_PREC_FP32_BULK, switch_tol=0.0,
+               ode=None, ode_method="ode23"):
+        """Queue a job; ``phase`` is a host uint8 array (N, N, N).  ``ode`` = (rtol, atol[,
+        max_substeps]) integrates the laws over each step by ``ode_method`` (FP64 jobs).
+        Returns the job id."""
         lib = load()
         ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
         E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
@@ -450,7 +455,9 @@ class Server:
         job = serve_job(int(ph.shape[0]), ph.ctypes.data, len(laws), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
                         int(precision), E.shape[0], E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iter),
-                        float(switch_tol))
+                        float(switch_tol), 0 if ode is None else 1 + ODE_METHODS[ode_method],
+                        float(ode[0]) if ode is not None else 1e-3, float(ode[1]) if ode is not None else 1e-6,
+                        int(ode[2]) if ode is not None and len(ode) > 2 else 100000)
         jid = ctypes.c_int64()
         _check(lib.serve_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)), "serve_submit")
         self.n_steps[jid.value] = E.shape[0]

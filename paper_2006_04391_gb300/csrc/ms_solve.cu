@@ -326,6 +326,27 @@ int job_alloc(Job& j, cudaStream_t s, const uint8_t* phase_host) {
   return GSM_OK;
 }
 
+// Work arrays of the ODE integrators (the strain at t_n and, for Michel-Suquet
+// phases, alpha double-buffered), allocated once; alpha_n starts at 0.
+int job_alloc_ode(Job& j, cudaStream_t s) {
+  const size_t n6 = 6 * (size_t)j.nvox * sizeof(double), n1 = (size_t)j.nvox * sizeof(double);
+  if (j.integrator >= 1 && !j.eps_prev && cudaMallocAsync(&j.eps_prev, n6, s) != cudaSuccess) return GSM_ENOMEM;
+  if (j.has_kin) {
+    if (!j.alpha_n && cudaMallocAsync(&j.alpha_n, n1, s) != cudaSuccess) return GSM_ENOMEM;
+    if (!j.alpha && cudaMallocAsync(&j.alpha, n1, s) != cudaSuccess) return GSM_ENOMEM;
+    cudaMemsetAsync(j.alpha_n, 0, n1, s);
+  }
+  return GSM_OK;
+}
+
+// Device bytes of the ODE work arrays of a loaded job.
+size_t ode_bytes(const Job& j) {
+  size_t b = 0;
+  if (j.integrator >= 1) b += 6 * (size_t)j.nvox * sizeof(double);
+  if (j.has_kin) b += 2 * (size_t)j.nvox * sizeof(double);
+  return b;
+}
+
 int job_load(Job& j, const ms_load* load) {
   if (!load || load->n_steps < 1 || !load->E || !load->h || load->max_iter < 1) return GSM_EINVAL;
   for (int k = 0; k < load->n_steps; ++k)
@@ -824,13 +845,8 @@ int ms_run(ms_handle h, const ms_load* load, ms_state* state, ms_result* result)
   for (int q = 0; q < 6; ++q) j.E_prev[q] = 0.0;
   // alpha (the Michel-Suquet law's seventh internal variable) lives in the context only
   if (j.has_kin && state && state->resume) return GSM_ENOTSUP;
-  if (j.integrator >= 1 && !j.eps_prev && cudaMallocAsync(&j.eps_prev, n6 * sizeof(double), s) != cudaSuccess)
-    return GSM_ENOMEM;
-  if (j.has_kin) {
-    if (!j.alpha_n && cudaMallocAsync(&j.alpha_n, j.nvox * sizeof(double), s) != cudaSuccess) return GSM_ENOMEM;
-    if (!j.alpha && cudaMallocAsync(&j.alpha, j.nvox * sizeof(double), s) != cudaSuccess) return GSM_ENOMEM;
-    cudaMemsetAsync(j.alpha_n, 0, j.nvox * sizeof(double), s);
-  }
+  rc = job_alloc_ode(j, s);
+  if (rc != GSM_OK) return rc;
   if (state && state->resume) {
     if (!state->eps || !state->z) return GSM_EINVAL;
     convert<double, double>(s, state->eps, j.f64.eps_raw, n6, n3);
@@ -919,12 +935,13 @@ int serve_submit(serve_handle h, const serve_job* desc, int64_t* id) {
   ld.stress_mask = 0;
   ld.Sigma = nullptr;
   ld.ref_update = 0;
-  ld.integrator = 0;
-  ld.ode_rtol = 1e-3;
-  ld.ode_atol = 1e-6;
-  ld.ode_max_substeps = 100000;
+  ld.integrator = desc->integrator;
+  ld.ode_rtol = desc->ode_rtol;
+  ld.ode_atol = desc->ode_atol;
+  ld.ode_max_substeps = desc->ode_max_substeps;
   rc = job_load(*p.job, &ld);
   if (rc != GSM_OK) return rc;
+  p.job->bytes += ode_bytes(*p.job);
   if (p.job->bytes + plan_bytes(desc->N, desc->precision) > sv->budget) return GSM_ENOMEM;  // never admissible
   p.phase.assign(desc->phase, desc->phase + p.job->nvox);
   p.job->id = sv->next_id++;
@@ -948,6 +965,7 @@ int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_
       if (!sv->plan_cost.count(std::make_pair(j.N, f))) extra += plan_bytes_one(j.N, f == 1);
     if (sv->used + extra > sv->budget) break;
     int rc = job_alloc(j, g.stream, p.phase.data());
+    if (rc == GSM_OK) rc = job_alloc_ode(j, g.stream);
     if (rc != GSM_OK) return rc;
     Plans* pl = nullptr;
     for (int f = 0; f < n_prec; ++f) {

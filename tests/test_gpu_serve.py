@@ -98,3 +98,49 @@ def test_stream_driver_poisson(gsm):
     lat = [r["latency"] for r in res["jobs"]]
     assert all(x > 0 for x in lat) and res["latency_p99"] >= res["latency_p50"] > 0
     assert all(r["rc"] == 0 for r in res["jobs"])
+
+
+def test_ode_law_jobs_served_with_implicit_jobs(gsm):
+    """Jobs whose laws integrate over each step by ode23 / ode23s (the paper's
+    Michel-Suquet metal-matrix composite; ODE tolerance below the equilibrium
+    tolerance) are served in the same ticks as an implicit-Euler Norton job:
+    each result equals its solo serve and the single-solve path bit for bit."""
+    import torch
+    ms_laws = [gsm.michel_suquet(*synth.ALUMINIUM_MS), gsm.elastic(*synth.ALUMINA)]
+    nor_laws = [gsm.norton(*synth.MATRIX_16), gsm.elastic(*synth.INCLUSION_16)]
+    specs = [  # (phase, laws, E, h, ode, method)
+        (synth.sphere_phase(10, 0.2), ms_laws, synth.ramp(2, [0.003, -0.001, -0.001, 0, 0, 0]), [0.5, 0.5],
+         (1e-8, 1e-11), "ode23"),
+        (synth.sphere_phase(12, 0.15), nor_laws, synth.ramp(2, [0.004, 0, 0, 0, 0.002, 0]), [0.1, 0.1],
+         None, "ode23"),
+        (synth.sphere_phase(8, 0.2), ms_laws, synth.ramp(2, [0.002, 0, 0, 0.002, 0, 0]), [0.5, 0.5],
+         (1e-8, 1e-11), "ode23s"),
+    ]
+
+    def serve(idx):
+        sv = gsm.Server(4 << 30, 8)
+        ids = {}
+        for k, i in enumerate(idx):
+            ph, laws, E, h, ode, meth = specs[i]
+            ids[i] = sv.submit(ph, laws, E, h, tol=1e-6, precision=gsm.MS_PREC_FP64, ode=ode, ode_method=meth)
+        out = {}
+        while len(out) < len(idx):
+            sv.tick()
+            for i, jid in ids.items():
+                if i not in out and sv.state(jid)[0] in (gsm.SERVE_DONE, gsm.SERVE_DONE_NOTCONV):
+                    out[i] = sv.fetch(jid)
+        sv.close()
+        return out
+
+    mixed = serve([0, 1, 2])
+    for i, (ph, laws, E, h, ode, meth) in enumerate(specs):
+        alone = serve([i])[i]
+        assert np.array_equal(mixed[i]["Sigma"], alone["Sigma"]) and np.array_equal(mixed[i]["iters"], alone["iters"])
+        single = gsm.ms_solve(torch.from_numpy(ph).cuda(), laws, E, h, tol=1e-6, max_iter=20000, ode=ode,
+                              ode_method=meth)
+        assert np.array_equal(single["Sigma"], alone["Sigma"])
+    # the Michel-Suquet law still needs an ODE integrator when served
+    sv = gsm.Server(1 << 30, 2)
+    with pytest.raises(gsm.GsmError):
+        sv.submit(specs[0][0], ms_laws, specs[0][2], specs[0][3], precision=gsm.MS_PREC_FP64)
+    sv.close()

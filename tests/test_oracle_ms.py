@@ -181,3 +181,63 @@ def test_homogeneous_viscoplastic_grid_follows_single_voxel_history():
     for k in range(4):
         s, zn = O.update(O.KIND_NORTON, prm, loads[k][None], zn, 0.1)
         assert np.max(np.abs(r["Sigma"][k] - s[0])) < 1e-14
+
+
+def _single_mode_stress(N, kvec, A, mean):
+    """sigma(x) = mean + A cos(2 pi k . x) on the voxel centres x = (i, j, l)/N
+    of the unit cell, stress-like Voigt (N^3, 6)."""
+    i, j, l = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    ph = 2.0 * np.pi * (kvec[0] * i + kvec[1] * j + kvec[2] * l) / N
+    return (np.asarray(mean)[None, :] + np.cos(ph).reshape(-1, 1) * np.asarray(A)[None, :])
+
+
+def _tensor(v):
+    s = np.asarray(v, dtype=float)
+    return np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+
+
+@pytest.mark.parametrize("N,kvec", [(8, (1, 2, -3)), (9, (2, -1, 4)), (6, (0, 1, 1))])
+def test_equilibrium_error_of_a_single_mode_field(N, kvec):
+    """Closed form of the stopping measure (Sec. 3 iterates until equilibrium; the
+    measure is reading 8): for sigma = S + A cos(2 pi k.x) the normalised DFT
+    holds A/2 at the two modes +-k, whose wave vectors are +-2 pi k, so
+        sum_xi |xi . c(xi)|^2 = 2 |2 pi (A k)/2|^2 = 2 pi^2 |A k|^2
+    and e = sqrt(2) pi |A k| / |S|_F, with |S|_F counting each shear twice.
+    A dropped 2 pi, a missing 1/N^3 or an engineering-shear weight on the
+    stress changes the value."""
+    A = np.array([0.3, -0.1, 0.2, 0.05, -0.07, 0.11])
+    S = np.array([1.0, 0.4, -0.2, 0.3, 0.1, -0.5])
+    sig = _single_mode_stress(N, kvec, A, S)
+    sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
+    e = MS.equilibrium_error(sig_hat, sig.mean(axis=0), N, floor=0.0)
+    Ak = _tensor(A) @ np.asarray(kvec, dtype=float)
+    S_F = np.sqrt(np.sum(S[:3] ** 2) + 2.0 * np.sum(S[3:] ** 2))
+    expect = np.sqrt(2.0) * np.pi * np.linalg.norm(Ak) / S_F
+    assert abs(e - expect) < 1e-12 * expect
+
+
+def test_equilibrium_error_nyquist_modes_and_floor():
+    """Even N: the pure-axis Nyquist mode k = (N/2, 0, 0) is a single real mode,
+    cos(pi i) = (-1)^i, with c = A and |xi| = pi N, so e = pi N |A e_1| / |S|_F;
+    a mixed Nyquist mode (N/2, 1, 0) is excluded (reading 6) and contributes
+    nothing; with zero mean stress the floor is the denominator."""
+    N = 8
+    A = np.array([0.3, -0.1, 0.2, 0.05, -0.07, 0.11])
+    S = np.array([1.0, 0.4, -0.2, 0.3, 0.1, -0.5])
+    S_F = np.sqrt(np.sum(S[:3] ** 2) + 2.0 * np.sum(S[3:] ** 2))
+    sig = _single_mode_stress(N, (N // 2, 0, 0), A, S)
+    sig_hat = np.stack([np.fft.fftn(sig[:, c].reshape(N, N, N)) for c in range(6)])
+    e = MS.equilibrium_error(sig_hat, sig.mean(axis=0), N, floor=0.0)
+    expect = np.pi * N * np.linalg.norm(_tensor(A)[:, 0]) / S_F
+    assert abs(e - expect) < 1e-12 * expect
+    mixed = _single_mode_stress(N, (N // 2, 1, 0), A, S)
+    mixed_hat = np.stack([np.fft.fftn(mixed[:, c].reshape(N, N, N)) for c in range(6)])
+    # (FFT rounding only: the same field on a non-excluded mode gives e of order 10)
+    assert MS.equilibrium_error(mixed_hat, mixed.mean(axis=0), N, floor=0.0) < 1e-12 * expect
+    # zero mean: e = sqrt(2) pi |A k| / floor
+    k = (1, 0, 2)
+    z = _single_mode_stress(N, k, A, np.zeros(6))
+    z_hat = np.stack([np.fft.fftn(z[:, c].reshape(N, N, N)) for c in range(6)])
+    e0 = MS.equilibrium_error(z_hat, np.zeros(6), N, floor=0.25)
+    expect0 = np.sqrt(2.0) * np.pi * np.linalg.norm(_tensor(A) @ np.array(k, float)) / 0.25
+    assert abs(e0 - expect0) < 1e-12 * expect0

@@ -13,6 +13,8 @@ Contents
   radial return (the conventional strategy of Sec. 4), and the ode23 update
   of the force-potential form with its tangent ODE (Sec. 4.3, Corollary 1)
   and stress-driven error control (Sec. 4.5).
+* ``material.flop_pieces`` -- the algorithmic flops of each piece of that
+  update, counted by running the same statements once on a counting scalar.
 * ``ms`` -- the Moulinec-Suquet basic scheme (cited by the paper in Sec. 1 and
   Sec. 3 "Material Law Evaluations") written with ``numpy.fft``.
 
@@ -24,4 +26,5 @@ from .material import (  # noqa: F401
     KIND_ELASTIC, KIND_NORTON, lame, update, radial_return, psi, psi_y, psi_yy,
     phi, phi_v, phi_vv, residual, newton_matrix, incremental_potential, stress,
     max_threads, P_MATRIX, G_MATRIX, update_ode23, psi_force_a, psi_force_ms, psi_force_aaa, gen_stress_ms, KIND_MICHEL_SUQUET,
+    flop_pieces, FLOP_PIECES, FLOP_KINDS,
 )

@@ -101,40 +101,48 @@ void make_law(int kind, const double* prm, Law* L) {
 
 // ------------------------------------------------------------ free energy psi
 // psi(eps, y) = 1/2 (eps - P y)^T C (eps - P y)   (Eq. michel_suquet_omega, H = 0)
+//
+// The helpers below are templates on the scalar type R: R = double is the
+// oracle; R = Counted (further down) runs the same statements once to count
+// the method's arithmetic (algorithmic flops per step of the update).
 
-void elastic_strain(const double eps[6], const double y[5], double e[6]) {
+template <class R>
+void elastic_strain(const R eps[6], const R y[5], R e[6]) {
   for (int i = 0; i < 6; ++i) {
-    double pz = 0.0;
+    R pz = 0.0;
     for (int a = 0; a < 5; ++a) pz += P[i][a] * y[a];
     e[i] = eps[i] - pz;
   }
 }
 
-void stress(const Law& L, const double eps[6], const double y[5], double sig[6]) {
-  double e[6];
+template <class R>
+void stress(const Law& L, const R eps[6], const R y[5], R sig[6]) {
+  R e[6];
   elastic_strain(eps, y, e);
   for (int i = 0; i < 6; ++i) {
-    double s = 0.0;
+    R s = 0.0;
     for (int j = 0; j < 6; ++j) s += L.C[i][j] * e[j];
     sig[i] = s;
   }
 }
 
-double psi(const Law& L, const double eps[6], const double y[5]) {
-  double e[6], sig[6];
+template <class R>
+R psi(const Law& L, const R eps[6], const R y[5]) {
+  R e[6], sig[6];
   elastic_strain(eps, y, e);
   stress(L, eps, y, sig);
-  double s = 0.0;
+  R s = 0.0;
   for (int i = 0; i < 6; ++i) s += e[i] * sig[i];
   return 0.5 * s;
 }
 
 // d psi / d y = -P^T C (eps - P y) = -P^T sigma
-void psi_y(const Law& L, const double eps[6], const double y[5], double g[5]) {
-  double sig[6];
+template <class R>
+void psi_y(const Law& L, const R eps[6], const R y[5], R g[5]) {
+  R sig[6];
   stress(L, eps, y, sig);
   for (int a = 0; a < 5; ++a) {
-    double s = 0.0;
+    R s = 0.0;
     for (int i = 0; i < 6; ++i) s += P[i][a] * sig[i];
     g[a] = -s;
   }
@@ -155,40 +163,47 @@ void psi_yy(const Law& L, double H[5][5]) {
 // phi(v) = sigma0 edot0 n/(n+1) (s/edot0)^((n+1)/n),  s = sqrt(v^T G v)
 // (convex dual of the paper's Psi, Eq. michel_suquet_psi, at sigma_Y = 0, H = 0)
 
-double eqrate(const Law& L, const double v[5], double Gv[5]) {
-  double q = 0.0;
+template <class R>
+R eqrate(const Law& L, const R v[5], R Gv[5]) {
+  R q = 0.0;
   for (int a = 0; a < 5; ++a) {
-    double s = 0.0;
+    R s = 0.0;
     for (int b = 0; b < 5; ++b) s += L.G[a][b] * v[b];
     Gv[a] = s;
     q += v[a] * s;
   }
-  return std::sqrt(q);
+  using std::sqrt;
+  return sqrt(q);
 }
 
-double phi(const Law& L, const double v[5]) {
-  double Gv[5];
-  const double s = eqrate(L, v, Gv);
-  return L.sigma0 * L.edot0 * L.n / (L.n + 1.0) * std::pow(s / L.edot0, (L.n + 1.0) / L.n);
+template <class R>
+R phi(const Law& L, const R v[5]) {
+  R Gv[5];
+  const R s = eqrate(L, v, Gv);
+  using std::pow;
+  return L.sigma0 * L.edot0 * L.n / (L.n + 1.0) * pow(s / L.edot0, (L.n + 1.0) / L.n);
 }
 
 // phi_v = sigma0 edot0^(-1/n) s^(1/n - 1) G v   (= 0 at v = 0 by continuity)
-void phi_v(const Law& L, const double v[5], double g[5]) {
-  double Gv[5];
-  const double s = eqrate(L, v, Gv);
+template <class R>
+void phi_v(const Law& L, const R v[5], R g[5]) {
+  R Gv[5];
+  const R s = eqrate(L, v, Gv);
   if (s == 0.0) {
     for (int a = 0; a < 5; ++a) g[a] = 0.0;
     return;
   }
-  const double c = L.sigma0 * std::pow(L.edot0, -1.0 / L.n) * std::pow(s, 1.0 / L.n - 1.0);
+  using std::pow;
+  const R c = L.sigma0 * std::pow(L.edot0, -1.0 / L.n) * pow(s, 1.0 / L.n - 1.0);
   for (int a = 0; a < 5; ++a) g[a] = c * Gv[a];
 }
 
 // phi_vv = sigma0 edot0^(-1/n) [ s^(1/n-1) G + (1/n - 1) s^(1/n-3) (Gv)(Gv)^T ]
 // At s = 0 it is finite only for n = 1; returns false otherwise.
-bool phi_vv(const Law& L, const double v[5], double H[5][5]) {
-  double Gv[5];
-  const double s = eqrate(L, v, Gv);
+template <class R>
+bool phi_vv(const Law& L, const R v[5], R H[5][5]) {
+  R Gv[5];
+  const R s = eqrate(L, v, Gv);
   const double k = L.sigma0 * std::pow(L.edot0, -1.0 / L.n);
   if (s == 0.0) {
     if (L.n != 1.0) return false;
@@ -196,8 +211,9 @@ bool phi_vv(const Law& L, const double v[5], double H[5][5]) {
       for (int b = 0; b < 5; ++b) H[a][b] = k * L.G[a][b];
     return true;
   }
-  const double c1 = k * std::pow(s, 1.0 / L.n - 1.0);
-  const double c2 = k * (1.0 / L.n - 1.0) * std::pow(s, 1.0 / L.n - 3.0);
+  using std::pow;
+  const R c1 = k * pow(s, 1.0 / L.n - 1.0);
+  const R c2 = k * (1.0 / L.n - 1.0) * pow(s, 1.0 / L.n - 3.0);
   for (int a = 0; a < 5; ++a)
     for (int b = 0; b < 5; ++b) H[a][b] = c1 * L.G[a][b] + c2 * Gv[a] * Gv[b];
   return true;
@@ -208,27 +224,31 @@ bool phi_vv(const Law& L, const double v[5], double H[5][5]) {
 // stationarity condition R(y) = psi_y + phi_v((y - y_n)/h) = 0 is the dual
 // form of Eq. (implicit_euler); Newton matrix K = psi_yy + phi_vv / h.
 
-void rate(const double y[5], const double yn[5], double h, double v[5]) {
+template <class R>
+void rate(const R y[5], const R yn[5], double h, R v[5]) {
   for (int a = 0; a < 5; ++a) v[a] = (y[a] - yn[a]) / h;
 }
 
-double Pi(const Law& L, const double eps[6], const double y[5], const double yn[5], double h) {
-  double v[5];
+template <class R>
+R Pi(const Law& L, const R eps[6], const R y[5], const R yn[5], double h) {
+  R v[5];
   rate(y, yn, h, v);
   return psi(L, eps, y) + h * phi(L, v);
 }
 
-void residual(const Law& L, const double eps[6], const double y[5], const double yn[5], double h,
-              double R[5]) {
-  double v[5], g1[5], g2[5];
+template <class R>
+void residual(const Law& L, const R eps[6], const R y[5], const R yn[5], double h, R Rv[5]) {
+  R v[5], g1[5], g2[5];
   rate(y, yn, h, v);
   psi_y(L, eps, y, g1);
   phi_v(L, v, g2);
-  for (int a = 0; a < 5; ++a) R[a] = g1[a] + g2[a];
+  for (int a = 0; a < 5; ++a) Rv[a] = g1[a] + g2[a];
 }
 
-bool newton_matrix(const Law& L, const double y[5], const double yn[5], double h, double K[5][5]) {
-  double v[5], H1[5][5], H2[5][5];
+template <class R>
+bool newton_matrix(const Law& L, const R y[5], const R yn[5], double h, R K[5][5]) {
+  R v[5], H2[5][5];
+  double H1[5][5];
   rate(y, yn, h, v);
   psi_yy(L, H1);
   if (!phi_vv(L, v, H2)) return false;
@@ -238,27 +258,29 @@ bool newton_matrix(const Law& L, const double y[5], const double yn[5], double h
 }
 
 // Dense Cholesky solve of A x = b (A symmetric positive definite, n <= 6).
-bool chol_solve(int n, const double* A, const double* b, double* x) {
-  double Lm[36];
+template <class RA, class R>
+bool chol_solve(int n, const RA* A, const R* b, R* x) {
+  RA Lm[36];
+  using std::sqrt;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j <= i; ++j) {
-      double s = A[i * n + j];
+      RA s = A[i * n + j];
       for (int k = 0; k < j; ++k) s -= Lm[i * n + k] * Lm[j * n + k];
       if (i == j) {
         if (!(s > 0.0)) return false;
-        Lm[i * n + i] = std::sqrt(s);
+        Lm[i * n + i] = sqrt(s);
       } else {
         Lm[i * n + j] = s / Lm[j * n + j];
       }
     }
-  double t[6];
+  R t[6];
   for (int i = 0; i < n; ++i) {
-    double s = b[i];
+    R s = b[i];
     for (int k = 0; k < i; ++k) s -= Lm[i * n + k] * t[k];
     t[i] = s / Lm[i * n + i];
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = t[i];
+    R s = t[i];
     for (int k = i + 1; k < n; ++k) s -= Lm[k * n + i] * x[k];
     x[i] = s / Lm[i * n + i];
   }
@@ -269,6 +291,23 @@ double maxabs(int n, const double* a) {
   double m = 0.0;
   for (int i = 0; i < n; ++i) m = std::fmax(m, std::fabs(a[i]));
   return m;
+}
+
+// Line-search function of step 3 of the update below: g(theta) = d . R(y_n +
+// theta d) and its derivative g'(theta) = d^T K d.
+template <class R>
+R line_g(const Law& L, const R eps[6], const R yn[5], const R d[5], double h, R th, R* gp) {
+  R yt[5], Rv[5], K[5][5];
+  for (int a = 0; a < 5; ++a) yt[a] = yn[a] + th * d[a];
+  residual(L, eps, yt, yn, h, Rv);
+  newton_matrix(L, yt, yn, h, K);
+  R g = 0.0, q = 0.0;
+  for (int a = 0; a < 5; ++a) {
+    g += d[a] * Rv[a];
+    for (int b = 0; b < 5; ++b) q += d[a] * K[a][b] * d[b];
+  }
+  *gp = q;
+  return g;
 }
 
 // Per-voxel diagnostics: line-search iterations, Newton iterations, flags.
@@ -306,19 +345,7 @@ void update_vp(const Law& L, const double eps[6], const double zn[6], double h, 
     for (int a = 0; a < 5; ++a) mr0[a] = -r0[a];
     if (!chol_solve(5, &H[0][0], mr0, d)) info->flags |= F_NOT_SPD;
 
-    auto g_of = [&](double th, double* gp) {
-      double yt[5], R[5], K[5][5];
-      for (int a = 0; a < 5; ++a) yt[a] = yn[a] + th * d[a];
-      residual(L, eps, yt, yn, h, R);
-      newton_matrix(L, yt, yn, h, K);
-      double g = 0.0, q = 0.0;
-      for (int a = 0; a < 5; ++a) {
-        g += d[a] * R[a];
-        for (int b = 0; b < 5; ++b) q += d[a] * K[a][b] * d[b];
-      }
-      *gp = q;
-      return g;
-    };
+    auto g_of = [&](double th, double* gp) { return line_g(L, eps, yn, d, h, th, gp); };
     double lo = 0.0, hi = 1.0, th = 1.0;
     for (int it = 0; it < 400; ++it) {
       ++info->line_iters;
@@ -1293,6 +1320,76 @@ void update_ode23s(const Law& L, const double epsn[6], const double eps1[6], con
   if (alpha_out) *alpha_out = NY == 6 ? y[NY - 1] : 0.0;
 }
 
+// ------------------------------------------------------ algorithmic flops
+// A scalar that counts the arithmetic of the statements above when they run
+// once on it (the algorithmic work of the method per step of the update; the
+// benchmark multiplies it by the iteration counts a GPU run reports).
+//   * Inputs of a voxel (eps, z_n, theta, ...) are "active"; law constants and
+//     the constant matrices P, G, C are "passive" and cost nothing: an
+//     implementation computes their products once per law.
+//   * An operation with a passive 0 (x + 0, x * 0) or a passive +-1 factor or
+//     divisor (P's entries) is structure, not work, and is not counted; nor is
+//     a negation, a comparison or |x|.
+//   * Every other add, sub, mul, div and sqrt counts as one flop; an FMA of a
+//     hardware implementation is two.  pow(x, c) counts as one power (an
+//     implementation spends tens of operations on it; reported apart).
+struct FlopTally {
+  int64_t add, mul, div, sqrt, pow;
+};
+FlopTally g_tally;  // ora_flop_pieces runs single-threaded
+
+struct Counted {
+  double v;
+  bool active;
+  Counted(double x = 0.0) : v(x), active(false) {}
+  static Counted var(double x) {
+    Counted c(x);
+    c.active = true;
+    return c;
+  }
+};
+inline bool is_pm1(const Counted& a) { return !a.active && (a.v == 1.0 || a.v == -1.0); }
+inline bool is_zero(const Counted& a) { return !a.active && a.v == 0.0; }
+inline Counted act(double x) { return Counted::var(x); }
+inline Counted operator-(const Counted& a) { Counted r(-a.v); r.active = a.active; return r; }
+inline Counted operator+(const Counted& a, const Counted& b) {
+  if (!a.active && !b.active) return Counted(a.v + b.v);
+  if (is_zero(a)) return b;
+  if (is_zero(b)) return a;
+  ++g_tally.add;
+  return act(a.v + b.v);
+}
+inline Counted operator-(const Counted& a, const Counted& b) { return a + (-b); }
+inline Counted operator*(const Counted& a, const Counted& b) {
+  if (!a.active && !b.active) return Counted(a.v * b.v);
+  if (is_zero(a) || is_zero(b)) return Counted(0.0);
+  if (is_pm1(a)) return a.v > 0 ? b : -b;
+  if (is_pm1(b)) return b.v > 0 ? a : -a;
+  ++g_tally.mul;
+  return act(a.v * b.v);
+}
+inline Counted operator/(const Counted& a, const Counted& b) {
+  if (!a.active && !b.active) return Counted(a.v / b.v);
+  if (is_zero(a)) return Counted(0.0);
+  if (is_pm1(b)) return b.v > 0 ? a : -a;
+  ++g_tally.div;
+  return act(a.v / b.v);
+}
+inline Counted& operator+=(Counted& a, const Counted& b) { return a = a + b; }
+inline Counted& operator-=(Counted& a, const Counted& b) { return a = a - b; }
+inline bool operator==(const Counted& a, double b) { return a.v == b; }
+inline bool operator>(const Counted& a, double b) { return a.v > b; }
+inline Counted sqrt(const Counted& a) {
+  if (!a.active) return Counted(std::sqrt(a.v));
+  ++g_tally.sqrt;
+  return act(std::sqrt(a.v));
+}
+inline Counted pow(const Counted& a, double e) {
+  if (!a.active) return Counted(std::pow(a.v, e));
+  ++g_tally.pow;
+  return act(std::pow(a.v, e));
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -1337,6 +1434,155 @@ int ora_radial_return(const double* params, int64_t n, const double* eps, const 
   make_law(1, params, &L);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) radial_return(L, eps + 6 * i, zn + 6 * i, h, sigma + 6 * i, z + 6 * i);
+  return 0;
+}
+
+// Algorithmic flops of the pieces of the implicit-Euler update (Sec. 4.1) of
+// the Norton law, counted by running the oracle's own statements once on the
+// Counted scalar at a flowing state: voxel inputs eps, z_n [6], the converged
+// y [5] (y != y_n) and h.  out[7][5]: per piece (add, mul, div, sqrt, pow):
+//   0 predictor  psi_y(eps, y_n) and d = -psi_yy^{-1} psi_y (psi_yy and its
+//                factor are law constants: only the substitutions count);
+//   1 line       one step of the 1-D search on y_n + theta d: g, g' and the
+//                Newton update of theta (a division and a subtraction);
+//   2 newton     one Newton step: R, K, the 5x5 Cholesky factor and solve, y += dy;
+//   3 residual   R = psi_y + phi_v alone (the residual sweep of a correction);
+//   4 subst      forward and back substitution with a given Cholesky factor;
+//   5 stress     z = P y and sigma = C (eps - P y);
+//   6 tangent    C_t = C - C P K^{-1} P^T C at y (Eq. tangent_formula).
+// Returns 0, or -1 if the state does not flow (s = 0).
+int ora_flop_pieces(const double* params, const double* eps, const double* zn, const double* y, double h,
+                    int64_t* out) {
+  Law L;
+  make_law(1, params, &L);
+  Counted E[6], Yn[5], Y[5];
+  for (int i = 0; i < 6; ++i) E[i] = Counted::var(eps[i]);
+  const double yn5[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
+  for (int a = 0; a < 5; ++a) {
+    Yn[a] = Counted::var(yn5[a]);
+    Y[a] = Counted::var(y[a]);
+  }
+  bool flows = false;
+  for (int a = 0; a < 5; ++a) flows = flows || y[a] != yn5[a];
+  if (!flows) return -1;
+  auto take = [&](int piece) {
+    out[5 * piece + 0] = g_tally.add;
+    out[5 * piece + 1] = g_tally.mul;
+    out[5 * piece + 2] = g_tally.div;
+    out[5 * piece + 3] = g_tally.sqrt;
+    out[5 * piece + 4] = g_tally.pow;
+    g_tally = FlopTally{0, 0, 0, 0, 0};
+  };
+  g_tally = FlopTally{0, 0, 0, 0, 0};
+  double H[5][5];
+  psi_yy(L, H);
+  // 0 predictor
+  Counted r0[5], mr0[5], d[5];
+  psi_y(L, E, Yn, r0);
+  for (int a = 0; a < 5; ++a) mr0[a] = -r0[a];
+  chol_solve(5, &H[0][0], mr0, d);
+  take(0);
+  // 1 line: g, g' at theta = 1/2 and the Newton update of theta
+  {
+    Counted gp;
+    const Counted th = Counted::var(0.5);
+    const Counted g = line_g(L, E, Yn, d, h, th, &gp);
+    const Counted tn = th - g / gp;
+    (void)tn;
+  }
+  take(1);
+  // 2 newton
+  {
+    Counted Rv[5], K[5][5], mR[5], dy[5], yy[5];
+    residual(L, E, Y, Yn, h, Rv);
+    newton_matrix(L, Y, Yn, h, K);
+    for (int a = 0; a < 5; ++a) mR[a] = -Rv[a];
+    chol_solve(5, &K[0][0], mR, dy);
+    for (int a = 0; a < 5; ++a) yy[a] = Y[a] + dy[a];
+  }
+  take(2);
+  // 3 residual
+  {
+    Counted Rv[5];
+    residual(L, E, Y, Yn, h, Rv);
+  }
+  take(3);
+  // the Cholesky factor alone: a solve with a zero right-hand side (0 / x and
+  // x * 0 are not counted, so only the factorization remains)
+  auto factor_count = [&](Counted (&K)[5][5]) {
+    const FlopTally keep = g_tally;
+    g_tally = FlopTally{0, 0, 0, 0, 0};
+    Counted zero[5], x[5];
+    chol_solve(5, &K[0][0], zero, x);
+    const FlopTally f = g_tally;
+    g_tally = keep;
+    return f;
+  };
+  auto minus = [](FlopTally a, const FlopTally& b) {
+    a.add -= b.add; a.mul -= b.mul; a.div -= b.div; a.sqrt -= b.sqrt; a.pow -= b.pow;
+    return a;
+  };
+  // 4 substitutions with a given factor
+  {
+    Counted K[5][5], Rv[5], dy[5];
+    newton_matrix(L, Y, Yn, h, K);
+    residual(L, E, Y, Yn, h, Rv);
+    const FlopTally fac = factor_count(K);
+    g_tally = FlopTally{0, 0, 0, 0, 0};
+    chol_solve(5, &K[0][0], Rv, dy);
+    g_tally = minus(g_tally, fac);
+  }
+  take(4);
+  // 5 stress and z
+  {
+    Counted z[6], sig[6];
+    for (int i = 0; i < 6; ++i) {
+      Counted t = 0.0;
+      for (int a = 0; a < 5; ++a) t += P[i][a] * Y[a];
+      z[i] = t;
+    }
+    stress(L, E, Y, sig);
+  }
+  take(5);
+  // 6 tangent: K, one factor of K, then per column j of P^T C the solve
+  // K dy/deps_j = (P^T C)_j and C_t(:, j) = C(:, j) - (C P) dy/deps_j
+  // (update_vp's tangent block, with the factor counted once)
+  {
+    Counted K[5][5], Ct[6][6];
+    newton_matrix(L, Y, Yn, h, K);
+    const FlopTally fac = factor_count(K);
+    const FlopTally before = g_tally;
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) Ct[i][j] = L.C[i][j];
+    double PtC[5][6];
+    for (int a = 0; a < 5; ++a)
+      for (int j = 0; j < 6; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < 6; ++i) t += P[i][a] * L.C[i][j];
+        PtC[a][j] = t;
+      }
+    FlopTally solves{0, 0, 0, 0, 0};
+    for (int j = 0; j < 6; ++j) {
+      Counted col[5], x[5];
+      for (int a = 0; a < 5; ++a) col[a] = PtC[a][j];
+      const FlopTally t0 = g_tally;
+      chol_solve(5, &K[0][0], col, x);
+      const FlopTally one = minus(minus(g_tally, t0), fac);  // substitutions of this column
+      g_tally = t0;
+      solves.add += one.add; solves.mul += one.mul; solves.div += one.div;
+      for (int i = 0; i < 6; ++i) {
+        Counted t = 0.0;
+        for (int a = 0; a < 5; ++a) t += PtC[a][i] * x[a];
+        Ct[i][j] -= t;
+      }
+    }
+    g_tally.add += fac.add + solves.add;
+    g_tally.mul += fac.mul + solves.mul;
+    g_tally.div += fac.div + solves.div;
+    g_tally.sqrt += fac.sqrt;
+    (void)before;
+  }
+  take(6);
   return 0;
 }
 

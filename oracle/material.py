@@ -71,6 +71,8 @@ def _load():
         lib.ora_psi_force_aaa.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
         lib.ora_psi_force_ms.restype = ctypes.c_double
         lib.ora_gen_stress_ms.argtypes = [_dp, _dp, _dp, _dp]
+        lib.ora_flop_pieces.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+        lib.ora_flop_pieces.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -294,3 +296,21 @@ def psi_force_aaa(params, A, u, v, kind=KIND_NORTON):
     lib.ora_psi_force_aaa(int(kind), _ptr(prm), _ptr(_f64(A).reshape(k)), _ptr(_f64(u).reshape(k)),
                           _ptr(_f64(v).reshape(k)), _ptr(out))
     return out
+
+
+FLOP_PIECES = ("predictor", "line", "newton", "residual", "subst", "stress", "tangent")
+FLOP_KINDS = ("add", "mul", "div", "sqrt", "pow")
+
+
+def flop_pieces(params, eps, z_n, y, h):
+    """Algorithmic flops of the pieces of the implicit-Euler update (Sec. 4.1)
+    of the Norton law, counted on the oracle's own statements at a flowing
+    state (``y`` the converged 5 unknowns, y != y_n).  Returns
+    {piece: {kind: count}} for the pieces of ``FLOP_PIECES`` and the kinds
+    of ``FLOP_KINDS`` (add/sub, mul, div, sqrt: one flop each; pow apart)."""
+    out = np.zeros((len(FLOP_PIECES), len(FLOP_KINDS)), dtype=np.int64)
+    rc = _load().ora_flop_pieces(_ptr(_params(params)), _ptr(_f64(eps)), _ptr(_f64(z_n)), _ptr(_f64(y)), float(h),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc != 0:
+        raise ValueError("flop_pieces needs a flowing state (y != y_n)")
+    return {p: dict(zip(FLOP_KINDS, map(int, row))) for p, row in zip(FLOP_PIECES, out)}

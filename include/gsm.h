@@ -194,6 +194,18 @@ const char* gsm_strerror(int code);
  * calling process (all entry points, all devices); for instrumentation. */
 int64_t gsm_kernel_launches(void);
 
+/* gsm_peak_probe -- SIMT FMA-throughput probe, for the rooflines of the
+ * material kernels (the paper has no counterpart: it measures no roofline).
+ * Launches one kernel on `stream` (asynchronous): blocks_per_sm x (SM count)
+ * blocks of 512 threads, each thread running 8 independent dependent chains
+ * x <- fma(x, a, b) for `iters` steps in FP64 (precision 0) or FP32 (1).
+ * The caller times the launch on `stream`; the FLOP rate is
+ * 2 * (*fmas_out) / time.  Allocates nothing; *fmas_out (host) receives the
+ * number of FMAs the launch performs.  Errors: GSM_EINVAL (precision not 0
+ * or 1, iters outside [1, 2^32], blocks_per_sm outside [1, 64], fmas_out
+ * NULL), GSM_ECUDA. */
+int gsm_peak_probe(int precision, int64_t iters, int blocks_per_sm, double* fmas_out, void* stream);
+
 /* ================================================ Moulinec-Suquet basic scheme
  *
  * Periodic unit cell discretised by N^3 voxels; voxel (i, j, k) with k the
@@ -347,14 +359,20 @@ int ms_tape_destroy(ms_tape_handle tape);
 
 /* ===================================================== serving (batched jobs)
  *
- * A server keeps many basic-scheme jobs resident on one GPU and advances all
+ * A server keeps many basic-scheme jobs resident on one GPU and advances the
  * active jobs by one iteration per serve_tick: one material launch, one
- * Green-operator launch and one reduction launch cover every active job (per-
- * job cuFFT calls in between), then one device-to-host copy of all jobs'
+ * Green-operator launch and one reduction launch cover every job of the tick
+ * (per-job cuFFT calls in between), then one device-to-host copy of their
  * errors.  Jobs that arrive while others run are admitted first come first
  * served at the next tick when a slot (max_active) and the HBM budget allow;
- * finished jobs release their memory at once.  A job's arithmetic does not
- * depend on the other jobs: its results are bit-identical alone or in a mix.
+ * finished jobs release their memory at once.  Which active jobs a tick takes
+ * is fair share: each job carries the GPU work it has received (N^3 per FP32
+ * iteration, 8 N^3 per FP64 one) and a tick takes the jobs within one
+ * largest-job iteration of the least-served one, so a small grid runs many
+ * iterations while a large one runs one; an admitted job starts at the
+ * least-served active job's count.  A job's arithmetic does not depend on
+ * the other jobs or on the schedule: its results are bit-identical alone or
+ * in a mix.
  * (The paper has no serving layer; this is the continuous-batching engine
  * around its material law and basic scheme.)
  */
@@ -395,8 +413,8 @@ int serve_destroy(serve_handle h);
  * ms_run refuses. */
 int serve_submit(serve_handle h, const serve_job* job, int64_t* id);
 
-/* serve_tick -- admit queued jobs, run one iteration of every active job,
- * retire finished ones.  Synchronous (one device-to-host copy per tick).
+/* serve_tick -- admit queued jobs, run one iteration of the active jobs the
+ * fair-share rule selects (at least one), retire finished ones.  Synchronous (one device-to-host copy per tick).
  * Outputs (may be NULL): active, queued and finished-but-unfetched counts. */
 int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_finished);
 
@@ -429,10 +447,14 @@ size_t serve_job_bytes(int N, int precision);
  *   z        device [6][N^3] internal variables at t_{n+1}; 0 in elastic phases (out)
  *   mean     device [6] FP64 mean of sigma                              (out)
  * Same kernel and reduction as the material step of ms_run.  Its scratch is
- * a file-scope device array of 6*1024+8 doubles that every GPU loading the
- * library holds until exit; all calls share it, so calls whose work overlaps
- * on the GPU race.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress): make that first call before any stream
+ * a file-scope device array of 6*1024+8 doubles (the per-block partial sums
+ * and the reduced result) that every GPU loading the library holds until
+ * exit, so the material launch always uses at most 1024 blocks, which loop
+ * over the voxels; the N <= 1024 bound is the input limit of every grid
+ * entry point, not a consequence of that cap.  All calls share the array, so
+ * calls whose work overlaps on the GPU race.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and the
+ * kernel's occupancy, under a lock: make that first call before any stream
  * capture.  Asynchronous on `stream`.  Errors: GSM_EINVAL, GSM_ECUDA.
  */
 int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, const gsm_handle* laws, double step_h,

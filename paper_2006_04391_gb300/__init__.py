@@ -33,7 +33,7 @@ EXPORTS = ("gsm_create", "gsm_destroy", "gsm_update", "gsm_strerror", "gsm_kerne
            "ms_create", "ms_destroy", "ms_workspace_bytes", "ms_run", "ms_solve", "ms_evaluate_noalloc",
            "serve_create", "serve_destroy", "serve_submit", "serve_tick", "serve_job_state", "serve_fetch",
            "serve_job_bytes", "ms_run_taped", "ms_adjoint", "ms_tape_destroy", "gsm_update_ode23",
-           "gsm_update_ode", "gsm_update_host")
+           "gsm_update_ode", "gsm_update_host", "gsm_peak_probe")
 
 _lib = None
 
@@ -101,6 +101,7 @@ def load(path=None):
     lib.gsm_strerror.restype = ctypes.c_char_p
     lib.gsm_strerror.argtypes = [ctypes.c_int]
     lib.gsm_kernel_launches.restype = i64
+    lib.gsm_peak_probe.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.POINTER(dbl), vp]
     if hasattr(lib, "ms_evaluate_noalloc"):
         lib.ms_evaluate_noalloc.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp), dbl, vp, vp, vp, vp,
                                             vp, vp]
@@ -154,6 +155,15 @@ def _stream_ptr(stream):
 
 def kernel_launches():
     return int(load().gsm_kernel_launches())
+
+
+def peak_probe(precision, iters, blocks_per_sm=4, stream=None):
+    """Launch the FMA-throughput probe (``gsm_peak_probe``); returns the number
+    of FMAs the launch performs.  The caller times it on ``stream``."""
+    f = ctypes.c_double()
+    _check(load().gsm_peak_probe(int(precision), int(iters), int(blocks_per_sm), ctypes.byref(f),
+                                 _stream_ptr(stream)), "gsm_peak_probe")
+    return f.value
 
 
 # ------------------------------------------------------------------ materials

@@ -55,6 +55,17 @@ def test_create_validates_parameters(lib):
         G.gsm_create(G.GSM_PSI_ELASTIC, G.GSM_PHI_NONE, (1.0, 0.2), 7)
 
 
+def test_peak_probe_validates_arguments(lib):
+    """The FMA-throughput probe refuses bad arguments before any CUDA call."""
+    f = ctypes.c_double()
+    lib.gsm_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.c_void_p]
+    for prec, iters, bps, out in [(2, 10, 1, ctypes.byref(f)), (0, 0, 1, ctypes.byref(f)),
+                                  (1, 1 << 33, 1, ctypes.byref(f)), (0, 10, 0, ctypes.byref(f)),
+                                  (0, 10, 65, ctypes.byref(f)), (0, 10, 1, None)]:
+        assert lib.gsm_peak_probe(prec, iters, bps, out, None) == -1
+
+
 def test_update_entries_validate_before_any_device_work(lib):
     """Argument checks of the update entry points that return before any CUDA
     call: no handle, negative sizes, an unknown integrator, a negative chunk,

@@ -334,7 +334,9 @@ int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_re
  * checkpoints (the paper's AD is local to a voxel, Sec. 4.1/5; this is its
  * continuation to the homogenization run).  Backward over the steps, each
  * step solves the adjoint equilibrium P_V(C_t lam) = P_V(a_u) by the
- * basic-scheme fixed point with the consistent tangent field C_t.
+ * basic-scheme fixed point with the consistent tangent field C_t, on the
+ * isotropic reference medium at the midpoints of that field's bulk and shear
+ * measures (as the forward run's per-step reference).
  */
 typedef struct ms_tape* ms_tape_handle;
 
@@ -342,9 +344,10 @@ typedef struct ms_tape* ms_tape_handle;
  * checkpoints (eps_k, z_{k-1}) of every step on the device (2 * 6 * N^3
  * doubles per step) plus adjoint work arrays (53 * N^3 doubles).  The tape
  * refers to the context, which must outlive it.  Prescribed macroscopic
- * strains, the fixed reference medium and the implicit-Euler update only
- * (stress_mask = 0, ref_update = 0, integrator = 0; GSM_ENOTSUP otherwise).
- * Errors as ms_run. */
+ * strains and the implicit-Euler update only (stress_mask = 0, integrator =
+ * 0; GSM_ENOTSUP otherwise); the reference medium may be fixed or per step
+ * (ref_update), which changes the iteration counts, not the converged states
+ * the adjoint linearises.  Errors as ms_run. */
 int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_handle* tape);
 
 /* ms_adjoint -- dJ/d(E, sigma0, n) of the Norton phase `phase_id` for the

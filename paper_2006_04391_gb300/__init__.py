@@ -390,10 +390,11 @@ class Tape:
             self.handle = None
 
 
-def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000, forced_iters=None):
-    """Load history from a fresh state keeping per-step checkpoints; returns (result, Tape)."""
+def ms_run_taped(ctx, E, hs, tol=1e-10, max_iter=20000, forced_iters=None, ref_update=False):
+    """Load history from a fresh state keeping per-step checkpoints; returns (result, Tape).
+    ref_update: the forward run's per-step reference medium from tangents."""
     lib = load()
-    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, 0.0)
+    ld, keep, n = _load_struct(E, hs, tol, max_iter, forced_iters, 0.0, ref_update=ref_update)
     res, out = _result_struct(n)
     th = ctypes.c_void_p()
     rc = lib.ms_run_taped(ctx.handle, ctypes.byref(ld), ctypes.byref(res), ctypes.byref(th))

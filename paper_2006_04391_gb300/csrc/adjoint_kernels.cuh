@@ -157,6 +157,47 @@ __global__ void __launch_bounds__(kAdjBlock) adj_prepare_kernel(int64_t nvox, co
 }
 
 // tau = C_t lam - a_u, lam = lam_raw / N^3 (C2R output).
+// Reference medium of a step's adjoint equilibrium from its tangent field
+// (as the forward per-step reference, Sec. 3): per voxel the isotropic
+// measures 3k = (1/3) sum_{i,j<3} C_ij and 10 mu = tr_Mandel C - 3k of C_t,
+// per block their min and max -> part[q * gridDim.x + block], q = kmin,
+// kmax, mumin, mumax.  Launch with kAdjBlock threads.
+__global__ void __launch_bounds__(kAdjBlock) adj_reference_kernel(int64_t nvox, const double* __restrict__ Ct21,
+                                                                  double* __restrict__ part) {
+  double r[4] = {1e300, -1e300, 1e300, -1e300};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    // packed upper triangle: C11 0, C12 1, C13 2, C22 6, C23 7, C33 11, C44 15, C55 18, C66 20
+    const double d0 = Ct21[i], d1 = Ct21[6 * nvox + i], d2 = Ct21[11 * nvox + i];
+    const double tk = (d0 + d1 + d2 + 2.0 * (Ct21[nvox + i] + Ct21[2 * nvox + i] + Ct21[7 * nvox + i])) * (1.0 / 3.0);
+    const double tr = d0 + d1 + d2 + 2.0 * (Ct21[15 * nvox + i] + Ct21[18 * nvox + i] + Ct21[20 * nvox + i]);
+    const double k = tk * (1.0 / 3.0), mu = (tr - tk) * 0.1;
+    r[0] = fmin(r[0], k);
+    r[1] = fmax(r[1], k);
+    r[2] = fmin(r[2], mu);
+    r[3] = fmax(r[3], mu);
+  }
+  __shared__ double sh[4][kAdjBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = r[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, v, off);
+      v = (q & 1) ? fmax(v, o) : fmin(v, o);
+    }
+    if (lane == 0) sh[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    double v = sh[q][0];
+    for (int k = 1; k < kAdjBlock / 32; ++k) v = (q & 1) ? fmax(v, sh[q][k]) : fmin(v, sh[q][k]);
+    part[q * gridDim.x + blockIdx.x] = v;
+  }
+}
+
 __global__ void adj_tau_kernel(int64_t nvox, const double* __restrict__ Ct21, const double* __restrict__ a_u,
                                const double* __restrict__ lam_raw, double inv_n3, double* __restrict__ tau) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -65,7 +65,8 @@ struct JobView {
   int64_t nvox, nmodes;
   int64_t vchunk0, mchunk0;  // first chunk of this job in its launch
   int n_vch, n_mch;
-  int N, pad;
+  int N;
+  int warm;              // 1: z holds this job's previous evaluation of the current step (warm start)
   double h, inv_h, inv_n3, lam0, mu0;
   // ode23 laws (Sec. 4.3): strain at t_n, the Michel-Suquet alpha, tolerances
   const double* eps_prev;  // [6][nvox]
@@ -117,21 +118,26 @@ template <class T, int MODE>
 __device__ __forceinline__ void material_voxel(int64_t i, bool in, int64_t nvox, const uint8_t* __restrict__ phase,
                                                const PhaseTable& tab, const Step& hs, T inv_n3,
                                                const T* __restrict__ eps_raw, const T* __restrict__ zn,
-                                               T* __restrict__ sig, T* __restrict__ z, T (&acc)[6]) {
+                                               T* __restrict__ sig, T* __restrict__ z, T (&acc)[6],
+                                               bool warm = false) {
   const int ph = in ? (int)phase[i] : 0;
   const bool vp = in && tab.kind[ph] == GSM_PSI_ELASTIC_VP_DEV;
-  T e[6], zi[6], s[6], zo[6];
+  T e[6], zi[6], s[6], zo[6], zp[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     e[c] = in ? __ldg(eps_raw + c * nvox + i) * inv_n3 : T(0);
     zi[c] = vp ? __ldg(zn + c * nvox + i) : T(0);
+    // warm start: this voxel's z from the previous evaluation of the step
+    // (read before this evaluation overwrites it)
+    zp[c] = (warm && vp) ? z[c * nvox + i] : zi[c];
   }
+  const T* zprev = warm ? zp : nullptr;
   if constexpr (MODE == MODE_FP64) {
-    voxel_fp64<NortonDev>(tab.p64[ph], e, zi, hs, vp, s, zo, nullptr);
+    voxel_fp64<NortonDev>(tab.p64[ph], e, zi, hs, vp, s, zo, nullptr, zprev);
   } else if constexpr (MODE == MODE_FP32_FIX) {
-    voxel_fp32_fix<NortonDev>(tab.p64[ph], tab.p32[ph], e, zi, hs, vp, s, zo, nullptr);
+    voxel_fp32_fix<NortonDev>(tab.p64[ph], tab.p32[ph], e, zi, hs, vp, s, zo, nullptr, zprev);
   } else {
-    voxel_fp32<NortonDev>(tab.p32[ph], e, zi, hs, vp, s, zo, nullptr);
+    voxel_fp32<NortonDev>(tab.p32[ph], e, zi, hs, vp, s, zo, nullptr, zprev);
   }
   if (in && !vp) {
     if constexpr (sizeof(T) == 8) voxel_elastic<double>(tab.p64[ph], e, s, nullptr);
@@ -214,6 +220,89 @@ __device__ __forceinline__ void gamma_mode(int N, double inv2mu, double coef, ty
   }
 }
 
+// The Green-operator update of one FP32 mode on registers: s = sig_hat, e =
+// eps_hat (in/out, the updated strain spectrum); (a, b, c) its half-spectrum
+// index.  Same arithmetic as gamma_mode.
+__device__ __forceinline__ void gamma_mode_f32_regs(int N, int a, int b, int c, float inv2mu, float coef,
+                                                    const float2 (&s)[6], float2 (&e)[6], double& res) {
+  const int Nh = N / 2 + 1;
+  (void)Nh;
+  const bool even = (N % 2) == 0;
+  const int kx = freq(a, N), ky = freq(b, N), kz = c;
+  const int nz = (kx != 0) + (ky != 0) + (kz != 0);
+  const bool nyq = even && (a == N / 2 || b == N / 2 || c == N / 2);
+  if (nz == 0 || (nyq && nz >= 2)) return;  // Gamma0 = 0: eps_hat unchanged
+  const float k1 = (float)kx, k2 = (float)ky, k3 = (float)kz;
+  float qr[3], qi[3];
+  qr[0] = s[0].x * k1 + s[5].x * k2 + s[4].x * k3;
+  qi[0] = s[0].y * k1 + s[5].y * k2 + s[4].y * k3;
+  qr[1] = s[5].x * k1 + s[1].x * k2 + s[3].x * k3;
+  qi[1] = s[5].y * k1 + s[1].y * k2 + s[3].y * k3;
+  qr[2] = s[4].x * k1 + s[3].x * k2 + s[2].x * k3;
+  qi[2] = s[4].y * k1 + s[3].y * k2 + s[2].y * k3;
+  const double w = (c == 0 || (even && c == N / 2)) ? 1.0 : 2.0;
+  res += w * ((double)(qr[0] * qr[0] + qi[0] * qi[0]) + (double)(qr[1] * qr[1] + qi[1] * qi[1]) +
+              (double)(qr[2] * qr[2] + qi[2] * qi[2]));
+  const float kk = k1 * k1 + k2 * k2 + k3 * k3;
+  const float ik2 = 1.0f / kk;
+  const float a1 = inv2mu * ik2;
+  const float a2 = coef * ik2 * ik2;
+  const float kqr = k1 * qr[0] + k2 * qr[1] + k3 * qr[2];
+  const float kqi = k1 * qi[0] + k2 * qi[1] + k3 * qi[2];
+  const float kv[3] = {k1, k2, k3};
+  const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int i = ii[q], j = jj[q];
+    const float f = q < 3 ? 1.0f : 2.0f;
+    e[q].x -= f * (a1 * (kv[j] * qr[i] + kv[i] * qr[j]) - a2 * kqr * kv[i] * kv[j]);
+    e[q].y -= f * (a1 * (kv[j] * qi[i] + kv[i] * qi[j]) - a2 * kqi * kv[i] * kv[j]);
+  }
+}
+
+// Two consecutive FP32 modes m0 (even) and m0 + 1 with 16-byte loads and
+// stores (nmodes even, so every component's base is 16-byte aligned); the
+// index (a, b, c) of m0 by 32-bit division (nmodes < 2^31), that of m0 + 1 by
+// a carry.
+__device__ __forceinline__ void gamma_pair_f32(int N, float inv2mu, float coef, float4* __restrict__ sig_hat,
+                                               float4* __restrict__ eps_hat, int64_t nmodes, unsigned m0,
+                                               double& res) {
+  const unsigned Nh = (unsigned)(N / 2 + 1);
+  const size_t st = (size_t)nmodes / 2, p = m0 / 2;
+  float4 S[6], E[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[q] = sig_hat[q * st + p];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) E[q] = eps_hat[q * st + p];
+  const unsigned ab = m0 / Nh;
+  int c = (int)(m0 - ab * Nh);
+  int a = (int)(ab / (unsigned)N);
+  int b = (int)(ab - (unsigned)a * (unsigned)N);
+  float2 s0[6], e0[6], s1[6], e1[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    s0[q] = make_float2(S[q].x, S[q].y);
+    s1[q] = make_float2(S[q].z, S[q].w);
+    e0[q] = make_float2(E[q].x, E[q].y);
+    e1[q] = make_float2(E[q].z, E[q].w);
+  }
+  gamma_mode_f32_regs(N, a, b, c, inv2mu, coef, s0, e0, res);
+  if (++c == (int)Nh) {
+    c = 0;
+    if (++b == N) {
+      b = 0;
+      ++a;
+    }
+  }
+  gamma_mode_f32_regs(N, a, b, c, inv2mu, coef, s1, e1, res);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float4 o = make_float4(e0[q].x, e0[q].y, e1[q].x, e1[q].y);
+    eps_hat[q * st + p] = o;
+    sig_hat[q * st + p] = o;
+  }
+}
+
 // ------------------------------------------------------------------ kernels
 
 // Single-problem material evaluation (grid-stride over voxels; one partial
@@ -263,7 +352,7 @@ __global__ void __launch_bounds__(kMatBlock) ms_material_batch_kernel(const JobV
       const int64_t i = lc * kVChunk + sweep * kMatBlock + threadIdx.x;
       material_voxel<T, MODE>(i, i < v.nvox, v.nvox, v.phase, *v.tab, hs, (T)v.inv_n3,
                               static_cast<const T*>(v.eps_raw), static_cast<const T*>(v.zn),
-                              static_cast<T*>(v.sig), static_cast<T*>(v.z), acc);
+                              static_cast<T*>(v.sig), static_cast<T*>(v.z), acc, v.warm != 0);
     }
     double accd[6];
 #pragma unroll
@@ -285,12 +374,23 @@ __global__ void __launch_bounds__(kGamBlock) ms_gamma_batch_kernel(const JobView
     const double inv2mu = 1.0 / (2.0 * v.mu0);
     const double coef = (v.lam0 + v.mu0) / (v.mu0 * (v.lam0 + 2.0 * v.mu0));
     double res[1] = {0.0};
+    if (sizeof(T) == 4 && v.nmodes % 2 == 0) {
+      // FP32 fields: pairs of modes per thread, 16-byte accesses
 #pragma unroll 1
-    for (int sweep = 0; sweep < kMChunk / kGamBlock; ++sweep) {
-      const int64_t m = lc * kMChunk + sweep * kGamBlock + threadIdx.x;
-      if (m < v.nmodes)
-        gamma_mode<T>(v.N, inv2mu, coef, static_cast<typename cplx<T>::type*>(v.sig_hat),
-                      static_cast<typename cplx<T>::type*>(v.eps_hat), v.nmodes, m, res[0]);
+      for (int sweep = 0; sweep < kMChunk / (2 * kGamBlock); ++sweep) {
+        const int64_t m = lc * kMChunk + sweep * 2 * kGamBlock + 2 * threadIdx.x;
+        if (m < v.nmodes)
+          gamma_pair_f32(v.N, (float)inv2mu, (float)coef, static_cast<float4*>(v.sig_hat),
+                         static_cast<float4*>(v.eps_hat), v.nmodes, (unsigned)m, res[0]);
+      }
+    } else {
+#pragma unroll 1
+      for (int sweep = 0; sweep < kMChunk / kGamBlock; ++sweep) {
+        const int64_t m = lc * kMChunk + sweep * kGamBlock + threadIdx.x;
+        if (m < v.nmodes)
+          gamma_mode<T>(v.N, inv2mu, coef, static_cast<typename cplx<T>::type*>(v.sig_hat),
+                        static_cast<typename cplx<T>::type*>(v.eps_hat), v.nmodes, m, res[0]);
+      }
     }
     block_sum_at<1>(res, v.gam_part, v.n_mch, lc);
   }

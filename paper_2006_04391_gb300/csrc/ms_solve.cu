@@ -212,6 +212,7 @@ struct Job {
   // state
   int step = 0, n_eval = 0, n32 = 0, since_best = 0;
   bool fp32_phase = false, need_start = true, done = false, notconv = false;
+  bool warm = false;  // z holds the previous evaluation of this step, in the current field precision
   double best = 1e300;
   double E_prev[6] = {0, 0, 0, 0, 0, 0};  // macroscopic strain at the end of the previous step
   double E_cur[6] = {0, 0, 0, 0, 0, 0};   // macroscopic strain of the current iterate
@@ -219,6 +220,7 @@ struct Job {
   std::vector<double> Sigma, final_error, E_out, ref_out;
   std::vector<int32_t> iters, fp32_iters;
   int64_t total_iters = 0;
+  double vt = 0.0;  // serving: virtual time, the GPU work this job has received (voxel-iteration units)
   // optional per-step checkpoints for the adjoint: [n_steps][6][nvox] each
   double* tape_eps = nullptr;   // converged strain eps_k
   double* tape_zprev = nullptr; // internal variables z_{k-1} entering step k
@@ -527,6 +529,7 @@ int step_start(Engine& g, Job& j) {
     if (rc != GSM_OK) return rc;
   }
   mixed_setup(j);
+  j.warm = false;
   j.n_eval = 0;
   j.n32 = 0;
   j.best = 1e300;
@@ -560,6 +563,7 @@ template <class T> void move_mean(Engine& g, Job& j, const double (&dS)[6]) {
 // evaluation becomes the FP64 strain, resynthesised from its spectrum so that
 // its mean is E_k exactly.
 int switch_to_fp64(Engine& g, Job& j) {
+  j.warm = false;  // the FP64 z is not this step's
   convert<float, double>(g.stream, j.f32.eps_raw, j.f64.eps_raw, 6 * j.nvox, 1.0);
   int rc = spectrum_start<double>(g, j, j.E_cur, j.E_cur);
   if (rc != GSM_OK) return rc;
@@ -572,6 +576,7 @@ int switch_to_fp64(Engine& g, Job& j) {
 // After the tick's evaluation: convergence, precision switch, step end.
 int post_eval(Engine& g, Job& j, const Reduced& r) {
   ++j.n_eval;
+  j.warm = true;  // z now holds this evaluation (step_start and the precision switch clear it)
   double e = r.e;
   double dS[6] = {0, 0, 0, 0, 0, 0};
   if (j.stress_mask) {
@@ -690,7 +695,7 @@ int tick(Engine& g, const std::vector<Job*>& jobs) {
     v.n_vch = j.n_vch;
     v.n_mch = j.n_mch;
     v.N = j.N;
-    v.pad = 0;
+    v.warm = (j.warm && j.integrator == 0) ? 1 : 0;
     v.h = j.h[j.step];
     v.inv_h = 1.0 / v.h;
     v.inv_n3 = 1.0 / (double)j.nvox;
@@ -777,6 +782,10 @@ struct Pending {
   std::unique_ptr<Job> job;
   std::vector<uint8_t> phase;
 };
+
+// GPU work of one iteration of a job, in FP32-voxel units: an FP64 iteration
+// (FP64 fields, FFTs and law) costs several FP32 ones.
+double serve_cost(const Job& j) { return (double)j.nvox * (j.fp32_phase ? 1.0 : 8.0); }
 
 struct Server {
   Engine eng;
@@ -955,7 +964,10 @@ int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_
   if (!h) return GSM_EINVAL;
   Server* sv = reinterpret_cast<Server*>(h);
   Engine& g = sv->eng;
-  // admission: first come first served while a slot and the HBM budget allow
+  // admission: first come first served while a slot and the HBM budget allow;
+  // an admitted job starts at the smallest virtual time of the active jobs
+  double vt_min = 0.0;
+  for (size_t i = 0; i < sv->active.size(); ++i) vt_min = i ? std::min(vt_min, sv->active[i]->vt) : sv->active[i]->vt;
   while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active) {
     Pending& p = sv->queue.front();
     Job& j = *p.job;
@@ -976,13 +988,27 @@ int serve_tick(serve_handle h, int32_t* n_active, int32_t* n_queued, int32_t* n_
     }
     sv->used += extra;
     sv->state[j.id] = 1;
+    j.vt = vt_min;
     sv->active.push_back(std::move(p.job));
     sv->queue.pop_front();
   }
+  // fair share: the tick takes the jobs whose virtual time is within one
+  // iteration of the largest job of the least-served job, so each active job
+  // receives about the same GPU work per unit of time (a small grid runs many
+  // iterations while a large one runs one) instead of one iteration each
   std::vector<Job*> batch;
-  for (auto& j : sv->active) batch.push_back(j.get());
+  if (!sv->active.empty()) {
+    double lo = sv->active[0]->vt, quantum = 0.0;
+    for (auto& j : sv->active) {
+      lo = std::min(lo, j->vt);
+      quantum = std::max(quantum, serve_cost(*j));
+    }
+    for (auto& j : sv->active)
+      if (j->vt <= lo + quantum) batch.push_back(j.get());
+  }
   int rc = tick(g, batch);
   if (rc != GSM_OK) return rc;
+  for (Job* j : batch) j->vt += serve_cost(*j);
   for (size_t i = 0; i < sv->active.size();) {
     if (sv->active[i]->done) {
       std::unique_ptr<Job> j = std::move(sv->active[i]);
@@ -1072,8 +1098,10 @@ int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_ha
   Ctx& c = *reinterpret_cast<Ctx*>(h);
   Job& j = c.job;
   if (load->n_steps < 1) return GSM_EINVAL;
-  // the adjoint assumes prescribed macroscopic strains and the fixed reference medium
-  if (load->stress_mask != 0 || load->ref_update != 0 || load->integrator != 0) return GSM_ENOTSUP;
+  // the adjoint assumes prescribed macroscopic strains and the implicit-Euler
+  // update; the reference medium of the forward run (fixed or per step) does
+  // not enter the converged states the adjoint linearises
+  if (load->stress_mask != 0 || load->integrator != 0) return GSM_ENOTSUP;
   Tape* t = new (std::nothrow) Tape;
   if (!t) return GSM_ENOMEM;
   t->ctx = &c;
@@ -1154,6 +1182,31 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
                                                                          gs[0], gs[1], gs[2], gs[3], gs[4], gs[5],
                                                                          t.gz, t.Ct21, t.a_u, t.yK);
     count_launch();
+    // the step's reference medium for the adjoint equilibrium: midpoints of the
+    // tangent field's isotropic measures
+    double lam0 = j.lam0_el, mu0 = j.mu0_el;
+    {
+      const int rg = std::min(grid_cap(nv, kAdjBlock, 4), 1024);
+      adj_reference_kernel<<<rg, kAdjBlock, 0, s>>>(nv, t.Ct21, t.part);
+      count_launch();
+      std::vector<double> part(4 * (size_t)rg);
+      if (cudaMemcpyAsync(part.data(), t.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return GSM_ECUDA;
+      double r[4] = {1e300, -1e300, 1e300, -1e300};
+      for (int b = 0; b < rg; ++b) {
+        r[0] = std::min(r[0], part[b]);
+        r[1] = std::max(r[1], part[rg + b]);
+        r[2] = std::min(r[2], part[2 * rg + b]);
+        r[3] = std::max(r[3], part[3 * rg + b]);
+      }
+      const double k0 = 0.5 * (r[0] + r[1]), m0 = 0.5 * (r[2] + r[3]);
+      if (m0 > 0.0 && k0 > 0.0 && std::isfinite(k0 + m0)) {
+        mu0 = m0;
+        lam0 = k0 - 2.0 * m0 / 3.0;
+      }
+    }
     // adjoint equilibrium: lam in eps_raw (N^3 lam), lam^ in eps_hat
     cudaMemsetAsync(j.f64.eps_raw, 0, n6 * sizeof(double), s);
     cudaMemsetAsync(j.f64.eps_hat, 0, 6 * j.nmodes * sizeof(cufftDoubleComplex), s);
@@ -1169,8 +1222,8 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
     v.n_mch = j.n_mch;
     v.N = j.N;
     v.inv_n3 = inv_n3;
-    v.lam0 = j.lam0;
-    v.mu0 = j.mu0;
+    v.lam0 = lam0;
+    v.mu0 = mu0;
     cudaMemcpyAsync(g.views_dev, g.views_host, sizeof(JobView), cudaMemcpyHostToDevice, s);
     const int gam_grid = (int)std::min<int64_t>(j.n_mch, (int64_t)sm_count() * g.per_sm_gam[0]);
     double first = -1.0;
@@ -1252,10 +1305,12 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_per_sm[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up on the
-// first call per device).
-int noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device and the material
+// kernel's resident blocks per SM there (both set up on the first call per
+// device, under the mutex).
+int noalloc_scratch(double** out, int* per_sm) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GSM_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return GSM_ENOTSUP;
@@ -1263,9 +1318,16 @@ int noalloc_scratch(double** out) {
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_ms_eval_scratch) != cudaSuccess || !p) return GSM_ECUDA;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_kernel<double, MODE_FP64>, kMatBlock, 0) !=
+            cudaSuccess ||
+        b <= 0)
+      b = 1;
+    g_noalloc_per_sm[dev] = b;
     g_noalloc_ptr[dev] = static_cast<double*>(p);
   }
   *out = g_noalloc_ptr[dev];
+  *per_sm = g_noalloc_per_sm[dev];
   return GSM_OK;
 }
 
@@ -1290,18 +1352,10 @@ extern "C" int ms_evaluate_noalloc(int N, const uint8_t* phase, int n_phases, co
     tab.p32[p] = m->p32;
   }
   double* scratch = nullptr;
-  int rc = noalloc_scratch(&scratch);
+  int per_sm = 1;
+  int rc = noalloc_scratch(&scratch, &per_sm);
   if (rc != GSM_OK) return rc;
   const int64_t nvox = (int64_t)N * N * N;
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_material_kernel<double, MODE_FP64>, kMatBlock, 0) !=
-            cudaSuccess ||
-        b <= 0)
-      b = 1;
-    per_sm = b;
-  }
   const int grid = std::min(grid_cap(nvox, kMatBlock, per_sm), kNoAllocMaxBlocks);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* partials = scratch;                                    // [6][grid]

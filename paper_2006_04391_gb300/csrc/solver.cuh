@@ -490,11 +490,48 @@ template <class T> AD_HD T absmax6(const T (&a)[6]) {
   return m;
 }
 
+// One Newton step on R(w) = psi_y(e_s, w) + phi_v(w/h) = 0: w += dw with
+// K dw = -R; the factor of K stays in `ch`.  Returns dw's largest entry, or
+// -1 if K is not positive definite (w unchanged), +inf if dw is not finite.
+template <class Law, class T>
+AD_HD T newton_step(const LawParams<T>& p, const T (&es)[6], T inv_h, T (&w)[5], Chol5<T>& ch) {
+  T v[5], R[5], K[5][5], gv[5], Hv[5][5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
+  psi_y_yy<Law>(p, es, w, R, K);
+  phi_v_vv<Law>(p, v, gv, Hv);
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    R[a] = -(R[a] + gv[a]);
+#pragma unroll
+    for (int b = 0; b < 5; ++b) K[a][b] += Hv[a][b] * inv_h;
+  }
+  T dw[5];
+  const bool spd = ch.factor(K);
+  ch.solve(R, dw);
+  if (!spd) return T(-1);
+  const T dmax = absmax5(dw);
+  if (!(dmax < T(sizeof(T) == 8 ? 1e300 : 1e37))) return T(INFINITY);
+#pragma unroll
+  for (int a = 0; a < 5; ++a) w[a] += dw[a];
+  return dmax;
+}
+
+constexpr int kWarmIterMax = 4;
+
 // Solve the implicit Euler step in precision T for the increment w, posed
 // on the trial strain e_s (Law::trial_strain): R(w) = psi_y(e_s, w) +
 // phi_v(w / h) = 0.  Returns the Cholesky factor of the last Newton matrix
 // in `ch` (for the tangent or for an FP64 correction).  `active` = false for
 // padding lanes: they take part in the warp votes only.
+//
+// Warm start (w0 != NULL, the basic scheme's later evaluations of a load
+// step): Newton from w0, the previous evaluation's increment of the same
+// voxel, which the scheme's strain update has moved only a little.  A lane
+// whose warm Newton has not converged after kWarmIterMax steps, or meets a
+// non-SPD or non-finite step, or starts from w0 = 0, takes the cold path
+// (predictor, segment minimisation, Newton).  Pi is strictly convex, so both
+// paths reach the same root.
 //
 // Rates below 1e-140 (FP64) or 1e-18 (FP32) of |d| / h, d the predictor,
 // are not resolved (this keeps the dissipation's q = |v|^2 from
@@ -504,13 +541,48 @@ template <class T> AD_HD T absmax6(const T (&a)[6]) {
 // the trial strain.
 template <class Law, class T>
 AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const Step& hs, bool active, T newton_tol,
-                               T (&w)[5], Chol5<T>& ch) {
+                               T (&w)[5], Chol5<T>& ch, const T* w0 = nullptr) {
   T h, inv_h;
   step_of(hs, h, inv_h);
   unsigned st = 0;
   int n_line = 0, n_newton = 0;
+  bool warm = false;
+  if (w0) {
+    T wt[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) w[a] = T(0);
+    for (int a = 0; a < 5; ++a) wt[a] = w0[a];
+    bool wdone = !(active && absmax5(wt) > T(0));
+    for (int it = 0; it < kWarmIterMax; ++it) {
+      if (all_done(wdone)) break;
+      if (!wdone) {
+        ++n_newton;
+        const T dmax = newton_step<Law, T>(p, es, inv_h, wt, ch);
+        if (!(dmax >= T(0) && dmax < T(INFINITY))) {
+          wdone = true;  // not SPD or not finite: the cold path decides
+        } else if (dmax <= newton_tol * fmax_(absmax5(wt), T(sizeof(T) == 8 ? 1e-300 : 1e-30))) {
+          warm = true;
+          wdone = true;
+        }
+      }
+    }
+    if (warm) {
+#pragma unroll
+      for (int a = 0; a < 5; ++a) w[a] = wt[a];
+      st |= ST_CONVERGED;
+    } else {
+      n_newton = 0;
+    }
+  }
+  const bool cold = active && !warm;
+  if (!warm) {
+#pragma unroll
+    for (int a = 0; a < 5; ++a) w[a] = T(0);
+  }
+  if (all_done(!cold)) {  // every lane of the warp converged warm (or pads)
+    if (!active) st |= ST_CONVERGED;
+    st |= (unsigned)(n_newton & 0xff) << ST_NEWTON_SHIFT;
+    return st;
+  }
 
   // 1. predictor at w = 0.  In the trial frame psi_y(e_s, 0) vanishes only
   // for a zero deviatoric trial stress: then there is no flow.
@@ -521,8 +593,8 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
     const T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
     psi_y_yy<Law>(p, es, zero, r0, Hp);
     const T r0max = absmax5(r0);
-    flows = active && r0max > T(0);
-    if (active && !(r0max == r0max)) { st |= ST_NONFINITE; flows = false; }
+    flows = cold && r0max > T(0);
+    if (cold && !(r0max == r0max)) { st |= ST_NONFINITE; flows = false; }
     Chol5<T> hp;
     const bool ok = hp.factor(Hp);
     if (flows && !ok) { st |= ST_NOT_SPD; flows = false; }
@@ -576,31 +648,16 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
     if (all_done(done)) break;
     if (!done) {
       ++n_newton;
-      T v[5], R[5], K[5][5], gv[5], Hv[5][5];
-#pragma unroll
-      for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
-      psi_y_yy<Law>(p, es, w, R, K);
-      phi_v_vv<Law>(p, v, gv, Hv);
-#pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        R[a] = -(R[a] + gv[a]);
-#pragma unroll
-        for (int b = 0; b < 5; ++b) K[a][b] += Hv[a][b] * inv_h;
-      }
-      T dw[5];
-      const bool spd = ch.factor(K);
-      ch.solve(R, dw);
-      const T dmax = absmax5(dw);
-      if (!spd) {
+      const T dmax = newton_step<Law, T>(p, es, inv_h, w, ch);
+      if (dmax < T(0)) {
         st |= ST_NOT_SPD;
         done = true;
-      } else if (!(dmax < T(sizeof(T) == 8 ? 1e300 : 1e37))) {
+      } else if (!(dmax < T(INFINITY))) {
         st |= ST_NONFINITE;  // w keeps the last finite iterate
         done = true;
-      } else {
-#pragma unroll
-        for (int a = 0; a < 5; ++a) w[a] += dw[a];
-        if (dmax <= newton_tol * fmax_(absmax5(w), T(sizeof(T) == 8 ? 1e-300 : 1e-30))) { conv = true; done = true; }
+      } else if (dmax <= newton_tol * fmax_(absmax5(w), T(sizeof(T) == 8 ? 1e-300 : 1e-30))) {
+        conv = true;
+        done = true;
       }
     }
   }

@@ -12,6 +12,7 @@
 //   MODE_FP32       FP32 only (for FP32 bulk iterations of the basic scheme).
 #pragma once
 
+#include "dfloat.cuh"
 #include "solver.cuh"
 
 namespace gsm {
@@ -77,13 +78,18 @@ AD_HD void tangent(const LawParams<T>& p, const T (&eps)[6], const T (&y)[5], co
 // Viscoplastic voxel, FP64 arithmetic.
 template <class Law>
 AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], const double (&zn)[6], const Step& hs,
-                          bool active, double (&sig)[6], double (&z)[6], double* C21) {
+                          bool active, double (&sig)[6], double (&z)[6], double* C21, const double* zprev = nullptr) {
   const double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
   double es[6];
   Law::trial_strain(eps, yn, es);
-  double w[5];
+  double w[5], w0[5];
+  if (zprev) {
+    const double yp[5] = {zprev[0], zprev[1], zprev[3], zprev[4], zprev[5]};
+#pragma unroll
+    for (int a = 0; a < 5; ++a) w0[a] = yp[a] - yn[a];
+  }
   Chol5<double> ch;
-  const unsigned st = solve_increment<Law, double>(p, es, hs, active, 1e-10, w, ch);
+  const unsigned st = solve_increment<Law, double>(p, es, hs, active, 1e-10, w, ch, zprev ? w0 : nullptr);
   double y[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) y[a] = yn[a] + w[a];
@@ -96,6 +102,70 @@ AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], co
     for (int c = 0; c < 21; ++c) C21[c] = t[c];
   }
   return st;
+}
+
+// Residual of the Norton law's implicit-Euler step (Sec. 4.1) in double-float
+// arithmetic, on the trial frame scaled by 2^-k (the frame of the FP32 solve):
+//   R_s = psi_y(e_s, w_s) + phi_v(w_s / h) = 2^-k R(e_s 2^k, w_s 2^k),
+// with the stress sigma_s = psi_eps(e_s, w_s) of the same sweep.  These are the
+// derivatives the AD sweeps of the FP64 correction give, written out for this
+// law: a = e_s - P w, tr = a0 + a1 + a2,
+//   sigma_i = lam tr + 2 mu a_i (i < 3), mu a_i (shears),
+//   psi_y = (sigma2 - sigma0, sigma2 - sigma1, -sigma3, -sigma4, -sigma5),
+//   q = 4/3 (v0^2 + v1^2 + v0 v1) + 1/3 (v2^2 + v3^2 + v4^2),  v = w/h,
+//   phi_v = a_phi c_phi q^(a_phi - 1) dq/dv.
+// The power takes the unscaled q = 2^2k q_s in FP64 (the table-driven power,
+// the one FP64-heavy step).  The factor F = a_phi c_phi q^(a_phi-1) is the
+// same in both frames and dq/dv = 2^k dq_s/dv_s, so the scaled dissipation
+// gradient is 2^-k phi_v = F dq_s/dv_s with the unscaled c_phi.
+struct NortonDf {
+  df lam, mu, inv_h;
+  double ac;     // a_phi * c_phi (unscaled)
+  double am1;    // a_phi - 1
+};
+
+AD_HD NortonDf norton_df(const LawParams<double>& p, double inv_h) {
+  return NortonDf{df_of(p.lam), df_of(p.mu), df_of(inv_h), p.a_phi * p.c_phi, p.a_phi - 1.0};
+}
+
+AD_HD void norton_residual_df(const NortonDf& c, const df (&es)[6], const df (&w)[5], int k, df (&R)[5],
+                              df (&sig)[6]) {
+  df a[6];
+  a[0] = es[0] - w[0];
+  a[1] = es[1] - w[1];
+  a[2] = es[2] + (w[0] + w[1]);
+  a[3] = es[3] - w[2];
+  a[4] = es[4] - w[3];
+  a[5] = es[5] - w[4];
+  const df ltr = c.lam * ((a[0] + a[1]) + a[2]);
+  const df mu2 = c.mu + c.mu;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) sig[i] = ltr + mu2 * a[i];
+#pragma unroll
+  for (int i = 3; i < 6; ++i) sig[i] = c.mu * a[i];
+  df v[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) v[j] = w[j] * c.inv_h;
+  // dq/dv = (4/3 (2 v0 + v1), 4/3 (2 v1 + v0), 2/3 v_j), and q = (v . dq/dv) / 2;
+  // the constants 4/3 and 2/3 in double-float (as FP32 numbers their rounding,
+  // 2^-25 relative, would enter q and phi_v)
+  df dq[5];
+  const df c43 = df_of(4.0 / 3.0), c23 = df_of(2.0 / 3.0);
+  dq[0] = (v[0] + v[0] + v[1]) * c43;
+  dq[1] = (v[1] + v[1] + v[0]) * c43;
+#pragma unroll
+  for (int j = 2; j < 5; ++j) dq[j] = v[j] * c23;
+  df q2 = v[0] * dq[0];
+#pragma unroll
+  for (int j = 1; j < 5; ++j) q2 = q2 + v[j] * dq[j];
+  // unscaled q = 2^(2k) q_s = 2^(2k) q2 / 2
+  const double q = f64_of(q2, 2 * k - 1);
+  const df F = df_of(c.ac * fpow::pow_pos(q, c.am1));
+  R[0] = (sig[2] - sig[0]) + F * dq[0];
+  R[1] = (sig[2] - sig[1]) + F * dq[1];
+  R[2] = F * dq[2] - sig[3];
+  R[3] = F * dq[3] - sig[4];
+  R[4] = F * dq[4] - sig[5];
 }
 
 // Viscoplastic voxel, FP32 bulk + FP64 correction.
@@ -112,18 +182,23 @@ AD_HD unsigned voxel_fp64(const LawParams<double>& p, const double (&eps)[6], co
 template <class Law>
 AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>& pf, const double (&eps)[6],
                               const double (&zn)[6], const Step& hs, bool active, double (&sig)[6], double (&z)[6],
-                              double* C21) {
+                              double* C21, const double* zprev = nullptr) {
   const double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
   double es[6];
   const double tr = Law::trial_strain(eps, yn, es);
   const int k = ilog2_max(es);  // s = 2^k ~ max |e_s|, applied in the conversions
-  float esf[6], wf[5];
+  float esf[6], wf[5], w0f[5];
 #pragma unroll
   for (int i = 0; i < 6; ++i) esf[i] = f32_of(es[i], -k);
+  if (zprev) {
+    const double yp[5] = {zprev[0], zprev[1], zprev[3], zprev[4], zprev[5]};
+#pragma unroll
+    for (int a = 0; a < 5; ++a) w0f[a] = f32_of(yp[a] - yn[a], -k);
+  }
   LawParams<float> ps = pf;
   const bool in_range = Law::rescale(ps, k);
   Chol5<float> chf;
-  unsigned st = solve_increment<Law, float>(ps, esf, hs, active && in_range, 1e-4f, wf, chf);
+  unsigned st = solve_increment<Law, float>(ps, esf, hs, active && in_range, 1e-4f, wf, chf, zprev ? w0f : nullptr);
   if (active && !in_range) st |= ST_CONVERGED;  // no resolvable flow (Law::rescale)
   const bool flows = absmax5(wf) > 0.0f;
   double w[5];
@@ -140,29 +215,71 @@ AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>
     double R[5];
     psi_y_and_stress<Law>(p, es, w, R, sig);
   }
-  for (int it = 0; it < 4; ++it) {
-    if (all_done(done)) break;
-    if (!done) {
-      ++n_fix;
-      double v[5], R[5], gv[5];
+  if constexpr (std::is_same<Law, NortonDev>::value) {
+    // the residual sweeps in double-float on the scaled frame (the FP32
+    // solve's); only the power and the conversions are FP64
+    if (!all_done(done)) {
+      const NortonDf c = norton_df(p, inv_h);
+      df esd[6], wd[5], sd[6];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
-      psi_y_and_stress<Law>(p, es, w, R, sig);
-      phi_v<Law>(p, v, gv);
-      float Rf[5];
+      for (int i = 0; i < 6; ++i) esd[i] = df_of(es[i], -k);
 #pragma unroll
-      for (int a = 0; a < 5; ++a) Rf[a] = f32_of(-(R[a] + gv[a]), -k);
-      chf.solve(Rf, dwf);
-      const float dmax = absmax5(dwf);
-      if (!(dmax < 1e37f)) {
-        st |= ST_NONFINITE;
-        done = true;
+      for (int a = 0; a < 5; ++a) wd[a] = df{wf[a], 0.0f};
+      for (int it = 0; it < 4; ++it) {
+        if (all_done(done)) break;
+        if (!done) {
+          ++n_fix;
+          df Rd[5];
+          norton_residual_df(c, esd, wd, k, Rd, sd);
+          float Rf[5];
 #pragma unroll
-        for (int a = 0; a < 5; ++a) dwf[a] = 0.0f;
-      } else {
+          for (int a = 0; a < 5; ++a) Rf[a] = -(Rd[a].hi + Rd[a].lo);
+          chf.solve(Rf, dwf);
+          const float dmax = absmax5(dwf);
+          if (!(dmax < 1e37f)) {
+            st |= ST_NONFINITE;
+            done = true;
 #pragma unroll
-        for (int a = 0; a < 5; ++a) w[a] += f64_of(dwf[a], k);
-        if (dmax <= 1e-6f * absmax5(wf)) { done = true; conv = true; }
+            for (int a = 0; a < 5; ++a) dwf[a] = 0.0f;
+          } else {
+#pragma unroll
+            for (int a = 0; a < 5; ++a) wd[a] = wd[a] + dwf[a];
+            if (dmax <= 1e-6f * absmax5(wf)) { done = true; conv = true; }
+          }
+        }
+      }
+      if (active && flows) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) w[a] = f64_of(wd[a], k);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sig[i] = f64_of(sd[i], k);
+      }
+    }
+  } else {
+    for (int it = 0; it < 4; ++it) {
+      if (all_done(done)) break;
+      if (!done) {
+        ++n_fix;
+        double v[5], R[5], gv[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) v[a] = w[a] * inv_h;
+        psi_y_and_stress<Law>(p, es, w, R, sig);
+        phi_v<Law>(p, v, gv);
+        float Rf[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) Rf[a] = f32_of(-(R[a] + gv[a]), -k);
+        chf.solve(Rf, dwf);
+        const float dmax = absmax5(dwf);
+        if (!(dmax < 1e37f)) {
+          st |= ST_NONFINITE;
+          done = true;
+#pragma unroll
+          for (int a = 0; a < 5; ++a) dwf[a] = 0.0f;
+        } else {
+#pragma unroll
+          for (int a = 0; a < 5; ++a) w[a] += f64_of(dwf[a], k);
+          if (dmax <= 1e-6f * absmax5(wf)) { done = true; conv = true; }
+        }
       }
     }
   }
@@ -200,7 +317,7 @@ AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>
 // Viscoplastic voxel, FP32 only (same scaled trial frame as above).
 template <class Law>
 AD_HD unsigned voxel_fp32(const LawParams<float>& pf, const float (&eps)[6], const float (&zn)[6], const Step& hs,
-                          bool active, float (&sig)[6], float (&z)[6], float* C21) {
+                          bool active, float (&sig)[6], float (&z)[6], float* C21, const float* zprev = nullptr) {
   const float yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
   float es[6];
   Law::trial_strain(eps, yn, es);
@@ -208,11 +325,17 @@ AD_HD unsigned voxel_fp32(const LawParams<float>& pf, const float (&eps)[6], con
   const float s = exp2i(k, 0.0f), inv_s = exp2i(-k, 0.0f);
 #pragma unroll
   for (int i = 0; i < 6; ++i) es[i] *= inv_s;
+  float w0[5];
+  if (zprev) {
+    const float yp[5] = {zprev[0], zprev[1], zprev[3], zprev[4], zprev[5]};
+#pragma unroll
+    for (int a = 0; a < 5; ++a) w0[a] = (yp[a] - yn[a]) * inv_s;
+  }
   LawParams<float> ps = pf;
   const bool in_range = Law::rescale(ps, k);
   float w[5];
   Chol5<float> ch;
-  unsigned st = solve_increment<Law, float>(ps, es, hs, active && in_range, 1e-6f, w, ch);
+  unsigned st = solve_increment<Law, float>(ps, es, hs, active && in_range, 1e-6f, w, ch, zprev ? w0 : nullptr);
   if (active && !in_range) st |= ST_CONVERGED;
   float y[5];
 #pragma unroll

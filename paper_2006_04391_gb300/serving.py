@@ -5,10 +5,11 @@ serving engine (``serve_submit``), which admits it when a slot and the HBM
 budget allow and advances every active job by one batched basic-scheme
 iteration per ``serve_tick``.  The driver records, per job, arrival,
 admission and completion times, and reports latency percentiles and
-throughput.  The baseline is the plain one-job-at-a-time FP64 path
-(``ms_solve`` per job, in arrival order); its latencies under the same
-arrivals follow from its measured service times by the single-server queue
-recursion c_i = max(a_i, c_{i-1}) + s_i.
+throughput.  The baselines are one-job-at-a-time paths (``ms_solve`` per
+job, in arrival order: the plain FP64 path, and the same FP32-bulk path the
+server runs); their latencies under the same arrivals follow from their
+service times by the single-server queue recursion c_i = max(a_i, c_{i-1}) +
+s_i.
 
 This module is host-side orchestration only; all arithmetic runs in the
 library's kernels.
@@ -104,6 +105,28 @@ def run_stream(G, jobs, arrivals, hbm_budget, max_active=64, ms_precision=None, 
     return {"jobs": rec, "makespan_s": makespan, "ticks": ticks, "max_active": max_seen_active,
             "jobs_per_s": n / makespan, "voxel_updates_per_s": evals / makespan,
             **{f"latency_{k}": v for k, v in percentiles([r["latency"] for r in rec]).items()}}
+
+
+def iteration_times(G, jobs, ms_precision=None, law_precision=None, n_iter=6, warm=2):
+    """Seconds per basic-scheme iteration of each job run alone through ms_run
+    (default: the plain FP64 path): ``n_iter`` forced iterations of the first
+    load step after ``warm`` untimed ones."""
+    import torch
+    ms_precision = G.MS_PREC_FP64 if ms_precision is None else ms_precision
+    law_precision = G.GSM_FP64 if law_precision is None else law_precision
+    out = []
+    for j in jobs:
+        laws = make_laws(G, j["laws"], law_precision)
+        phase = torch.from_numpy(np.ascontiguousarray(j["phase"])).cuda()
+        ctx = G.ms_create(phase, laws, ms_precision)
+        G.ms_run(ctx, j["E"][:1], j["h"][:1], forced_iters=[warm], switch_tol=1e30)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        G.ms_run(ctx, j["E"][:1], j["h"][:1], forced_iters=[n_iter], switch_tol=1e30)
+        torch.cuda.synchronize()
+        out.append((time.perf_counter() - t) / n_iter)
+        G.ms_destroy(ctx)
+    return np.array(out)
 
 
 def run_sequential(G, jobs, tol=1e-6, max_iter=20000, ms_precision=None, law_precision=None):

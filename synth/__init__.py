@@ -242,7 +242,16 @@ def unit_direction(rng):
     return d / np.linalg.norm(d)
 
 
-def serving_stream(n_jobs=64, seed=0, grids=(32, 64, 96, 128, 192), steps=(5, 20), matrix_n=(3.0, 5.0, 10.0)):
+def _stream_phase(args):
+    """Microstructure of one serving job (a process-pool task)."""
+    kind, N, frac, seed = args
+    if kind == "spheres":
+        return rsa_spheres(N, max(2.0, N / 10.0), frac, seed=seed, max_tries=20000)
+    return rsa_cylinders(N, max(1.5, N / 32.0), frac, 0.35 * N, seed=seed, max_tries=20000)
+
+
+def serving_stream(n_jobs=64, seed=0, grids=(32, 64, 96, 128, 192), steps=(5, 20), matrix_n=(3.0, 5.0, 10.0),
+                   workers=1):
     """Homogenization jobs of the serving workload.
 
     Per job: N uniform over ``grids``; microstructure RSA spheres (5-25 %,
@@ -253,25 +262,37 @@ def serving_stream(n_jobs=64, seed=0, grids=(32, 64, 96, 128, 192), steps=(5, 20
     sigma0=0.1, edot0=1) with n drawn from ``matrix_n``; inclusion E=400,
     nu=0.2; macro strain ramp along a random unit direction with amplitude
     U[1 %, 2 %] over a step count uniform in ``steps`` (inclusive), h = 0.1.
+    The microstructures (each from its own seed) are built by ``workers``
+    processes (spawned, so safe after CUDA initialisation); the result does
+    not depend on ``workers``.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    jobs = []
+    specs, jobs = [], []
     for k in range(n_jobs):
         N = int(rng.choice(grids))
         if rng.uniform() < 0.5:
-            frac = rng.uniform(0.05, 0.25)
-            ph, achieved, _ = rsa_spheres(N, max(2.0, N / 10.0), frac, seed=seed * 1000 + k, max_tries=20000)
-            kind = "spheres"
+            kind, frac = "spheres", rng.uniform(0.05, 0.25)
         else:
-            frac = rng.uniform(0.10, 0.30)
-            ph, achieved, _ = rsa_cylinders(N, max(1.5, N / 32.0), frac, 0.35 * N, seed=seed * 1000 + k,
-                                            max_tries=20000)
-            kind = "cylinders"
+            kind, frac = "cylinders", rng.uniform(0.10, 0.30)
+        specs.append((kind, N, frac, seed * 1000 + k))
         n_exp = float(rng.choice(matrix_n))
         amp = rng.uniform(0.01, 0.02)
         n_steps = int(rng.integers(steps[0], steps[1] + 1))
         E = ramp(n_steps, amp * unit_direction(rng))
-        jobs.append({"N": N, "phase": ph, "fraction": achieved, "kind": kind,
+        jobs.append({"N": N, "kind": kind,
                      "laws": [(1, (70.0, 0.3, 0.1, 1.0, n_exp)), (0, (400.0, 0.2))],
                      "E": E, "h": [0.1] * n_steps})
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        # largest grids first, so the pool's tail is short
+        order = sorted(range(n_jobs), key=lambda i: -specs[i][1])
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            built = dict(zip(order, ex.map(_stream_phase, [specs[i] for i in order])))
+        phases = [built[i] for i in range(n_jobs)]
+    else:
+        phases = [_stream_phase(sp) for sp in specs]
+    for j, (ph, achieved, _) in zip(jobs, phases):
+        j["phase"] = ph
+        j["fraction"] = achieved
     return jobs

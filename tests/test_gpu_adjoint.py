@@ -38,6 +38,22 @@ def test_adjoint_matches_oracle_adjoint(gsm):
     assert np.all(np.abs(g - g_ref) <= 1e-7 * np.abs(g_ref) + 1e-12), (g, g_ref)
 
 
+def test_adjoint_after_a_forward_run_with_the_per_step_reference(gsm):
+    """The forward run with the per-step reference medium from tangents (Sec.
+    3) converges to the same states, so its adjoint (whose equilibrium solves
+    take each step's tangent-field reference) gives the oracle adjoint."""
+    import torch
+    ph, loads, hs = setup()
+    laws = [(O.KIND_NORTON, PRM), (O.KIND_ELASTIC, synth.INCLUSION_16)]
+    r = OMS.solve_taped(ph, laws, loads, hs, tol=1e-12)
+    g_ref, _ = OMS.adjoint(ph, laws, loads, hs, r["tape"], W, 0, tol=1e-12)
+    ctx = gsm.ms_create(torch.from_numpy(ph).cuda(), [gsm.norton(*PRM), gsm.elastic(*synth.INCLUSION_16)])
+    res, tape = gsm.ms_run_taped(ctx, loads, hs, tol=1e-12, ref_update=True)
+    assert np.all(res["reference"][1:, 1] < res["reference"][0, 1])  # the matrix flows: a softer reference
+    g, its = gsm.ms_adjoint(tape, W, 0, tol=1e-12)
+    assert np.all(np.abs(g - g_ref) <= 1e-7 * np.abs(g_ref) + 1e-12), (g, g_ref)
+
+
 def test_adjoint_matches_central_differences(gsm):
     import torch
     ph, loads, hs = setup()

@@ -22,7 +22,7 @@ def glaws(G, spec, precision=0):
     return [G.norton(*p, precision=precision) if k == O.KIND_NORTON else G.elastic(*p) for k, p in spec]
 
 
-def serve_all(G, jobs, budget=8 << 30, max_active=16, precision=1, stagger=False):
+def serve_all(G, jobs, budget=8 << 30, max_active=16, precision=1, stagger=False, tol=1e-7):
     sv = G.Server(budget, max_active)
     ids = []
     done = {}
@@ -33,7 +33,7 @@ def serve_all(G, jobs, budget=8 << 30, max_active=16, precision=1, stagger=False
         if pending and (not stagger or ticks % 7 == 0):
             i = pending.pop(0)
             j = jobs[i]
-            ids.append((sv.submit(j["phase"], glaws(G, j["laws"], G.GSM_FP32_FP64FIX), j["E"], j["h"], tol=1e-7,
+            ids.append((sv.submit(j["phase"], glaws(G, j["laws"], G.GSM_FP32_FP64FIX), j["E"], j["h"], tol=tol,
                                   precision=precision), i))
         a, q, f = sv.tick()
         ticks += 1
@@ -144,3 +144,43 @@ def test_ode_law_jobs_served_with_implicit_jobs(gsm):
     with pytest.raises(gsm.GsmError):
         sv.submit(specs[0][0], ms_laws, specs[0][2], specs[0][3], precision=gsm.MS_PREC_FP64)
     sv.close()
+
+
+def test_serving_tolerance_holds_the_effective_stress(gsm):
+    """Jobs of the serving stream (32^3, 5-6 steps, n in {3, 5, 10}) served at
+    the benchmark's equilibrium tolerance 1e-4: the effective stresses are
+    within 1e-6 (relative to the largest) of the FP64 path converged to 1e-9,
+    which the parity tests hold to the oracle."""
+    import torch
+    jobs = synth.serving_stream(3, seed=21, grids=(32,), steps=(5, 6))
+    out, _ = serve_all(gsm, jobs, precision=gsm.MS_PREC_FP32_BULK, tol=1e-4)
+    for i, j in enumerate(jobs):
+        ref = gsm.ms_solve(torch.from_numpy(j["phase"]).cuda(), glaws(gsm, j["laws"]), j["E"], j["h"], tol=1e-9,
+                           max_iter=50000)
+        assert ref["rc"] == 0
+        err = np.max(np.abs(out[i]["Sigma"] - ref["Sigma"])) / np.max(np.abs(ref["Sigma"]))
+        assert err < 1e-6, (i, err)
+
+
+def test_fair_share_lets_small_jobs_pass_a_large_one(gsm):
+    """A 48^3 job submitted first and three 12^3 jobs after it: with fair-share
+    ticks the small jobs run many iterations per iteration of the large one
+    and finish first, with results bit-identical to their solo runs."""
+    big = job(48, 0.15, 5.0, [0.004, 0, 0, 0, 0, 0.002], 3, 0)
+    small = [job(12, 0.1 + 0.05 * k, 5.0, [0.002, 0.001, 0, 0, 0, 0], 2, 2 * k) for k in range(3)]
+    sv = gsm.Server(8 << 30, 8)
+    ids = [sv.submit(j["phase"], glaws(gsm, j["laws"], gsm.GSM_FP32_FP64FIX), j["E"], j["h"], tol=1e-7)
+           for j in [big] + small]
+    finished = []
+    res = {}
+    while len(finished) < 4:
+        sv.tick()
+        for jid in ids:
+            if jid not in finished and sv.state(jid)[0] in (gsm.SERVE_DONE, gsm.SERVE_DONE_NOTCONV):
+                finished.append(jid)
+                res[jid] = sv.fetch(jid)
+    sv.close()
+    assert finished[-1] == ids[0]
+    for jid, j in zip(ids[1:], small):
+        alone, _ = serve_all(gsm, [j], tol=1e-7)
+        assert np.array_equal(res[jid]["Sigma"], alone[0]["Sigma"])

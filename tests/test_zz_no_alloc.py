@@ -94,3 +94,37 @@ def test_noalloc_rejects_bad_sizes(gsm):
         rc = lib.ms_evaluate_noalloc(N, p, 1, ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), ctypes.c_double(0.1),
                                      p, p, p, p, p, None)
         assert rc == gsm.GSM_EINVAL
+
+
+def test_noalloc_call_allocates_no_device_memory(gsm):
+    """After a first call (which sets the device up), a further call leaves the
+    device's free memory and torch's reserved pool unchanged."""
+    import torch
+    lib = gsm.load()
+    N = 24
+    nvox = N ** 3
+    ph = torch.from_numpy(synth.sphere_phase(N, 0.2)).cuda()
+    laws = [gsm.norton(*synth.MATRIX_16), gsm.elastic(*synth.INCLUSION_16)]
+    arr = (ctypes.c_void_p * 2)(*[m.handle.value for m in laws])
+    eps_np, zn_np = synth.material_batch(nvox, seed=4, eps_amp=0.01, z_amp=0.002)
+    eps, zn = soa(eps_np), soa(zn_np)
+    sigma, z = torch.empty_like(eps), torch.empty_like(eps)
+    mean = torch.empty(6, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call():
+        return lib.ms_evaluate_noalloc(N, ctypes.c_void_p(ph.data_ptr()), 2,
+                                       ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), ctypes.c_double(0.1),
+                                       ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(zn.data_ptr()),
+                                       ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                       ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+
+    assert call() == 0
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    first = mean.cpu().numpy()
+    assert call() == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert np.array_equal(mean.cpu().numpy(), first)

@@ -333,16 +333,19 @@ int ms_solve(const ms_problem* prob, const ms_load* load, ms_state* state, ms_re
  * history: material update and basic scheme, discrete adjoint with per-step
  * checkpoints (the paper's AD is local to a voxel, Sec. 4.1/5; this is its
  * continuation to the homogenization run).  Backward over the steps, each
- * step solves the adjoint equilibrium P_V(C_t lam) = P_V(a_u) by the
- * basic-scheme fixed point with the consistent tangent field C_t, on the
- * isotropic reference medium at the midpoints of that field's bulk and shear
- * measures (as the forward run's per-step reference).
+ * step solves the adjoint equilibrium P_V(C_t lam) = P_V(a_u) with the
+ * consistent tangent field C_t by conjugate gradients on G C_t lam = G a_u,
+ * G the Green operator of the identity reference (the orthogonal projector
+ * onto compatible zero-mean strain fields; G C_t is symmetric positive
+ * definite there), in about the square root of the basic scheme's
+ * iterations.  A step whose CG meets a non-positive curvature falls back to
+ * the basic-scheme fixed point on the tangent field's isotropic reference.
  */
 typedef struct ms_tape* ms_tape_handle;
 
 /* ms_run_taped -- ms_run from a fresh state (no resume) that keeps the
  * checkpoints (eps_k, z_{k-1}) of every step on the device (2 * 6 * N^3
- * doubles per step) plus adjoint work arrays (53 * N^3 doubles).  The tape
+ * doubles per step) plus adjoint work arrays (71 * N^3 doubles).  The tape
  * refers to the context, which must outlive it.  Prescribed macroscopic
  * strains and the implicit-Euler update only (stress_mask = 0, integrator =
  * 0; GSM_ENOTSUP otherwise); the reference medium may be fixed or per step
@@ -354,7 +357,8 @@ int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_ha
  * weights w (host [6], tensor-shear Voigt pairing with Sigma_K) into grad
  * (host [3]).  Each adjoint equilibrium is solved until its residual falls
  * by `tol`, at most max_iter iterations (lam_iters: host [n_steps] or NULL,
- * the iterations each step took).  Synchronous.  Returns GSM_ENOTCONV, with
+ * the iterations each step took: CG iterations, or fixed-point evaluations
+ * where a step fell back).  Synchronous.  Returns GSM_ENOTCONV, with
  * grad filled, when a step reached max_iter.  Errors: GSM_EINVAL, GSM_ECUDA. */
 int ms_adjoint(ms_tape_handle tape, const double* w, int phase_id, double tol, int max_iter, double* grad,
                int32_t* lam_iters);

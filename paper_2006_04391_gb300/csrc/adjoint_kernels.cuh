@@ -324,6 +324,95 @@ __global__ void __launch_bounds__(kAdjBlock) adj_finish_kernel(
   block_sum<3>(acc, partials, gridDim.x);
 }
 
+// ---------------------------------------------- conjugate gradients (adjoint)
+// The adjoint equilibrium G (C_t lam) = G a_u on compatible zero-mean strain
+// fields, with G the Green operator of the reference C0 = identity (lam0 =
+// 0, mu0 = 1/2), which is the orthogonal projector onto those fields in the
+// tensor inner product X : Y, is symmetric positive definite there (C_t is
+// SPD, Theorem 1); conjugate gradients need about the square root of the
+// basic scheme's iterations.  On strain-like Voigt vectors (engineering
+// shears) X : Y = sum of the normal products + half the shear products.
+
+// out = C_t x (stress-like, tensor shears) for a strain-like x.
+__global__ void adj_ct_apply_kernel(int64_t nvox, const double* __restrict__ Ct21, const double* __restrict__ x,
+                                    double* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+    double l[6], C[6][6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) l[c] = x[c * nvox + i];
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) {
+        const double v = Ct21[(q++) * nvox + i];
+        C[r][c] = v;
+        C[c][r] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc += C[r][c] * l[c];
+      out[r * nvox + i] = acc;
+    }
+  }
+}
+
+// Block-wide fixed-order sum; thread 0 writes part[blockIdx.x].
+__device__ void cg_block_sum(double v, double* __restrict__ part) {
+  __shared__ double sh[kAdjBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kAdjBlock / 32; ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// part[block] = block's share of x : (ys y) for strain-like x, y.
+__global__ void __launch_bounds__(kAdjBlock) cg_dot_kernel(int64_t nvox, const double* __restrict__ x,
+                                                           const double* __restrict__ y, double ys,
+                                                           double* __restrict__ part) {
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc += (c < 3 ? 1.0 : 0.5) * x[c * nvox + i] * (ys * y[c * nvox + i]);
+  }
+  cg_block_sum(acc, part);
+}
+
+// lam += a p, r -= a (qs q); part[block] = block's share of r : r.
+__global__ void __launch_bounds__(kAdjBlock) cg_update_kernel(int64_t nvox, double a, double qs,
+                                                              const double* __restrict__ p,
+                                                              const double* __restrict__ q, double* __restrict__ lam,
+                                                              double* __restrict__ r, double* __restrict__ part) {
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int64_t k = c * nvox + i;
+      lam[k] += a * p[k];
+      const double rn = r[k] - a * (qs * q[k]);
+      r[k] = rn;
+      acc += (c < 3 ? 1.0 : 0.5) * rn * rn;
+    }
+  }
+  cg_block_sum(acc, part);
+}
+
+// p = r + b p.
+__global__ void cg_direction_kernel(int64_t n, double b, const double* __restrict__ r, double* __restrict__ p) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = r[i] + b * p[i];
+}
+
 __global__ void adj_sum_kernel(const double* __restrict__ partials, int n, double* __restrict__ out) {
   const int t = threadIdx.x;
   if (t < 3) {

@@ -1085,6 +1085,9 @@ struct Tape {
   double* yK = nullptr;    // [20][nvox]: y (5) and K upper triangle (15)
   double* gz = nullptr;    // [6][nvox]
   double* gz_prev = nullptr;
+  double* cg_lam = nullptr;  // [6][nvox] conjugate gradients: lam, residual, direction
+  double* cg_r = nullptr;
+  double* cg_p = nullptr;
   double* part = nullptr;  // [3][grid]
   double* out_dev = nullptr;
   double* out_host = nullptr;
@@ -1114,6 +1117,9 @@ int ms_run_taped(ms_handle h, const ms_load* load, ms_result* result, ms_tape_ha
             cudaMalloc((void**)&t->yK, 20 * j.nvox * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&t->gz, n6 * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&t->gz_prev, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->cg_lam, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->cg_r, n6 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&t->cg_p, n6 * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&t->part, 3 * 4096 * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&t->out_dev, 4 * sizeof(double)) == cudaSuccess &&
             cudaMallocHost((void**)&t->out_host, 4 * sizeof(double)) == cudaSuccess;
@@ -1182,34 +1188,10 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
                                                                          gs[0], gs[1], gs[2], gs[3], gs[4], gs[5],
                                                                          t.gz, t.Ct21, t.a_u, t.yK);
     count_launch();
-    // the step's reference medium for the adjoint equilibrium: midpoints of the
-    // tangent field's isotropic measures
-    double lam0 = j.lam0_el, mu0 = j.mu0_el;
-    {
-      const int rg = std::min(grid_cap(nv, kAdjBlock, 4), 1024);
-      adj_reference_kernel<<<rg, kAdjBlock, 0, s>>>(nv, t.Ct21, t.part);
-      count_launch();
-      std::vector<double> part(4 * (size_t)rg);
-      if (cudaMemcpyAsync(part.data(), t.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return GSM_ECUDA;
-      double r[4] = {1e300, -1e300, 1e300, -1e300};
-      for (int b = 0; b < rg; ++b) {
-        r[0] = std::min(r[0], part[b]);
-        r[1] = std::max(r[1], part[rg + b]);
-        r[2] = std::min(r[2], part[2 * rg + b]);
-        r[3] = std::max(r[3], part[3 * rg + b]);
-      }
-      const double k0 = 0.5 * (r[0] + r[1]), m0 = 0.5 * (r[2] + r[3]);
-      if (m0 > 0.0 && k0 > 0.0 && std::isfinite(k0 + m0)) {
-        mu0 = m0;
-        lam0 = k0 - 2.0 * m0 / 3.0;
-      }
-    }
-    // adjoint equilibrium: lam in eps_raw (N^3 lam), lam^ in eps_hat
-    cudaMemsetAsync(j.f64.eps_raw, 0, n6 * sizeof(double), s);
-    cudaMemsetAsync(j.f64.eps_hat, 0, 6 * j.nmodes * sizeof(cufftDoubleComplex), s);
+    // adjoint equilibrium by conjugate gradients on G (C_t lam) = G a_u, G the
+    // Green operator of C0 = identity (lam0 = 0, mu0 = 1/2): lam, r, p
+    // normalised in the tape's CG arrays, C_t p in sig, G (.) through sig_hat /
+    // eps_hat into eps_raw as -N^3 G (.)
     JobView& v = g.views_host[0];
     std::memset(&v, 0, sizeof v);
     v.sig_hat = j.f64.sig_hat;
@@ -1222,30 +1204,136 @@ int ms_adjoint(ms_tape_handle th, const double* w, int phase_id, double tol, int
     v.n_mch = j.n_mch;
     v.N = j.N;
     v.inv_n3 = inv_n3;
-    v.lam0 = lam0;
-    v.mu0 = mu0;
+    v.lam0 = 0.0;
+    v.mu0 = 0.5;
     cudaMemcpyAsync(g.views_dev, g.views_host, sizeof(JobView), cudaMemcpyHostToDevice, s);
     const int gam_grid = (int)std::min<int64_t>(j.n_mch, (int64_t)sm_count() * g.per_sm_gam[0]);
-    double first = -1.0;
-    int it = 0;
-    bool conv = false;
-    for (; it < max_iter; ++it) {
-      adj_tau_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.a_u, j.f64.eps_raw, inv_n3, j.f64.sig);
-      if (cufftExecD2Z(pl->r2c, j.f64.sig, j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
+    auto apply_G = [&](const double* tau) -> int {
+      if (cufftExecD2Z(pl->r2c, const_cast<double*>(tau), j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
+      cudaMemsetAsync(j.f64.eps_hat, 0, 6 * j.nmodes * sizeof(cufftDoubleComplex), s);
       ms_gamma_batch_kernel<double><<<gam_grid, kGamBlock, 0, s>>>(g.views_dev, 1, j.n_mch);
-      ms_finalize_batch_kernel<<<1, kFinBlock, 0, s>>>(g.views_dev, g.red_dev);
-      count_launch(3);
-      cudaMemcpyAsync(g.red_host, g.red_dev, sizeof(Reduced), cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
-      const double r = std::sqrt(g.red_host->res);
-      if (first < 0.0) first = r;
-      if (r <= tol * first || first == 0.0) {
-        conv = true;
-        break;
-      }
+      count_launch();
       if (cufftExecZ2D(pl->c2r, j.f64.sig_hat, j.f64.eps_raw) != CUFFT_SUCCESS) return GSM_ECUDA;
+      return GSM_OK;
+    };
+    std::vector<double> part_h(grid_fin);
+    auto reduce = [&](double* out) -> int {  // fixed-order sum of the block partials
+      if (cudaMemcpyAsync(part_h.data(), t.part, grid_fin * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return GSM_ECUDA;
+      double acc = 0.0;
+      for (int b = 0; b < grid_fin; ++b) acc += part_h[b];
+      *out = acc;
+      return GSM_OK;
+    };
+    int it = 0;
+    bool conv = false, cg_ok = true;
+    {
+      if ((rc = apply_G(t.a_u)) != GSM_OK) return rc;
+      convert<double, double>(s, j.f64.eps_raw, t.cg_r, n6, -inv_n3);
+      cudaMemcpyAsync(t.cg_p, t.cg_r, n6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaMemsetAsync(t.cg_lam, 0, n6 * sizeof(double), s);
+      double rr = 0.0;
+      cg_dot_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, t.cg_r, t.cg_r, 1.0, t.part);
+      count_launch();
+      if ((rc = reduce(&rr)) != GSM_OK) return rc;
+      const double rr0 = rr;
+      if (!(rr0 > 0.0)) conv = true;
+      while (!conv && it < max_iter) {
+        adj_ct_apply_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.cg_p, j.f64.sig);
+        count_launch();
+        if ((rc = apply_G(j.f64.sig)) != GSM_OK) return rc;
+        double pq = 0.0;
+        cg_dot_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, t.cg_p, j.f64.eps_raw, -inv_n3, t.part);
+        count_launch();
+        if ((rc = reduce(&pq)) != GSM_OK) return rc;
+        if (!(pq > 0.0) || !std::isfinite(pq)) {  // not positive definite: the fixed point below
+          cg_ok = false;
+          break;
+        }
+        const double a = rr / pq;
+        double rr_new = 0.0;
+        cg_update_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, a, -inv_n3, t.cg_p, j.f64.eps_raw, t.cg_lam, t.cg_r,
+                                                         t.part);
+        count_launch();
+        if ((rc = reduce(&rr_new)) != GSM_OK) return rc;
+        ++it;
+        if (std::sqrt(rr_new) <= tol * std::sqrt(rr0)) {
+          conv = true;
+          break;
+        }
+        cg_direction_kernel<<<elt_grid(n6), 256, 0, s>>>(n6, rr_new / rr, t.cg_r, t.cg_p);
+        count_launch();
+        rr = rr_new;
+      }
+      if (cg_ok) convert<double, double>(s, t.cg_lam, j.f64.eps_raw, n6, n3);  // N^3 lam for the finish kernel
     }
-    if (lam_iters) lam_iters[k] = conv ? it + 1 : it;
+    if (!cg_ok) {
+      it = 0;
+      conv = false;
+      // the step's reference medium for the adjoint equilibrium: midpoints of the
+      // tangent field's isotropic measures
+      double lam0 = j.lam0_el, mu0 = j.mu0_el;
+      {
+        const int rg = std::min(grid_cap(nv, kAdjBlock, 4), 1024);
+        adj_reference_kernel<<<rg, kAdjBlock, 0, s>>>(nv, t.Ct21, t.part);
+        count_launch();
+        std::vector<double> part(4 * (size_t)rg);
+        if (cudaMemcpyAsync(part.data(), t.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          return GSM_ECUDA;
+        double r[4] = {1e300, -1e300, 1e300, -1e300};
+        for (int b = 0; b < rg; ++b) {
+          r[0] = std::min(r[0], part[b]);
+          r[1] = std::max(r[1], part[rg + b]);
+          r[2] = std::min(r[2], part[2 * rg + b]);
+          r[3] = std::max(r[3], part[3 * rg + b]);
+        }
+        const double k0 = 0.5 * (r[0] + r[1]), m0 = 0.5 * (r[2] + r[3]);
+        if (m0 > 0.0 && k0 > 0.0 && std::isfinite(k0 + m0)) {
+          mu0 = m0;
+          lam0 = k0 - 2.0 * m0 / 3.0;
+        }
+      }
+      // adjoint equilibrium: lam in eps_raw (N^3 lam), lam^ in eps_hat
+      cudaMemsetAsync(j.f64.eps_raw, 0, n6 * sizeof(double), s);
+      cudaMemsetAsync(j.f64.eps_hat, 0, 6 * j.nmodes * sizeof(cufftDoubleComplex), s);
+      std::memset(&v, 0, sizeof v);
+      v.sig_hat = j.f64.sig_hat;
+      v.eps_hat = j.f64.eps_hat;
+      v.mat_part = j.mat_part;
+      v.gam_part = j.gam_part;
+      v.nvox = nv;
+      v.nmodes = j.nmodes;
+      v.n_vch = 0;
+      v.n_mch = j.n_mch;
+      v.N = j.N;
+      v.inv_n3 = inv_n3;
+      v.lam0 = lam0;
+      v.mu0 = mu0;
+      cudaMemcpyAsync(g.views_dev, g.views_host, sizeof(JobView), cudaMemcpyHostToDevice, s);
+      double first = -1.0;
+      for (; it < max_iter; ++it) {
+        adj_tau_kernel<<<elt_grid(nv), 256, 0, s>>>(nv, t.Ct21, t.a_u, j.f64.eps_raw, inv_n3, j.f64.sig);
+        if (cufftExecD2Z(pl->r2c, j.f64.sig, j.f64.sig_hat) != CUFFT_SUCCESS) return GSM_ECUDA;
+        ms_gamma_batch_kernel<double><<<gam_grid, kGamBlock, 0, s>>>(g.views_dev, 1, j.n_mch);
+        ms_finalize_batch_kernel<<<1, kFinBlock, 0, s>>>(g.views_dev, g.red_dev);
+        count_launch(3);
+        cudaMemcpyAsync(g.red_host, g.red_dev, sizeof(Reduced), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GSM_ECUDA;
+        const double r = std::sqrt(g.red_host->res);
+        if (first < 0.0) first = r;
+        if (r <= tol * first || first == 0.0) {
+          conv = true;
+          break;
+        }
+        if (cufftExecZ2D(pl->c2r, j.f64.sig_hat, j.f64.eps_raw) != CUFFT_SUCCESS) return GSM_ECUDA;
+      }
+      if (conv) ++it;  // the evaluation that met the tolerance
+    }
+    if (lam_iters) lam_iters[k] = it;
     capped = capped || !conv;
     adj_finish_kernel<<<grid_fin, kAdjBlock, 0, s>>>(nv, j.phase, j.tab_dev, hk, phase_id, nt, eps_k, zprev, gs[0],
                                                      gs[1], gs[2], gs[3], gs[4], gs[5], t.gz, j.f64.eps_raw, inv_n3,
@@ -1271,6 +1359,9 @@ int ms_tape_destroy(ms_tape_handle th) {
   cudaFree(t->yK);
   cudaFree(t->gz);
   cudaFree(t->gz_prev);
+  cudaFree(t->cg_lam);
+  cudaFree(t->cg_r);
+  cudaFree(t->cg_p);
   cudaFree(t->part);
   cudaFree(t->out_dev);
   cudaFreeHost(t->out_host);

@@ -46,6 +46,12 @@ PARAMS = (70.0, 0.3, 0.1, 1.0, 5.0)
 ALG_FLOPS = {"predictor": 41, "line": 289, "newton": 304, "residual": 67, "subst": 50, "stress": 26,
              "tangent": 449}
 ALG_POWS = {"predictor": 0, "line": 3, "newton": 3, "residual": 1, "subst": 0, "stress": 0, "tangent": 2}
+# The GPU starts its 1-D search from the root of a scalar model of the
+# segment function, which the oracle's search does not use; hand count: per
+# scalar (FP32) iteration 9 flops and 2 exponentials, and in the FP64 mode one
+# FP64 refinement step of 12 flops, a power and an exponential.
+MODEL_FLOPS, MODEL_POWS = 9, 2
+MODEL64_FLOPS, MODEL64_POWS = 12, 2
 #
 # * executed FP64 operations: each DADD, DMUL or DFMA takes one FP64 issue
 #   slot and GB300 issues two FP64 operations per SM per cycle (ncu
@@ -205,11 +211,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _status_fields(status):
+def _status_fields(status, model=False):
     import numpy as np
     line = (status & 0xFF).astype(np.float64)
     newton = ((status >> 8) & 0xFF).astype(np.float64)
     fix = ((status >> 20) & 0xF).astype(np.float64)
+    if model:
+        return line, newton, fix, ((status >> 24) & 0x7F).astype(np.float64)
     return line, newton, fix
 
 
@@ -232,15 +240,17 @@ def alg_flops_per_voxel(status, mode):
     predictor, search and Newton steps of the FP32 solve are FP32; each FP64
     correction is an FP64 residual sweep, substitutions with the FP32 factor
     (FP32) and w += dw (5 FP64 adds); the stress is FP64."""
-    line, newton, fix = _status_fields(status)
+    line, newton, fix, model = _status_fields(status, model=True)
     A, W = ALG_FLOPS, ALG_POWS
     if mode == "fp64":
-        f64 = A["predictor"] + A["line"] * line + A["newton"] * newton + A["stress"]
-        p64 = W["line"] * line + W["newton"] * newton
-        return float(f64.mean()), 0.0, float(p64.mean()), 0.0
+        step64 = model > 0
+        f64 = A["predictor"] + A["line"] * line + A["newton"] * newton + A["stress"] + MODEL64_FLOPS * step64
+        p64 = W["line"] * line + W["newton"] * newton + MODEL64_POWS * step64
+        return float(f64.mean()), float((MODEL_FLOPS * model).mean()), float(p64.mean()), \
+            float((MODEL_POWS * model).mean())
     bulk = newton - fix
-    f32 = A["predictor"] + A["line"] * line + A["newton"] * bulk + A["subst"] * fix
-    p32 = W["line"] * line + W["newton"] * bulk
+    f32 = A["predictor"] + A["line"] * line + A["newton"] * bulk + A["subst"] * fix + MODEL_FLOPS * model
+    p32 = W["line"] * line + W["newton"] * bulk + MODEL_POWS * model
     f64 = (A["residual"] + 5) * fix + A["stress"]
     p64 = W["residual"] * fix
     return float(f64.mean()), float(f32.mean()), float(p64.mean()), float(p32.mean())
@@ -336,6 +346,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e_ms = bench_e2e(G, torch, np, eps, zn, e, z0, sig, z, st, stream, world, args)
 
+    # With several ranks (the scaling run) only the headline material update
+    # and its end-to-end path run: the other blocks are single-GPU measurements.
+    if world > 1:
+        args.no_ms = args.no_serve = args.no_adjoint = args.no_ode23 = args.no_cpu = True
     ms_block = None
     if not args.no_ms and rank == 0:
         ms_block = bench_ms(G, torch, args)
@@ -841,9 +855,9 @@ def bench_serve(G, args):
       (run, wall clock on the host);
     * sequential FP64: the plain FP64 path.  Running it on the whole stream
       takes ~20-60 min (FP64 is ~17x slower per iteration on GB300), so its
-      service times are modelled: each job's FP64 time per iteration (a
-      forced run of 6 iterations, measured) x the job's iteration count in
-      the FP32-bulk run.  The model is checked against full FP64 runs of the
+      service times are modelled: each job's FP64 time per iteration (the
+      steady-state rate of forced runs of 10 and 30 iterations, measured) x the
+      job's iteration count in the FP32-bulk run.  The model is checked against full FP64 runs of the
       stream's smallest-grid jobs (their measured service times and effective
       stresses are reported).
     Latencies of the sequential arms: FIFO queue over the same arrivals.
@@ -906,6 +920,8 @@ def bench_serve(G, args):
                             "measured": "modelled: per-job FP64 s/iteration (measured) x iterations",
                             "model_check": {"jobs": len(small), "grid": int(jobs[small[0]]["N"]) if small else None,
                                             "measured_s": float(val_s.sum()), "modelled_s": float(val_model.sum()),
+                                            "fp64_iters": int(sum(int(np.sum(r["iters"])) for r in val)),
+                                            "fp32_bulk_iters": int(iters[small].sum()),
                                             "max_rel_sigma_served_vs_fp64": val_sigma}},
         "throughput_ratio": {"served_vs_sequential_fp32_bulk": served_jps / (n / float(s32.sum())),
                              "sequential_fp32_bulk_vs_fp64": float(s64.sum()) / float(s32.sum()),

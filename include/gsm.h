@@ -33,7 +33,8 @@
  *   bits 0-7 line-search iterations, bits 8-15 Newton iterations (including
  *   FP64 corrections), bit 16 converged, bit 17 non-finite input or result,
  *   bit 18 iteration cap reached, bit 19 Newton matrix not positive definite,
- *   bits 20-23 FP64 corrections (GSM_FP32_FP64FIX).
+ *   bits 20-23 FP64 corrections (GSM_FP32_FP64FIX), bits 24-30 scalar
+ *   iterations of the segment model that starts the line search.
  */
 #ifndef GSM_GB300_H
 #define GSM_GB300_H

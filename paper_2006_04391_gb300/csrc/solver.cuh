@@ -36,7 +36,41 @@ enum : unsigned {
   ST_CAP = 1u << 18,
   ST_NOT_SPD = 1u << 19,
   ST_FIX_SHIFT = 20,     // bits 20-23: FP64 corrections (FP32-bulk mode)
+  ST_MODEL_SHIFT = 24,   // bits 24-31: scalar iterations of the segment model (see solve_increment)
 };
+
+// Scalar model of the segment function g(theta) = d . R(y_n + theta d) after
+// its value and slope at theta = 1 (g1 > 0, g1') are known: psi quadratic
+// makes the psi part exactly -A (1 - theta) with A = -d . R(y_n) > 0, and a
+// dissipation gradient homogeneous of degree p (a power law: p = 1/n) makes
+// the rest B theta^p with B = g1, p = (g1' - A) / B.  The root of
+//   f(u) = B e^(p u) - A (1 - e^u),  u = ln theta,
+// by Newton from u = 0 (f convex and increasing: the iterates decrease
+// monotonically onto the root), in FP32: the start of the segment search,
+// which then needs one or two evaluations of g instead of about four.
+// Returns theta in (0, 1) and the iteration count in `iters`.
+AD_HD float segment_model_root(float A, float B, float pw, int& iters) {
+  float u = 0.0f;
+  iters = 0;
+  for (int k = 0; k < 16; ++k) {
+    ++iters;
+#if defined(__CUDA_ARCH__)
+    const float e1 = __expf(pw * u), e2 = __expf(u);
+#else
+    const float e1 = std::exp(pw * u), e2 = std::exp(u);
+#endif
+    const float f = B * e1 - A * (1.0f - e2);
+    const float fp = pw * B * e1 + A * e2;
+    const float du = -f / fp;
+    u += du;
+    if (!(du < 0.0f ? -du > 1e-7f : du > 1e-7f)) break;
+  }
+#if defined(__CUDA_ARCH__)
+  return __expf(u);
+#else
+  return std::exp(u);
+#endif
+}
 
 constexpr int kLineIterMax = 60;
 constexpr int kNewtonIterMax = 12;
@@ -588,6 +622,7 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
   // for a zero deviatoric trial stress: then there is no flow.
   T d[5];
   bool flows;
+  T A = T(0);  // -d . R(y_n): the segment function's value at theta = 0 is -A
   {
     T r0[5], Hp[5][5];
     const T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -602,7 +637,10 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
 #pragma unroll
     for (int a = 0; a < 5; ++a) mr[a] = -r0[a];
     hp.solve(mr, d);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) A += d[a] * mr[a];
   }
+  int n_model = 0;
   const T th_min = T(sizeof(T) == 8 ? 1e-140 : 1e-18) * h / fmax_(absmax5(d), T(sizeof(T) == 8 ? 1e-300 : 1e-37));
   if (!(th_min < T(1))) flows = false;
 
@@ -626,6 +664,25 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
       const T du = fin ? -g * ad::inv(theta * gp) : T(0);
       const bool small = fin && (du < T(0) ? -du : du) <= T(sizeof(T) == 8 ? 1e-12 : 1e-6);
       T tn = theta * fp64_exp_step(du);
+      if (it == 0 && fin && !small && g > T(0) && gp > A && A > T(0)) {
+        // after the evaluation at theta = 1: start from the root of the
+        // segment model (a rounding of the model stays inside the bracket)
+        const float pw = (float)((gp - A) / g);
+        const float tm = segment_model_root((float)A, (float)g, pw, n_model);
+        if (tm > 0.0f && tm < 1.0f) {
+          tn = T(tm);
+          if constexpr (sizeof(T) == 8) {
+            // one FP64 Newton step of the model (table power), so that the
+            // next evaluation of g already meets the FP64 step tolerance
+            const T pwd = (gp - A) / g;
+            const T e1 = fpow::pow_pos(tn, pwd);
+            const T f = g * e1 - A * (T(1) - tn);
+            const T fd = pwd * g * e1 + A * tn;
+            const T tr = tn * fp64_exp_step(-f / fd);
+            if (tr > T(0) && tr < T(1)) tn = tr;
+          }
+        }
+      }
       // safeguard only steps that leave the bracket; a converged step may
       // round onto a bracket end and is kept
       if (!small && !(tn > lo && tn < hi)) tn = lo > T(0) ? sqrt_pos(lo * hi) : T(0.125) * hi;
@@ -665,6 +722,7 @@ AD_HD unsigned solve_increment(const LawParams<T>& p, const T (&es)[6], const St
   if (conv) st |= ST_CONVERGED;
   st |= (unsigned)(n_line & 0xff) << ST_LINE_SHIFT;
   st |= (unsigned)(n_newton & 0xff) << ST_NEWTON_SHIFT;
+  st |= (unsigned)(n_model & 0xff) << ST_MODEL_SHIFT;
   return st;
 }
 

@@ -107,10 +107,12 @@ def run_stream(G, jobs, arrivals, hbm_budget, max_active=64, ms_precision=None, 
             **{f"latency_{k}": v for k, v in percentiles([r["latency"] for r in rec]).items()}}
 
 
-def iteration_times(G, jobs, ms_precision=None, law_precision=None, n_iter=6, warm=2):
+def iteration_times(G, jobs, ms_precision=None, law_precision=None, k0=10, k1=30, warm=2):
     """Seconds per basic-scheme iteration of each job run alone through ms_run
-    (default: the plain FP64 path): ``n_iter`` forced iterations of the first
-    load step after ``warm`` untimed ones."""
+    (default: the plain FP64 path), in the steady state of a load step: the
+    difference of forced runs of k1 and k0 iterations of the first load step
+    (after ``warm`` untimed ones), divided by k1 - k0, so that the step start
+    and the first (cold-started) evaluation drop out."""
     import torch
     ms_precision = G.MS_PREC_FP64 if ms_precision is None else ms_precision
     law_precision = G.GSM_FP64 if law_precision is None else law_precision
@@ -120,11 +122,14 @@ def iteration_times(G, jobs, ms_precision=None, law_precision=None, n_iter=6, wa
         phase = torch.from_numpy(np.ascontiguousarray(j["phase"])).cuda()
         ctx = G.ms_create(phase, laws, ms_precision)
         G.ms_run(ctx, j["E"][:1], j["h"][:1], forced_iters=[warm], switch_tol=1e30)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        G.ms_run(ctx, j["E"][:1], j["h"][:1], forced_iters=[n_iter], switch_tol=1e30)
-        torch.cuda.synchronize()
-        out.append((time.perf_counter() - t) / n_iter)
+        t = {}
+        for k in (k0, k1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.ms_run(ctx, j["E"][:1], j["h"][:1], forced_iters=[k], switch_tol=1e30)
+            torch.cuda.synchronize()
+            t[k] = time.perf_counter() - t0
+        out.append((t[k1] - t[k0]) / (k1 - k0))
         G.ms_destroy(ctx)
     return np.array(out)
 

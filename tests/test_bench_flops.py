@@ -31,3 +31,17 @@ def test_alg_flops_from_status_words():
     f64, f32, p64, p32 = bench.alg_flops_per_voxel(st, "fp32fix")
     assert f64 == A["residual"] + 5 + A["stress"] and p64 == 1
     assert f32 == A["predictor"] + 4 * A["line"] + 2 * A["newton"] + A["subst"]
+
+
+def test_alg_flops_count_the_segment_model():
+    """Bits 24-30: scalar iterations of the segment model (FP32 flops and
+    exponentials); the FP64 mode adds one FP64 refinement step."""
+    import bench
+    A = bench.ALG_FLOPS
+    st = np.array([2 | (1 << 8) | (4 << 24)], dtype=np.int32)
+    f64, f32, p64, p32 = bench.alg_flops_per_voxel(st, "fp64")
+    assert f64 == A["predictor"] + 2 * A["line"] + A["newton"] + A["stress"] + bench.MODEL64_FLOPS
+    assert f32 == 4 * bench.MODEL_FLOPS and p32 == 4 * bench.MODEL_POWS
+    st = np.array([2 | (2 << 8) | (1 << 20) | (4 << 24)], dtype=np.int32)
+    f64, f32, p64, p32 = bench.alg_flops_per_voxel(st, "fp32fix")
+    assert f32 == A["predictor"] + 2 * A["line"] + A["newton"] + A["subst"] + 4 * bench.MODEL_FLOPS

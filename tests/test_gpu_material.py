@@ -227,3 +227,21 @@ def test_host_streamed_update(gsm, precision, chunk):
         gsm.gsm_update_host(mat, d_e, h_z0, 0.01, h_s, h_z, None, None, n_vox=n)
     with pytest.raises(gsm.GsmError):
         gsm.gsm_update_host(mat, soa_pad(eps), h_z0, 0.01, h_s, h_z, None, None, n_vox=n)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_segment_model_start_needs_two_evaluations(gsm, precision):
+    """The search starts from the root of the segment model (exact for the
+    power law's homogeneous dissipation gradient): two evaluations of the
+    segment function per voxel on the benchmark distribution, a handful of
+    scalar model iterations (status bits 24-30), and the oracle's result."""
+    eps, zn = synth.material_batch(20000, seed=12)
+    for n_exp in (3.0, 5.0, 10.0):
+        prm = synth.MATRIX_16[:4] + (n_exp,)
+        s, z, st = run(gsm, gsm.norton(*prm, precision=precision), eps, zn, 0.01)
+        s_ref, z_ref = O.update(O.KIND_NORTON, prm, eps, zn, 0.01)
+        assert np.max(rel_rows(s, s_ref)) < TOL
+        line = st & 0xFF
+        model = (st >> 24) & 0x7F
+        assert line.mean() <= 2.05, (n_exp, line.mean())
+        assert 1 <= model.min() and model.max() <= 16

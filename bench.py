@@ -61,20 +61,21 @@ MODEL64_FLOPS, MODEL64_POWS = 12, 2
 #     FP32 bulk + correction (double-float residual, FP64 power): 78.15 per
 #       voxel with one correction; a further correction repeats the power and
 #       its conversions (~30, estimated; one correction is the rule);
-#     FP64: 431.5 + 158.8 per line-search iteration (one Newton step), which
-#       reproduces the three counts within 0.01 %.
+#     FP64: 806.5 per voxel at the two line-search evaluations every voxel
+#       takes since the search starts from the segment model's root; 158.8 per
+#       further evaluation (the earlier fit over three step sizes).
 #   They explain the gap between the algorithmic rate and the peak: a power
 #   (one algorithmic operation) executes as tens of FP64 operations.
 FP64_ISSUE_PER_SM_CLK = 2
 OPS_FIX_FIRST = 78.15
 OPS_FIX_EXTRA = 30.0
-OPS_FP64_BASE = 431.5
+OPS_FP64_BASE = 488.9
 OPS_FP64_LINE = 158.8
 BYTES_PER_VOXEL_FP64 = 4 * 6 * 8          # eps, z_n in; sigma, z out
 # DRAM bytes of one full-size FP32-bulk launch (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one capture of launch 6 of this workload: the
 # inputs are read once, less what the 129 MB L2 still holds)
-TRAFFIC_FP32FIX = 1476656640 + 1630654976
+TRAFFIC_FP32FIX = 1477641216 + 1630558464
 
 
 def parse():
@@ -854,12 +855,14 @@ def bench_serve(G, args):
       time), the serving engine with continuous batching and fair-share ticks
       (run, wall clock on the host);
     * sequential FP64: the plain FP64 path.  Running it on the whole stream
-      takes ~20-60 min (FP64 is ~17x slower per iteration on GB300), so its
-      service times are modelled: each job's FP64 time per iteration (the
-      steady-state rate of forced runs of 10 and 30 iterations, measured) x the
-      job's iteration count in the FP32-bulk run.  The model is checked against full FP64 runs of the
-      stream's smallest-grid jobs (their measured service times and effective
-      stresses are reported).
+      takes about two hours (an FP64 iteration costs ~20 FP32-bulk ones on
+      GB300), so its service times are modelled: each job's FP64 time per
+      iteration (the steady-state rate of forced runs of 10 and 30
+      iterations, measured) x the job's iteration count in the FP32-bulk run.
+      The model is checked against full FP64 runs of the stream's
+      smallest-grid jobs and of its 128^3 job with the fewest load steps
+      (their measured and modelled service times and effective stresses are
+      reported).
     Latencies of the sequential arms: FIFO queue over the same arrivals.
     """
     import numpy as np
@@ -888,7 +891,12 @@ def bench_serve(G, args):
     t_it64 = serving.iteration_times(G, jobs)
     iters = np.array([int(np.sum(q["iters"])) for q in seq32])
     s64 = t_it64 * iters
+    # model check: full FP64 runs of the smallest-grid jobs (host-bound iterations) and of the
+    # 128^3 job with the fewest load steps (GPU-bound iterations)
     small = [i for i, j in enumerate(jobs) if j["N"] == min(jj["N"] for jj in jobs)]
+    mid = [i for i, j in enumerate(jobs) if j["N"] == 128]
+    if mid:
+        small.append(min(mid, key=lambda i: len(jobs[i]["h"])))
     val = serving.run_sequential(G, [jobs[i] for i in small], tol=tol)
     val_s = np.array([r["service_s"] for r in val])
     val_model = s64[small]
@@ -918,8 +926,9 @@ def bench_serve(G, args):
                             "latency_p99_s": float(np.percentile(lat64, 99)),
                             "jobs_per_s": n / float(s64.sum()), "busy_s": float(s64.sum()),
                             "measured": "modelled: per-job FP64 s/iteration (measured) x iterations",
-                            "model_check": {"jobs": len(small), "grid": int(jobs[small[0]]["N"]) if small else None,
-                                            "measured_s": float(val_s.sum()), "modelled_s": float(val_model.sum()),
+                            "model_check": {"jobs": len(small), "grids": [int(jobs[i]["N"]) for i in small],
+                                            "measured_s": [float(x) for x in val_s],
+                                            "modelled_s": [float(x) for x in val_model],
                                             "fp64_iters": int(sum(int(np.sum(r["iters"])) for r in val)),
                                             "fp32_bulk_iters": int(iters[small].sum()),
                                             "max_rel_sigma_served_vs_fp64": val_sigma}},

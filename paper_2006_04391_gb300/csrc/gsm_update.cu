@@ -27,10 +27,15 @@ constexpr int kBlock = 128;
 template <class T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
 // Viscoplastic (Norton) voxels.  The FP32-bulk update without tangent is
-// held to 128 registers (4 blocks of 128 threads per SM): its FP64 and
-// double-float correction needs the warps to hide the FP64 pipe's latency.
+// held to kFixBlocks blocks of 128 threads per SM (128 registers at 4): its
+// FP64 and double-float correction needs the warps to hide the FP64 pipe's
+// latency.
+#ifndef GSM_FIX_BLOCKS
+#define GSM_FIX_BLOCKS 4
+#endif
+constexpr int kFixBlocks = GSM_FIX_BLOCKS;
 template <int MODE, bool TAN>
-__global__ void __launch_bounds__(kBlock, (MODE == MODE_FP32_FIX && !TAN) ? 4 : 1) norton_kernel(int64_t n, int64_t ld, LawParams<double> p,
+__global__ void __launch_bounds__(kBlock, (MODE == MODE_FP32_FIX && !TAN) ? kFixBlocks : 1) norton_kernel(int64_t n, int64_t ld, LawParams<double> p,
                                                         LawParams<float> pf, Step hs,
                                                         const void* __restrict__ eps_,
                                                         const void* __restrict__ zn_, void* __restrict__ sig_,

@@ -78,6 +78,22 @@ BYTES_PER_VOXEL_FP64 = 4 * 6 * 8          # eps, z_n in; sigma, z out
 TRAFFIC_FP32FIX = 1477641216 + 1630558464
 
 
+# The paper's own figures for this path (context, other hardware and workload:
+# a 150^3 short-fibre metal-matrix composite, 80 load steps, 1681 elasticity
+# iterations with implicit Euler, FP64, 2x Intel Xeon E5-2687Wv4 (24 cores)
+# + NVIDIA Quadro GV100 over PCIe, the FFT solver on the CPU; Sec. 3 and the
+# timing tables of Sec. 6).  Voxel-update rates are derived from the totals:
+# 1681 x 150^3 evaluations / the material-law time (host staging included).
+PAPER_FIGURES = {
+    "hardware": "2x Intel Xeon E5-2687Wv4 (24 cores) + NVIDIA Quadro GV100, FP64",
+    "workload": "150^3 short-fibre metal-matrix composite, 80 load steps, 1681 iterations, implicit Euler",
+    "material_law_no_tangent_automatic_s": {"cpu": 4996.7, "gpu": 257.7},
+    "material_law_no_tangent_conventional_s": {"cpu": 830.1, "gpu": 249.7},
+    "derived_voxel_updates_per_s_automatic": {"cpu": 1681 * 150 ** 3 / 4996.7, "gpu": 1681 * 150 ** 3 / 257.7},
+    "total_homogenization_automatic_with_reference_update_s": {"cpu": 6282.41, "gpu": 541.88},
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +526,7 @@ def report(args, world, rank, results, e2e_ms, ms_block, serve_block=None, adj_b
                                "executed_fp64_ops_per_voxel": fpv,
                                "issue_frac": fpv * N_VOX / t64 / 1e9 / issue_peak},
         "simt_peaks": simt or None,
+        "paper_figures": PAPER_FIGURES,
         "e2e": e2e_block(world, e2e_ms),
         "gpu_launches": r32["launches"],
         "clocks": results["clocks"],

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == MODE_FP32_FIX && !TAN) ? kFix
   IO* z = static_cast<IO*>(z_);
   IO* tan = static_cast<IO*>(tan_);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const NortonDf cdf = norton_df(p, hs.inv_h);  // formed once per thread (FP32_FIX)
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
     const bool active = i < n;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == MODE_FP32_FIX && !TAN) ? kFix
     if constexpr (MODE == MODE_FP64) {
       st = voxel_fp64<NortonDev>(p, e, zi, hs, active, s, zo, TAN ? t : nullptr);
     } else if constexpr (MODE == MODE_FP32_FIX) {
-      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, hs, active, s, zo, TAN ? t : nullptr);
+      st = voxel_fp32_fix<NortonDev>(p, pf, e, zi, hs, active, s, zo, TAN ? t : nullptr, nullptr, &cdf);
     } else {
       st = voxel_fp32<NortonDev>(pf, e, zi, hs, active, s, zo, TAN ? t : nullptr);
     }

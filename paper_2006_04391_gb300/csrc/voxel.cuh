@@ -182,7 +182,7 @@ AD_HD void norton_residual_df(const NortonDf& c, const df (&es)[6], const df (&w
 template <class Law>
 AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>& pf, const double (&eps)[6],
                               const double (&zn)[6], const Step& hs, bool active, double (&sig)[6], double (&z)[6],
-                              double* C21, const double* zprev = nullptr) {
+                              double* C21, const double* zprev = nullptr, const NortonDf* cdf = nullptr) {
   const double yn[5] = {zn[0], zn[1], zn[3], zn[4], zn[5]};
   double es[6];
   const double tr = Law::trial_strain(eps, yn, es);
@@ -219,7 +219,9 @@ AD_HD unsigned voxel_fp32_fix(const LawParams<double>& p, const LawParams<float>
     // the residual sweeps in double-float on the scaled frame (the FP32
     // solve's); only the power and the conversions are FP64
     if (!all_done(done)) {
-      const NortonDf c = norton_df(p, inv_h);
+      // the law's double-float constants (a caller that updates many voxels
+      // of one law passes them formed once)
+      const NortonDf c = cdf ? *cdf : norton_df(p, inv_h);
       df esd[6], wd[5], sd[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) esd[i] = df_of(es[i], -k);

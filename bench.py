@@ -58,7 +58,7 @@ MODEL64_FLOPS, MODEL64_POWS = 12, 2
 #   peak_sustained).  Operations per voxel, counted by ncu
 #   (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on) on this
 #   workload at three step sizes (profiles/norton_kernel_fp64_op_counts_2p20.md):
-#     FP32 bulk + correction (double-float residual, FP64 power): 78.15 per
+#     FP32 bulk + correction (double-float residual, FP64 power): 75.37 per
 #       voxel with one correction; a further correction repeats the power and
 #       its conversions (~30, estimated; one correction is the rule);
 #     FP64: 806.5 per voxel at the two line-search evaluations every voxel
@@ -67,7 +67,7 @@ MODEL64_FLOPS, MODEL64_POWS = 12, 2
 #   They explain the gap between the algorithmic rate and the peak: a power
 #   (one algorithmic operation) executes as tens of FP64 operations.
 FP64_ISSUE_PER_SM_CLK = 2
-OPS_FIX_FIRST = 78.15
+OPS_FIX_FIRST = 75.37
 OPS_FIX_EXTRA = 30.0
 OPS_FP64_BASE = 488.9
 OPS_FP64_LINE = 158.8
@@ -75,7 +75,7 @@ BYTES_PER_VOXEL_FP64 = 4 * 6 * 8          # eps, z_n in; sigma, z out
 # DRAM bytes of one full-size FP32-bulk launch (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one capture of launch 6 of this workload: the
 # inputs are read once, less what the 129 MB L2 still holds)
-TRAFFIC_FP32FIX = 1477641216 + 1630558464
+TRAFFIC_FP32FIX = 1476548608 + 1630399232
 
 
 # The paper's own figures for this path (context, other hardware and workload:

@@ -464,6 +464,56 @@ template <class A> AD_HD Unary<A, FPosPow<typename A::scalar>> pospow(const Expr
   return {a.self(), {m}};
 }
 
+// ------------------------------------------------- structural second order
+// Which tangent components can reach a leaf's adjoint in a forward-over-reverse
+// sweep, read off the expression's type: a node passes its incoming adjoint's
+// mask down, a product adds the other factor's value mask, a nonlinear unary
+// node its argument's.  For leaves seeded with unit tangents (mask 1 << k) the
+// result is the structural pattern of the Hessian row of that leaf: the sweep
+// leaves every other component at its initial -0.0.  Kernels use it to skip the
+// structural zeros of constant Hessian blocks at compile time.
+template <class V> constexpr unsigned vmask_of() {
+  if constexpr (tan_info<V>::is_tan) return tan_info<V>::mask;
+  else return 0u;
+}
+template <class E> constexpr unsigned vmask() { return vmask_of<typename E::value_type>(); }
+
+template <unsigned LM, class E> struct Reach;
+template <unsigned LM, class V> struct Reach<LM, Var<V>> {
+  static constexpr unsigned at(unsigned in) { return vmask_of<V>() == LM ? in : 0u; }
+};
+template <unsigned LM, class V> struct Reach<LM, Cst<V>> {
+  static constexpr unsigned at(unsigned) { return 0u; }
+};
+template <unsigned LM, class L, class R> struct Reach<LM, Add<L, R>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in) | Reach<LM, R>::at(in); }
+};
+template <unsigned LM, class L, class R> struct Reach<LM, Sub<L, R>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in) | Reach<LM, R>::at(in); }
+};
+template <unsigned LM, class L, class R> struct Reach<LM, Mul<L, R>> {
+  static constexpr unsigned at(unsigned in) {
+    return Reach<LM, L>::at(in | vmask<R>()) | Reach<LM, R>::at(in | vmask<L>());
+  }
+};
+template <unsigned LM, class L> struct Reach<LM, Scale<L>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in); }
+};
+template <unsigned LM, class L> struct Reach<LM, Shift<L>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in); }
+};
+template <unsigned LM, class L> struct Reach<LM, Neg<L>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in); }
+};
+template <unsigned LM, class L, class F> struct Reach<LM, Unary<L, F>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in | vmask<L>()); }
+};
+template <unsigned LM, class L> struct Reach<LM, PowN<L>> {
+  static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in | vmask<L>()); }
+};
+// Hessian row pattern of the leaf seeded 1 << k in expression E (root adjoint 1).
+template <class E, int K> constexpr unsigned hess_row() { return Reach<(1u << K), E>::at(0u); }
+
 // ---------------------------------------------------------------- leaf packs
 // A heterogeneous, fixed-size set of leaves addressed by a compile-time index:
 // leaf k may carry its own tangent mask (unit seed e_k).

@@ -142,40 +142,99 @@ template <int NY, bool TAN> struct OdeState {
   double Y[TAN ? NY : 1][TAN ? 6 : 1];
 };
 
+// Second-derivative blocks of psi: psi_ye (NY x 6), psi_yy, psi_ee, psi_ey.
+// The free energies of both laws are quadratic in (eps, y), so the blocks are
+// constants of the law: one forward-over-reverse sweep (at eps = 0, y = 0)
+// gives them for every voxel and substep, instead of one sweep per stage.
+// (For a quadratic the sweep's second-order parts do not involve the point,
+// so the blocks equal those of a sweep at the stage bit for bit.)
+template <int NY> struct PsiBlocks {
+  double Hye[NY][6], Hyy[NY][NY], Cee[6][6], Cey[6][NY];
+};
+
+template <class Law> AD_HD void psi_const_blocks(const LawParams<double>& p, PsiBlocks<Law::NY>& B) {
+  constexpr int NY = Law::NY;
+  double e0[6], y0[NY], g[NY], sig[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) e0[i] = 0.0;
+#pragma unroll
+  for (int a = 0; a < NY; ++a) y0[a] = 0.0;
+  ode_blocks<Law, true>(p, e0, y0, g, B.Hye, B.Hyy, sig, B.Cee, B.Cey);
+}
+
+// Structural pattern of the blocks, read off psi's expression type with the
+// seeds of ode_blocks (leaves eps_0..5 then y_0..NY-1): the entries it marks
+// zero are exactly -0.0 in every sweep, and the block products below skip
+// them at compile time (for the laws here it marks 9 entries of psi_ye, 7 of
+// psi_yy, 12 of the 36 of psi_ee and 9 of psi_ey; of these the lambda terms of
+// psi_ye and psi_ey cancel numerically).
+template <class Law> struct PsiPattern {
+  static constexpr int NY = Law::NY, ND = 6 + NY;
+  using EP = ad::SeededPack<ad::Var, double, ND, 0, 6>;
+  using YP = ad::SeededPack<ad::Var, double, ND, 6, NY>;
+  using Expr = decltype(Law::psi(std::declval<const EP&>(), std::declval<const YP&>(),
+                                 std::declval<const LawParams<double>&>()));
+  template <int R> static constexpr unsigned row() { return ad::hess_row<Expr, R>(); }
+  template <int A, int K> static constexpr bool hye() { return ((row<6 + A>() >> K) & 1u) != 0u; }
+  template <int A, int B> static constexpr bool hyy() { return ((row<6 + A>() >> (6 + B)) & 1u) != 0u; }
+  template <int I, int K> static constexpr bool cee() { return ((row<I>() >> K) & 1u) != 0u; }
+  template <int I, int A> static constexpr bool cey() { return ((row<I>() >> (6 + A)) & 1u) != 0u; }
+};
+
+// dA_k = -(theta psi_ye e_k + psi_yy Y e_k) over the structural non-zeros.
+template <class Law, int K, class YM>
+AD_HD void dA_column(const PsiBlocks<Law::NY>& B, double theta, const YM& Y, double (&dA)[Law::NY]) {
+  using Pat = PsiPattern<Law>;
+  ad::For<0, Law::NY>::run([&](auto ac) {
+    constexpr int a = decltype(ac)::value;
+    double t = 0.0;
+    if constexpr (Pat::template hye<a, K>()) t = theta * B.Hye[a][K];
+    ad::For<0, Law::NY>::run([&](auto bc) {
+      constexpr int b = decltype(bc)::value;
+      if constexpr (Pat::template hyy<a, b>()) t = fma(B.Hyy[a][b], Y[b][K], t);
+    });
+    dA[a] = -t;
+  });
+}
+
+// C_ik = theta psi_ee,ik + sum_a psi_ey,ia Y_ak over the structural non-zeros.
+template <class Law, int I, int K, class YM>
+AD_HD double c_entry(const PsiBlocks<Law::NY>& B, double theta, const YM& Y) {
+  using Pat = PsiPattern<Law>;
+  double t = 0.0;
+  if constexpr (Pat::template cee<I, K>()) t = theta * B.Cee[I][K];
+  ad::For<0, Law::NY>::run([&](auto ac) {
+    constexpr int a = decltype(ac)::value;
+    if constexpr (Pat::template cey<I, a>()) t = fma(B.Cey[I][a], Y[a][K], t);
+  });
+  return t;
+}
+
 // Right-hand side at theta = t/h: f = Psi_A(A), A = -psi_y, and with TAN
-// F = Psi_AA(A) dA/deps_{n+1}, dA/deps_{n+1} = -(theta psi_ye + psi_yy Y).
+// F = Psi_AA(A) dA/deps_{n+1}, dA/deps_{n+1} = -(theta psi_ye + psi_yy Y)
+// (the blocks B of psi, required with TAN).
 template <class Law, bool TAN>
 AD_HD void ode_rhs(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
                    const OdeState<Law::NY, TAN>& s, double (&f)[Law::NY],
-                   double (&F)[TAN ? Law::NY : 1][TAN ? 6 : 1]) {
+                   double (&F)[TAN ? Law::NY : 1][TAN ? 6 : 1], const PsiBlocks<Law::NY>* B = nullptr) {
   constexpr int NY = Law::NY;
   double et[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
   double A[NY];
-  if constexpr (!TAN) {
-    double g[NY];
-    ode_psi_y<Law>(p, et, s.y, g);
+  double g[NY];
+  ode_psi_y<Law>(p, et, s.y, g);
 #pragma unroll
-    for (int a = 0; a < NY; ++a) A[a] = -g[a];
+  for (int a = 0; a < NY; ++a) A[a] = -g[a];
+  if constexpr (!TAN) {
     force_a<Law>(p, A, f);
   } else {
-    double g[NY], Hye[NY][6], Hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
-    ode_blocks<Law, false>(p, et, s.y, g, Hye, Hyy, sig_, Cee_, Cey_);
-#pragma unroll
-    for (int a = 0; a < NY; ++a) A[a] = -g[a];
     double H[NY][NY];
     force_a_aa<Law>(p, A, f, H);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    ad::For<0, 6>::run([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
       double dA[NY];
-#pragma unroll
-      for (int a = 0; a < NY; ++a) {
-        double t = theta * Hye[a][k];
-#pragma unroll
-        for (int b = 0; b < NY; ++b) t = fma(Hyy[a][b], s.Y[b][k], t);
-        dA[a] = -t;
-      }
+      dA_column<Law, k>(*B, theta, s.Y, dA);
 #pragma unroll
       for (int a = 0; a < NY; ++a) {
         double t = 0.0;
@@ -183,32 +242,28 @@ AD_HD void ode_rhs(const LawParams<double>& p, const double (&epsn)[6], const do
         for (int b = 0; b < NY; ++b) t = fma(H[a][b], dA[b], t);
         F[a][k] = t;
       }
-    }
+    });
   }
 }
 
 // Stress (and with TAN the tangent C = theta psi_ee + psi_ey Y) at theta.
 template <class Law, bool TAN>
 AD_HD void ode_stress(const LawParams<double>& p, const double (&epsn)[6], const double (&de)[6], double theta,
-                      const OdeState<Law::NY, TAN>& s, double (&sig)[6], double (&C)[TAN ? 6 : 1][TAN ? 6 : 1]) {
+                      const OdeState<Law::NY, TAN>& s, double (&sig)[6], double (&C)[TAN ? 6 : 1][TAN ? 6 : 1],
+                      const PsiBlocks<Law::NY>* B = nullptr) {
   constexpr int NY = Law::NY;
   double et[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
-  if constexpr (!TAN) {
-    ode_sigma<Law>(p, et, s.y, sig);
-  } else {
-    double g_[NY], Hye_[NY][6], Hyy_[NY][NY], Cee[6][6], Cey[6][NY];
-    ode_blocks<Law, true>(p, et, s.y, g_, Hye_, Hyy_, sig, Cee, Cey);
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        double t = theta * Cee[i][k];
-#pragma unroll
-        for (int a = 0; a < NY; ++a) t = fma(Cey[i][a], s.Y[a][k], t);
-        C[i][k] = t;
-      }
+  ode_sigma<Law>(p, et, s.y, sig);
+  if constexpr (TAN) {
+    ad::For<0, 6>::run([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      ad::For<0, 6>::run([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        C[i][k] = c_entry<Law, i, k>(*B, theta, s.Y);
+      });
+    });
   }
 }
 
@@ -239,10 +294,13 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
   int n_acc, n_rej;
   unsigned flags;
   bool last_rejected, done;
+  const PsiBlocks<NY>* blk;  // psi's second-derivative blocks (with TAN)
 
-  // zn: the NZ stored internal variables (z in Voigt order, then alpha, ...)
+  // zn: the NZ stored internal variables (z in Voigt order, then alpha, ...);
+  // B: the law's blocks (psi_const_blocks), required with TAN
   AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[NZ],
-                  double h) {
+                  double h, const PsiBlocks<NY>* B = nullptr) {
+    blk = B;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       epsn[i] = e0[i];
@@ -261,8 +319,8 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
 #pragma unroll
         for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
     }
-    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, k1, K1);
-    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, k1, K1, blk);
+    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old, blk);
     t = 0.0;
     dt = h;
     n_acc = n_rej = 0;
@@ -362,7 +420,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
     }
     double k[NY];
     M56 Kc;
-    ode_rhs<Law, TAN>(p, epsn, de, th1, sE, k, Kc);
+    ode_rhs<Law, TAN>(p, epsn, de, th1, sE, k, Kc, blk);
     const double hd = 0.5 * dt;
 #pragma unroll
     for (int a = 0; a < NY; ++a) {
@@ -373,10 +431,10 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
     }
     double s_hi[6], s_lo[6];
     M66 C_hi, C_lo;
-    ode_stress<Law, TAN>(p, epsn, de, th1, sH, s_hi, C_hi);
-    ode_stress<Law, TAN>(p, epsn, de, th1, sE, s_lo, C_lo);
+    ode_stress<Law, TAN>(p, epsn, de, th1, sH, s_hi, C_hi, blk);
+    ode_stress<Law, TAN>(p, epsn, de, th1, sE, s_lo, C_lo, blk);
     const double err = pair_error(s_hi, s_lo, C_hi, C_lo, ctl);
-    ode_rhs<Law, TAN>(p, epsn, de, th1, sH, k, Kc);
+    ode_rhs<Law, TAN>(p, epsn, de, th1, sH, k, Kc, blk);
     conclude(err, tn1, clip, sH, k, Kc, s_hi, C_hi);
   }
 
@@ -411,7 +469,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
           E[a][c] = e1 * dt * K1[a][c];
         }
     }
-    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc);
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, k, Kc, blk);
     // stage 3
 #pragma unroll
     for (int a = 0; a < NY; ++a) {
@@ -426,7 +484,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
           E[a][c] = fma(e2 * dt, Kc[a][c], E[a][c]);
         }
     }
-    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc);
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.75 * dt) * inv_h, st, k, Kc, blk);
 #pragma unroll
     for (int a = 0; a < NY; ++a) {
       y3[a] = fma(b3 * dt, k[a], y3[a]);
@@ -451,7 +509,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
     }
     double k4[NY];
     M56 K4;
-    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4);
+    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, k4, K4, blk);
 #pragma unroll
     for (int a = 0; a < NY; ++a) {
       e[a] = fma(e4 * dt, k4[a], e[a]);
@@ -462,7 +520,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
     // stress pair (and tangent pair) of the two embedded solutions
     double s_hi[6], s_lo[6];
     M66 C_hi, C_lo;
-    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
+    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi, blk);
     OdeState<NY, TAN> s2;
 #pragma unroll
     for (int a = 0; a < NY; ++a) {
@@ -471,7 +529,7 @@ template <class Law, bool TAN, int PAIR = ERK_BS23> struct ErkVoxel {
 #pragma unroll
         for (int c = 0; c < 6; ++c) s2.Y[a][c] = Y3[a][c] - E[a][c];
     }
-    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
+    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo, blk);
     conclude(pair_error(s_hi, s_lo, C_hi, C_lo, ctl), tn1, clip, s3, k4, K4, s_hi, C_hi);
   }
 
@@ -684,64 +742,95 @@ template <class Law, bool TAN> struct RosVoxel {
   double F0[NY];
   M56 G0;
   double J[NY][NY], T[NY];
-  double dAdy[NY][NY], dAdt[NY];
+  // dA/dy = -psi_yy (without TAN; with TAN it is read from the law's blocks)
+  double dAdy[TAN ? 1 : NY][TAN ? 1 : NY], dAdt[NY];
   // with TAN: Psi_AA and A at the substep start, psi_ye
-  double H0[TAN ? NY : 1][TAN ? NY : 1], A0[TAN ? NY : 1], Hye[TAN ? NY : 1][TAN ? 6 : 1];
+  double H0[TAN ? NY : 1][TAN ? NY : 1], A0[TAN ? NY : 1];
   double sig_old[6];
   M66 C_old;
   double t, dt;
   int n_acc, n_rej;
   unsigned flags;
   bool last_rejected, done;
+  const PsiBlocks<NY>* blk;  // psi's second-derivative blocks (with TAN)
 
   // Psi_AA at (theta, y): J, T (and, with TAN, H0, A0).
   AD_HD void refresh(const LawParams<double>& p, double theta, double inv_h) {
     double et[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) et[i] = fma(theta, de[i], epsn[i]);
-    double g[NY], hye[NY][6], hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
-    ode_blocks<Law, false>(p, et, s.y, g, hye, hyy, sig_, Cee_, Cey_);
     double A[NY], f[NY], H[NY][NY];
-#pragma unroll
-    for (int a = 0; a < NY; ++a) A[a] = -g[a];
-    force_a_aa<Law>(p, A, f, H);
-#pragma unroll
-    for (int a = 0; a < NY; ++a) {
-#pragma unroll
-      for (int b = 0; b < NY; ++b) dAdy[a][b] = -hyy[a][b];
-      double tt = 0.0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) tt = fma(hye[a][k], de[k], tt);
-      dAdt[a] = -tt * inv_h;
-    }
-#pragma unroll
-    for (int a = 0; a < NY; ++a) {
-      double tt = 0.0;
-#pragma unroll
-      for (int b = 0; b < NY; ++b) tt = fma(H[a][b], dAdt[b], tt);
-      T[a] = tt;
-#pragma unroll
-      for (int b = 0; b < NY; ++b) {
-        double jj = 0.0;
-#pragma unroll
-        for (int c = 0; c < NY; ++c) jj = fma(H[a][c], dAdy[c][b], jj);
-        J[a][b] = jj;
-      }
-    }
     if constexpr (TAN) {
+      // psi's blocks are the law's constants (blk), their structural zeros skipped
+      using Pat = PsiPattern<Law>;
+      double g[NY];
+      ode_psi_y<Law>(p, et, s.y, g);
+#pragma unroll
+      for (int a = 0; a < NY; ++a) A[a] = -g[a];
+      force_a_aa<Law>(p, A, f, H);
+      ad::For<0, NY>::run([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        double tt = 0.0;
+        ad::For<0, 6>::run([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          if constexpr (Pat::template hye<a, k>()) tt = fma(blk->Hye[a][k], de[k], tt);
+        });
+        dAdt[a] = -tt * inv_h;
+      });
 #pragma unroll
       for (int a = 0; a < NY; ++a) {
+        double tt = 0.0;
+#pragma unroll
+        for (int b = 0; b < NY; ++b) tt = fma(H[a][b], dAdt[b], tt);
+        T[a] = tt;
+        ad::For<0, NY>::run([&](auto bc) {
+          constexpr int b = decltype(bc)::value;
+          double jj = 0.0;
+          ad::For<0, NY>::run([&](auto cc) {
+            constexpr int c = decltype(cc)::value;
+            if constexpr (Pat::template hyy<c, b>()) jj = fma(H[a][c], -blk->Hyy[c][b], jj);
+          });
+          J[a][b] = jj;
+        });
         A0[a] = A[a];
 #pragma unroll
         for (int b = 0; b < NY; ++b) H0[a][b] = H[a][b];
+      }
+    } else {
+      double g[NY], hye[NY][6], hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
+      ode_blocks<Law, false>(p, et, s.y, g, hye, hyy, sig_, Cee_, Cey_);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) Hye[a][k] = hye[a][k];
+      for (int a = 0; a < NY; ++a) A[a] = -g[a];
+      force_a_aa<Law>(p, A, f, H);
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+#pragma unroll
+        for (int b = 0; b < NY; ++b) dAdy[a][b] = -hyy[a][b];
+        double tt = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tt = fma(hye[a][k], de[k], tt);
+        dAdt[a] = -tt * inv_h;
+      }
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        double tt = 0.0;
+#pragma unroll
+        for (int b = 0; b < NY; ++b) tt = fma(H[a][b], dAdt[b], tt);
+        T[a] = tt;
+#pragma unroll
+        for (int b = 0; b < NY; ++b) {
+          double jj = 0.0;
+#pragma unroll
+          for (int c = 0; c < NY; ++c) jj = fma(H[a][c], dAdy[c][b], jj);
+          J[a][b] = jj;
+        }
       }
     }
   }
 
   AD_HD void init(const LawParams<double>& p, const double (&e0)[6], const double (&e1)[6], const double (&zn)[NZ],
-                  double h) {
+                  double h, const PsiBlocks<NY>* B = nullptr) {
+    blk = B;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       epsn[i] = e0[i];
@@ -760,8 +849,8 @@ template <class Law, bool TAN> struct RosVoxel {
 #pragma unroll
         for (int k = 0; k < 6; ++k) s.Y[a][k] = 0.0;
     }
-    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, F0, G0);
-    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old);
+    ode_rhs<Law, TAN>(p, epsn, de, 0.0, s, F0, G0, blk);
+    ode_stress<Law, TAN>(p, epsn, de, 0.0, s, sig_old, C_old, blk);
     refresh(p, 0.0, 1.0 / h);
     t = 0.0;
     dt = h;
@@ -774,14 +863,17 @@ template <class Law, bool TAN> struct RosVoxel {
   // J~_k w (column k of the tangent) into out.
   AD_HD void jtil(const LawParams<double>& p, const double (&dAk)[NY], const double (&w)[NY],
                   double (&out)[NY]) const {
+    using Pat = PsiPattern<Law>;
     double v[NY];
-#pragma unroll
-    for (int a = 0; a < NY; ++a) {
+    ad::For<0, NY>::run([&](auto ac) {
+      constexpr int a = decltype(ac)::value;
       double tt = 0.0;
-#pragma unroll
-      for (int b = 0; b < NY; ++b) tt = fma(dAdy[a][b], w[b], tt);
+      ad::For<0, NY>::run([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        if constexpr (Pat::template hyy<a, b>()) tt = fma(-blk->Hyy[a][b], w[b], tt);
+      });
       v[a] = tt;
-    }
+    });
     const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
     force_aaa<Law>(p, A, dAk, v, out);
   }
@@ -822,13 +914,15 @@ template <class Law, bool TAN> struct RosVoxel {
       // and unrolling the six columns multiplies the code and the compile time)
 #pragma unroll 1
       for (int k = 0; k < 6; ++k) {
-#pragma unroll
-        for (int a = 0; a < NY; ++a) {
-          double v = th0 * Hye[a][k];
-#pragma unroll
-          for (int b = 0; b < NY; ++b) v = fma(-dAdy[a][b], s.Y[b][k], v);  // psi_yy = -dA/dy
+        ad::For<0, NY>::run([&](auto ac) {
+          constexpr int a = decltype(ac)::value;
+          double v = th0 * blk->Hye[a][k];
+          ad::For<0, NY>::run([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            if constexpr (PsiPattern<Law>::template hyy<a, b>()) v = fma(blk->Hyy[a][b], s.Y[b][k], v);
+          });
           dA[k][a] = -v;
-        }
+        });
         double dAt[NY];
         const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
         force_aaa<Law>(p, A, dA[k], dAdt, dAt);
@@ -838,7 +932,7 @@ template <class Law, bool TAN> struct RosVoxel {
         for (int a = 0; a < NY; ++a) {
           double hh = 0.0;
 #pragma unroll
-          for (int b = 0; b < NY; ++b) hh = fma(H0[a][b], Hye[b][k], hh);
+          for (int b = 0; b < NY; ++b) hh = fma(H0[a][b], blk->Hye[b][k], hh);
           Tt[k][a] = dAt[a] - hh * inv_h;
           r[a] = G0[a][k] + hd * Tt[k][a] + hd * jk[a];
         }
@@ -850,7 +944,7 @@ template <class Law, bool TAN> struct RosVoxel {
         }
       }
     }
-    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, F1, G1);
+    ode_rhs<Law, TAN>(p, epsn, de, (t + 0.5 * dt) * inv_h, st, F1, G1, blk);
     double w2[NY];
 #pragma unroll
     for (int a = 0; a < NY; ++a) rhs[a] = F1[a] - k1[a];
@@ -880,7 +974,7 @@ template <class Law, bool TAN> struct RosVoxel {
         }
       }
     }
-    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, F2, G2);
+    ode_rhs<Law, TAN>(p, epsn, de, th1, s3, F2, G2, blk);
 #pragma unroll
     for (int a = 0; a < NY; ++a) rhs[a] = F2[a] - e32 * (k2[a] - F1[a]) - 2.0 * (k1[a] - F0[a]) + hd * T[a];
     W.solve(rhs, k3);
@@ -905,8 +999,8 @@ template <class Law, bool TAN> struct RosVoxel {
     }
     double s_hi[6], s_lo[6];
     M66 C_hi, C_lo;
-    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi);
-    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo);
+    ode_stress<Law, TAN>(p, epsn, de, th1, s3, s_hi, C_hi, blk);
+    ode_stress<Law, TAN>(p, epsn, de, th1, s2, s_lo, C_lo, blk);
     double sum = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
@@ -994,9 +1088,17 @@ AD_HD unsigned voxel_ode23(const LawParams<double>& p, const double (&epsn)[6], 
                            const double (&zn)[stored_nz<Law>()], const Step& hs, const Ode23Ctl& ctl,
                            double (&sig)[6], double (&z)[stored_nz<Law>()], double* C36) {
   OdeVoxel<Law, TAN, PAIR> v;
-  v.init(p, epsn, eps1, zn, hs.h);
-  while (!v.done) v.attempt(p, hs, ctl);
-  return v.finish(hs.h, sig, z, C36);
+  if constexpr (TAN) {
+    PsiBlocks<Law::NY> B;
+    psi_const_blocks<Law>(p, B);
+    v.init(p, epsn, eps1, zn, hs.h, &B);
+    while (!v.done) v.attempt(p, hs, ctl);
+    return v.finish(hs.h, sig, z, C36);
+  } else {
+    v.init(p, epsn, eps1, zn, hs.h);
+    while (!v.done) v.attempt(p, hs, ctl);
+    return v.finish(hs.h, sig, z, C36);
+  }
 }
 
 }  // namespace gsm

@@ -52,6 +52,12 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int NZ = stored_nz<Law>();
   OdeVoxel<Law, TAN, PAIR> v;
+  // with TAN: psi's second-derivative blocks, constants of the law, once per block
+  __shared__ PsiBlocks<Law::NY> blk;
+  if constexpr (TAN) {
+    if (threadIdx.x == 0) psi_const_blocks<Law>(p, blk);
+    __syncthreads();
+  }
   auto start = [&](int64_t k) {
     double e0[6], e1[6], zi[NZ];
 #pragma unroll
@@ -61,7 +67,7 @@ __global__ void __launch_bounds__(kOdeBlock) ode23_kernel(int64_t n, int64_t ld,
     }
 #pragma unroll
     for (int c = 0; c < NZ; ++c) zi[c] = __ldg(zn + c * ld + k);
-    v.init(p, e0, e1, zi, hs.h);
+    v.init(p, e0, e1, zi, hs.h, TAN ? &blk : nullptr);
   };
   if constexpr (TAN) {
     // with the tangent the state lives mostly in local memory (register

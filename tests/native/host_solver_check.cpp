@@ -31,6 +31,38 @@ void run_ode23(const LawParams<double>& p, int64_t n, const double* eps_n, const
   }
 }
 
+// psi's second-derivative blocks by one forward-over-reverse sweep at (eps, y)
+// and at the origin (psi_const_blocks), and their structural pattern
+// (PsiPattern): out = [Hye (NY x 6), Hyy (NY x NY), Cee (6 x 6), Cey (6 x NY)]
+// twice (at the point, at the origin); rows[r] = pattern row r (leaves
+// eps_0..5, then y_0..NY-1).
+template <class Law>
+void const_blocks_check(const LawParams<double>& p, const double* eps, const double* y, double* out, uint32_t* rows) {
+  constexpr int NY = Law::NY;
+  double e[6], yy[NY], g[NY], sig[6];
+  for (int i = 0; i < 6; ++i) e[i] = eps[i];
+  for (int a = 0; a < NY; ++a) yy[a] = y[a];
+  PsiBlocks<NY> B, B0;
+  ode_blocks<Law, true>(p, e, yy, g, B.Hye, B.Hyy, sig, B.Cee, B.Cey);
+  psi_const_blocks<Law>(p, B0);
+  const int m = NY * 6 + NY * NY + 36 + 6 * NY;
+  const PsiBlocks<NY>* src[2] = {&B, &B0};
+  for (int q = 0; q < 2; ++q) {
+    double* o = out + q * m;
+    for (int a = 0; a < NY; ++a)
+      for (int k = 0; k < 6; ++k) *o++ = src[q]->Hye[a][k];
+    for (int a = 0; a < NY; ++a)
+      for (int b = 0; b < NY; ++b) *o++ = src[q]->Hyy[a][b];
+    for (int i = 0; i < 6; ++i)
+      for (int k = 0; k < 6; ++k) *o++ = src[q]->Cee[i][k];
+    for (int i = 0; i < 6; ++i)
+      for (int a = 0; a < NY; ++a) *o++ = src[q]->Cey[i][a];
+  }
+  ad::For<0, 6 + NY>::run([&](auto rc) {
+    rows[decltype(rc)::value] = PsiPattern<Law>::template row<decltype(rc)::value>();
+  });
+}
+
 extern "C" {
 
 // params = {E, nu, sigma0, edot0, n}; fields AoS [n][6]; tangent [n][21] or NULL.
@@ -152,6 +184,14 @@ void host_psi_blocks(const double* prm, const double* eps, const double* y, doub
     for (int j = 0; j < 6; ++j) Cee[6 * i + j] = A[i][j];
     for (int j = 0; j < 5; ++j) Cey[5 * i + j] = B[i][j];
   }
+}
+
+// kind 1 Norton (NY = 5), 2 Michel-Suquet (NY = 6); see const_blocks_check.
+int host_const_blocks(int kind, const double* prm, const double* eps, const double* y, double* out, uint32_t* rows) {
+  const LawParams<double> p = make_params(prm, kind);
+  if (kind == 1) const_blocks_check<NortonDev>(p, eps, y, out, rows);
+  else const_blocks_check<MichelSuquet>(p, eps, y, out, rows);
+  return 0;
 }
 
 }  // extern "C"

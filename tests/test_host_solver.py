@@ -308,3 +308,54 @@ def test_host_ode23s_matches_oracle(hlib, tangent, kind):
         tight &= np.abs(C - C2).max(1) / np.abs(C2).max(1) < 1e-9
     assert tight.mean() >= 0.98
     assert np.all(np.abs(sig - out[0]) <= 10 * (1e-3 * np.abs(out[0]).max(1, keepdims=True) + 1e-6))
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_constant_psi_blocks_and_their_pattern(hlib, kind):
+    """The ODE tangents use psi's second-derivative blocks as constants of the
+    law: psi is quadratic in (eps, y) for both laws, so a sweep at any point
+    gives the blocks of the sweep at the origin bit for bit.  The structural
+    pattern read off the expression type must cover every non-zero entry, and
+    the blocks take the closed forms of the isotropic elastic energy
+    (psi_yy = P^T C P with z = (y0, y1, -y0-y1, y2, y3, y4), psi_ee = C)."""
+    prm = np.array(synth.MATRIX_16[:4] + (5.0,)) if kind == 1 else np.array(synth.ALUMINIUM_MS)
+    NY = 5 if kind == 1 else 6
+    E, nu = prm[0], prm[1]
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    m = NY * 6 + NY * NY + 36 + 6 * NY
+    rng = np.random.default_rng(kind)
+    for trial in range(3):
+        out = np.empty(2 * m)
+        rows = np.empty(6 + NY, dtype=np.uint32)
+        eps = rng.uniform(-0.02, 0.02, 6)
+        y = rng.uniform(-0.005, 0.005, NY)
+        hlib.host_const_blocks(kind, P(prm), P(eps), P(y), P(out), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+        B, B0 = out[:m], out[m:]
+        assert np.array_equal(B, B0)
+        o = 0
+        Hye = B[o:o + 6 * NY].reshape(NY, 6); o += 6 * NY
+        Hyy = B[o:o + NY * NY].reshape(NY, NY); o += NY * NY
+        Cee = B[o:o + 36].reshape(6, 6); o += 36
+        Cey = B[o:o + 6 * NY].reshape(6, NY)
+        full = np.zeros((6 + NY, 6 + NY))
+        full[:6, :6], full[:6, 6:], full[6:, :6], full[6:, 6:] = Cee, Cey, Hye, Hyy
+        pat = np.array([[(int(r) >> j) & 1 for j in range(6 + NY)] for r in rows])
+        assert np.all(pat[full != 0] == 1)
+        # structure: 9 / 7 / 12 / 9 marked entries (the lambda terms of psi_ye cancel numerically)
+        assert (pat[6:, :6].sum(), pat[6:, 6:].sum(), pat[:6, :6].sum(), pat[:6, 6:].sum()) == (9, 7, 12, 9)
+        Pm = np.zeros((6, NY))
+        Pm[0, 0] = Pm[1, 1] = 1.0
+        Pm[2, 0] = Pm[2, 1] = -1.0
+        Pm[3, 2] = Pm[4, 3] = Pm[5, 4] = 1.0
+        C = np.zeros((6, 6))
+        C[:3, :3] = lam
+        C[:3, :3] += 2 * mu * np.eye(3)
+        C[3:, 3:] = mu * np.eye(3)
+        Hyy_ref = Pm.T @ C @ Pm
+        if kind == 2:
+            Hyy_ref[:5, :5] += prm[3] * (2.0 / 3.0) * np.array(
+                [[2, 1, 0, 0, 0], [1, 2, 0, 0, 0], [0, 0, 0.5, 0, 0], [0, 0, 0, 0.5, 0], [0, 0, 0, 0, 0.5]])
+        assert np.allclose(Cee, C, rtol=1e-14, atol=0)
+        assert np.allclose(Cey, -C @ Pm, rtol=1e-14, atol=1e-12 * mu)
+        assert np.allclose(Hye, -(C @ Pm).T, rtol=1e-14, atol=1e-12 * mu)
+        assert np.allclose(Hyy, Hyy_ref, rtol=1e-14, atol=1e-12 * mu)

@@ -511,6 +511,35 @@ template <unsigned LM, class L, class F> struct Reach<LM, Unary<L, F>> {
 template <unsigned LM, class L> struct Reach<LM, PowN<L>> {
   static constexpr unsigned at(unsigned in) { return Reach<LM, L>::at(in | vmask<L>()); }
 };
+// Polynomial degree of an expression in its active (tangent-carrying) leaves,
+// read off its type; kNonPoly for anything a polynomial cannot express.  A
+// degree <= 2 certifies that the Hessian does not depend on the point.
+constexpr int kNonPoly = 1 << 20;
+constexpr int deg_max(int a, int b) { return a > b ? a : b; }
+constexpr int deg_mul(int a, int b) { return (a >= kNonPoly || b >= kNonPoly) ? kNonPoly : a + b; }
+template <class E> struct Degree;
+template <class V> struct Degree<Var<V>> { static constexpr int value = vmask_of<V>() ? 1 : 0; };
+template <class V> struct Degree<Cst<V>> { static constexpr int value = vmask_of<V>() ? 1 : 0; };
+template <class L, class R> struct Degree<Add<L, R>> {
+  static constexpr int value = deg_max(Degree<L>::value, Degree<R>::value);
+};
+template <class L, class R> struct Degree<Sub<L, R>> {
+  static constexpr int value = deg_max(Degree<L>::value, Degree<R>::value);
+};
+template <class L, class R> struct Degree<Mul<L, R>> {
+  static constexpr int value = deg_mul(Degree<L>::value, Degree<R>::value);
+};
+template <class L> struct Degree<Scale<L>> { static constexpr int value = Degree<L>::value; };
+template <class L> struct Degree<Shift<L>> { static constexpr int value = Degree<L>::value; };
+template <class L> struct Degree<Neg<L>> { static constexpr int value = Degree<L>::value; };
+template <class L, class T> struct Degree<Unary<L, FSq<T>>> {
+  static constexpr int value = deg_mul(Degree<L>::value, Degree<L>::value);
+};
+template <class L, class F> struct Degree<Unary<L, F>> {
+  static constexpr int value = Degree<L>::value == 0 ? 0 : kNonPoly;
+};
+template <class L> struct Degree<PowN<L>> { static constexpr int value = Degree<L>::value == 0 ? 0 : kNonPoly; };
+
 // Hessian row pattern of the leaf seeded 1 << k in expression E (root adjoint 1).
 template <class E, int K> constexpr unsigned hess_row() { return Reach<(1u << K), E>::at(0u); }
 

@@ -152,7 +152,9 @@ template <int NY> struct PsiBlocks {
   double Hye[NY][6], Hyy[NY][NY], Cee[6][6], Cey[6][NY];
 };
 
+template <class Law> struct PsiPattern;
 template <class Law> AD_HD void psi_const_blocks(const LawParams<double>& p, PsiBlocks<Law::NY>& B) {
+  static_assert(sizeof(PsiPattern<Law>) > 0, "");  // instantiates the quadratic check
   constexpr int NY = Law::NY;
   double e0[6], y0[NY], g[NY], sig[6];
 #pragma unroll
@@ -174,6 +176,8 @@ template <class Law> struct PsiPattern {
   using YP = ad::SeededPack<ad::Var, double, ND, 6, NY>;
   using Expr = decltype(Law::psi(std::declval<const EP&>(), std::declval<const YP&>(),
                                  std::declval<const LawParams<double>&>()));
+  static_assert(ad::Degree<Expr>::value <= 2,
+                "the constant-block tangent needs a free energy quadratic in (eps, y)");
   template <int R> static constexpr unsigned row() { return ad::hess_row<Expr, R>(); }
   template <int A, int K> static constexpr bool hye() { return ((row<6 + A>() >> K) & 1u) != 0u; }
   template <int A, int B> static constexpr bool hyy() { return ((row<6 + A>() >> (6 + B)) & 1u) != 0u; }
@@ -577,69 +581,89 @@ template <class Law, bool TAN> using Ode23Voxel = ErkVoxel<Law, TAN, ERK_BS23>;
 // and along u (dx = m.u_z + u_a, ds = m.u_z, dm = Q u_z / s):
 //   dH_zz = r'' dx m m^T + (r' - r/s)(dm m^T + m dm^T) + (r' dx - r ds/s) Q/s,
 //   dH_za = r'' dx m + r' dm,  dH_aa = r'' dx;  zero where x <= 0 or s = 0.
+// The factors of Psi_AAA that depend on A alone (m, 1/s and r0..r2), formed
+// once per state; apply() adds the parts along u and v.  The Rosenbrock
+// tangent applies it 24 times per substep at the substep's start state.
+template <class Law> struct ForceAAA {
+  double m[5], inv_s, r0, r1, r2;
+  bool on;  // false where x <= 0 or s = 0 (Psi_AAA = 0)
+
+  AD_HD void setup(const LawParams<double>& p, const double (&A)[Law::NY]) {
+    double MA[5];
+    MA[0] = A[0] - 0.5 * A[1];
+    MA[1] = A[1] - 0.5 * A[0];
+    MA[2] = 3.0 * A[2];
+    MA[3] = 3.0 * A[3];
+    MA[4] = 3.0 * A[4];
+    double s2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) s2 = fma(A[a], MA[a], s2);
+    const double s = sqrt(s2);
+    double x = s;
+    if constexpr (Law::kYield) x += A[5];
+    on = x > 0.0 && s > 0.0;
+    if (!on) return;
+    const double beta = Law::Psi_beta(p);
+    const double px = fpow::pow_pos(x, beta - 3.0);
+    r2 = p.c_Psi * beta * (beta - 1.0) * (beta - 2.0) * px;
+    r1 = p.c_Psi * beta * (beta - 1.0) * px * x;
+    r0 = p.c_Psi * beta * px * x * x;
+    inv_s = 1.0 / s;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) m[a] = MA[a] * inv_s;
+  }
+
+  // out = Psi_AAA[u, v]
+  AD_HD void apply(const double (&u)[Law::NY], const double (&v)[Law::NY], double (&out)[Law::NY]) const {
+    constexpr int NY = Law::NY;
+#pragma unroll
+    for (int a = 0; a < NY; ++a) out[a] = 0.0;
+    if (!on) return;
+    double Mu[5], Mv[5];
+    Mu[0] = u[0] - 0.5 * u[1];
+    Mu[1] = u[1] - 0.5 * u[0];
+    Mv[0] = v[0] - 0.5 * v[1];
+    Mv[1] = v[1] - 0.5 * v[0];
+#pragma unroll
+    for (int a = 2; a < 5; ++a) {
+      Mu[a] = 3.0 * u[a];
+      Mv[a] = 3.0 * v[a];
+    }
+    double ds = 0.0, mv = 0.0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      ds = fma(m[a], u[a], ds);
+      mv = fma(m[a], v[a], mv);
+    }
+    double dx = ds;
+    double va = 0.0;
+    if constexpr (Law::kYield) {
+      dx += u[5];
+      va = v[5];
+    }
+    // dm = Q u / s = (M u - m ds)/s;  dm.v;  Q v = M v - m mv
+    double dm[5], dmv = 0.0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      dm[a] = (Mu[a] - m[a] * ds) * inv_s;
+      dmv = fma(dm[a], v[a], dmv);
+    }
+    const double c1 = r1 - r0 * inv_s, c2 = (r1 * dx - r0 * ds * inv_s) * inv_s;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      const double Qv = Mv[a] - m[a] * mv;
+      out[a] = r2 * dx * m[a] * mv + c1 * (dm[a] * mv + m[a] * dmv) + c2 * Qv + (r2 * dx * m[a] + r1 * dm[a]) * va;
+    }
+    if constexpr (Law::kYield) out[5] = r2 * dx * mv + r1 * dmv + r2 * dx * va;
+  }
+};
+
 template <class Law>
 AD_HD void force_aaa(const LawParams<double>& p, const double (&A)[Law::NY], const double (&u)[Law::NY],
                      const double (&v)[Law::NY], double (&out)[Law::NY]) {
-  constexpr int NY = Law::NY;
-#pragma unroll
-  for (int a = 0; a < NY; ++a) out[a] = 0.0;
-  double MA[5];
-  MA[0] = A[0] - 0.5 * A[1];
-  MA[1] = A[1] - 0.5 * A[0];
-  MA[2] = 3.0 * A[2];
-  MA[3] = 3.0 * A[3];
-  MA[4] = 3.0 * A[4];
-  double s2 = 0.0;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) s2 = fma(A[a], MA[a], s2);
-  const double s = sqrt(s2);
-  double x = s;
-  if constexpr (Law::kYield) x += A[5];
-  if (!(x > 0.0) || !(s > 0.0)) return;
-  const double beta = Law::Psi_beta(p);
-  const double px = fpow::pow_pos(x, beta - 3.0);
-  const double r2 = p.c_Psi * beta * (beta - 1.0) * (beta - 2.0) * px;
-  const double r1 = p.c_Psi * beta * (beta - 1.0) * px * x;
-  const double r0 = p.c_Psi * beta * px * x * x;
-  const double inv_s = 1.0 / s;
-  double m[5], Mu[5], Mv[5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) m[a] = MA[a] * inv_s;
-  Mu[0] = u[0] - 0.5 * u[1];
-  Mu[1] = u[1] - 0.5 * u[0];
-  Mv[0] = v[0] - 0.5 * v[1];
-  Mv[1] = v[1] - 0.5 * v[0];
-#pragma unroll
-  for (int a = 2; a < 5; ++a) {
-    Mu[a] = 3.0 * u[a];
-    Mv[a] = 3.0 * v[a];
-  }
-  double ds = 0.0, mv = 0.0;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    ds = fma(m[a], u[a], ds);
-    mv = fma(m[a], v[a], mv);
-  }
-  double dx = ds;
-  double va = 0.0;
-  if constexpr (Law::kYield) {
-    dx += u[5];
-    va = v[5];
-  }
-  // dm = Q u / s = (M u - m ds)/s;  dm.v;  Q v = M v - m mv
-  double dm[5], dmv = 0.0;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    dm[a] = (Mu[a] - m[a] * ds) * inv_s;
-    dmv = fma(dm[a], v[a], dmv);
-  }
-  const double c1 = r1 - r0 * inv_s, c2 = (r1 * dx - r0 * ds * inv_s) * inv_s;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    const double Qv = Mv[a] - m[a] * mv;
-    out[a] = r2 * dx * m[a] * mv + c1 * (dm[a] * mv + m[a] * dmv) + c2 * Qv + (r2 * dx * m[a] + r1 * dm[a]) * va;
-  }
-  if constexpr (Law::kYield) out[5] = r2 * dx * mv + r1 * dmv + r2 * dx * va;
+  ForceAAA<Law> f;
+  f.setup(p, A);
+  f.apply(u, v, out);
 }
 
 // W x = b for the NY x NY matrix of a Rosenbrock stage: Gaussian elimination
@@ -745,7 +769,8 @@ template <class Law, bool TAN> struct RosVoxel {
   // dA/dy = -psi_yy (without TAN; with TAN it is read from the law's blocks)
   double dAdy[TAN ? 1 : NY][TAN ? 1 : NY], dAdt[NY];
   // with TAN: Psi_AA and A at the substep start, psi_ye
-  double H0[TAN ? NY : 1][TAN ? NY : 1], A0[TAN ? NY : 1];
+  double H0[TAN ? NY : 1][TAN ? NY : 1];
+  ForceAAA<Law> f3;  // Psi_AAA's factors at the substep start (with TAN)
   double sig_old[6];
   M66 C_old;
   double t, dt;
@@ -754,7 +779,7 @@ template <class Law, bool TAN> struct RosVoxel {
   bool last_rejected, done;
   const PsiBlocks<NY>* blk;  // psi's second-derivative blocks (with TAN)
 
-  // Psi_AA at (theta, y): J, T (and, with TAN, H0, A0).
+  // Psi_AA at (theta, y): J, T (and, with TAN, H0 and the factors of Psi_AAA).
   AD_HD void refresh(const LawParams<double>& p, double theta, double inv_h) {
     double et[6];
 #pragma unroll
@@ -792,10 +817,10 @@ template <class Law, bool TAN> struct RosVoxel {
           });
           J[a][b] = jj;
         });
-        A0[a] = A[a];
 #pragma unroll
         for (int b = 0; b < NY; ++b) H0[a][b] = H[a][b];
       }
+      f3.setup(p, A);
     } else {
       double g[NY], hye[NY][6], hyy[NY][NY], sig_[6], Cee_[6][6], Cey_[6][NY];
       ode_blocks<Law, false>(p, et, s.y, g, hye, hyy, sig_, Cee_, Cey_);
@@ -874,8 +899,7 @@ template <class Law, bool TAN> struct RosVoxel {
       });
       v[a] = tt;
     });
-    const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
-    force_aaa<Law>(p, A, dAk, v, out);
+    f3.apply(dAk, v, out);
   }
 
   AD_HD void attempt(const LawParams<double>& p, const Step& hs, const Ode23Ctl& ctl) {
@@ -924,8 +948,7 @@ template <class Law, bool TAN> struct RosVoxel {
           dA[k][a] = -v;
         });
         double dAt[NY];
-        const double(&A)[NY] = reinterpret_cast<const double(&)[NY]>(A0);
-        force_aaa<Law>(p, A, dA[k], dAdt, dAt);
+        f3.apply(dA[k], dAdt, dAt);
         double jk[NY], r[NY], col[NY];
         jtil(p, dA[k], k1, jk);
 #pragma unroll

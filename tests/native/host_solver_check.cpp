@@ -194,4 +194,9 @@ int host_const_blocks(int kind, const double* prm, const double* eps, const doub
   return 0;
 }
 
+// Polynomial degree of psi read off its expression type (kind 1 Norton, 2 Michel-Suquet).
+int host_psi_degree(int kind) {
+  return kind == 1 ? ad::Degree<PsiPattern<NortonDev>::Expr>::value : ad::Degree<PsiPattern<MichelSuquet>::Expr>::value;
+}
+
 }  // extern "C"

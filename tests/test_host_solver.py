@@ -320,6 +320,7 @@ def test_constant_psi_blocks_and_their_pattern(hlib, kind):
     (psi_yy = P^T C P with z = (y0, y1, -y0-y1, y2, y3, y4), psi_ee = C)."""
     prm = np.array(synth.MATRIX_16[:4] + (5.0,)) if kind == 1 else np.array(synth.ALUMINIUM_MS)
     NY = 5 if kind == 1 else 6
+    assert hlib.host_psi_degree(kind) == 2  # the compile-time certificate of a quadratic psi
     E, nu = prm[0], prm[1]
     lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
     m = NY * 6 + NY * NY + 36 + 6 * NY

@@ -58,17 +58,18 @@ MODEL64_FLOPS, MODEL64_POWS = 12, 2
 #   peak_sustained).  Operations per voxel, counted by ncu
 #   (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on) on this
 #   workload at three step sizes (profiles/norton_kernel_fp64_op_counts_2p20.md):
-#     FP32 bulk + correction (double-float residual, FP64 power): 75.37 per
-#       voxel with one correction; a further correction repeats the power and
-#       its conversions (~30, estimated; one correction is the rule);
+#     FP32 bulk + correction (double-float residual and power): 50.52 per
+#       voxel with one correction; a further correction repeats the power's
+#       FP64 exponent product and the conversions (~5, estimated; one
+#       correction is the rule);
 #     FP64: 806.5 per voxel at the two line-search evaluations every voxel
 #       takes since the search starts from the segment model's root; 158.8 per
 #       further evaluation (the earlier fit over three step sizes).
 #   They explain the gap between the algorithmic rate and the peak: a power
 #   (one algorithmic operation) executes as tens of FP64 operations.
 FP64_ISSUE_PER_SM_CLK = 2
-OPS_FIX_FIRST = 75.37
-OPS_FIX_EXTRA = 30.0
+OPS_FIX_FIRST = 50.52
+OPS_FIX_EXTRA = 5.0
 OPS_FP64_BASE = 488.9
 OPS_FP64_LINE = 158.8
 BYTES_PER_VOXEL_FP64 = 4 * 6 * 8          # eps, z_n in; sigma, z out

@@ -35,7 +35,7 @@ def sources():
 
 def _digest(extra_flags):
     h = hashlib.sha256()
-    files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".inc")))
     files.append(os.path.join(INCLUDE, "gsm.h"))
     for f in files:
         h.update(f.encode())

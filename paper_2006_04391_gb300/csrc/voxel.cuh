@@ -13,6 +13,7 @@
 #pragma once
 
 #include "dfloat.cuh"
+#include "dpow.cuh"
 #include "solver.cuh"
 
 namespace gsm {
@@ -122,10 +123,15 @@ struct NortonDf {
   df lam, mu, inv_h;
   double ac;     // a_phi * c_phi (unscaled)
   double am1;    // a_phi - 1
+  df am1d;       // a_phi - 1 as a pair
+  df acm;        // ac = acm 2^ace, acm in [1, 2), for the double-float power
+  int ace;
 };
 
 AD_HD NortonDf norton_df(const LawParams<double>& p, double inv_h) {
-  return NortonDf{df_of(p.lam), df_of(p.mu), df_of(inv_h), p.a_phi * p.c_phi, p.a_phi - 1.0};
+  const double ac = p.a_phi * p.c_phi, am1 = p.a_phi - 1.0;
+  const int ace = (int)((fpow::bits_of(ac) >> 52) & 0x7ff) - 1023;
+  return NortonDf{df_of(p.lam), df_of(p.mu), df_of(inv_h), ac, am1, df_of(am1), df_of(ac, -ace), ace};
 }
 
 AD_HD void norton_residual_df(const NortonDf& c, const df (&es)[6], const df (&w)[5], int k, df (&R)[5],
@@ -158,9 +164,11 @@ AD_HD void norton_residual_df(const NortonDf& c, const df (&es)[6], const df (&w
   df q2 = v[0] * dq[0];
 #pragma unroll
   for (int j = 1; j < 5; ++j) q2 = q2 + v[j] * dq[j];
-  // unscaled q = 2^(2k) q_s = 2^(2k) q2 / 2
-  const double q = f64_of(q2, 2 * k - 1);
-  const df F = df_of(c.ac * fpow::pow_pos(q, c.am1));
+  // unscaled q = 2^(2k) q_s = 2^(2k) q2 / 2; F = ac q^(a-1) by the double-float
+  // power (FP32 pipe), the FP64 power where q or F leaves its fast path
+  df F;
+  if (!dpow::pow_scaled(q2, 2 * k - 1, c.am1, c.am1d, c.acm, c.ace, F))
+    F = df_of(c.ac * fpow::pow_pos(f64_of(q2, 2 * k - 1), c.am1));
   R[0] = (sig[2] - sig[0]) + F * dq[0];
   R[1] = (sig[2] - sig[1]) + F * dq[1];
   R[2] = F * dq[2] - sig[3];

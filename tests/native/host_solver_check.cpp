@@ -6,6 +6,7 @@
 #include "../../paper_2006_04391_gb300/csrc/common.cuh"
 #include "../../paper_2006_04391_gb300/csrc/voxel.cuh"
 #include "../../paper_2006_04391_gb300/csrc/ode23.cuh"
+#include "../../paper_2006_04391_gb300/csrc/dpow.cuh"
 
 using namespace gsm;
 
@@ -197,6 +198,23 @@ int host_const_blocks(int kind, const double* prm, const double* eps, const doub
 // Polynomial degree of psi read off its expression type (kind 1 Norton, 2 Michel-Suquet).
 int host_psi_degree(int kind) {
   return kind == 1 ? ad::Degree<PsiPattern<NortonDev>::Expr>::value : ad::Degree<PsiPattern<MichelSuquet>::Expr>::value;
+}
+
+// The double-float power of the correction: F = ac (x 2^e)^a with x, a, ac
+// given as doubles and rounded to pairs here; out = {x.hi, x.lo, F.hi, F.lo}
+// (x the pair actually used).  Returns 1 on the fast path, 0 where the
+// caller would take the FP64 power.
+int host_dpow(double x, int e, double a, double ac, float* out) {
+  const df xd = df_of(x), ad = df_of(a);
+  const int ace = (int)((fpow::bits_of(ac) >> 52) & 0x7ff) - 1023;
+  const df acm = df_of(ac, -ace);
+  df F{0.0f, 0.0f};
+  const bool ok = dpow::pow_scaled(xd, e, a, ad, acm, ace, F);
+  out[0] = xd.hi;
+  out[1] = xd.lo;
+  out[2] = F.hi;
+  out[3] = F.lo;
+  return ok ? 1 : 0;
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 // Double-float power for the double-float residual of the FP32-bulk
-// correction: F = c (x 2^e)^a with x a double-float near 1 and 2^e an exact
+// correction: F = c (x 2^e)^a with x a positive double-float and 2^e an exact
 // scaling, in FP32 pairs except three FP64 operations.
 //
 // The residual's power was ~26 of the correction's ~75 FP64 operations per
@@ -21,10 +21,11 @@
 //   e^z - 1 = z + z^2/2 (pairs) + z^3/6 + z^4/24 + z^5/120 (FP32; |z| < 2^-8.4,
 //   remainder < 2^-59).
 //
-// Relative error about 2^-46 (host test against a 50-digit reference).
-// Inputs outside the fast path -- x not a positive normal pair, a result
-// exponent outside [-100, 100] -- report false; the caller takes the FP64
-// power there.
+// Relative error below 2^-45 (host test against a 40-digit reference; the
+// pairs' own rounding, 2^-48 per operation, sets it).
+// Inputs outside the fast path -- x not a positive normal pair, |a (e + E2)|
+// >= 4096, a result exponent outside [-100, 100] -- report false; the caller
+// takes the FP64 power there.
 #pragma once
 
 #include <cmath>

@@ -9,7 +9,9 @@
 // of the high parts plus the sum of the low parts, renormalised, whose error
 // is below ~2^-46 (|a| + |b|) -- relative to the operands, which is what a
 // residual that cancels to ~0 needs.  Device code uses the _rn intrinsics, so
-// no contraction into FMAs can change the error-free transformations.
+// no contraction into FMAs can change the error-free transformations; a host
+// build must not contract either (g++ -ffp-contract=off: on aarch64 g++
+// fuses a*b + c by default in C++).
 //
 // Conversions from and to FP64 go through the integer-pipe helpers f32_of /
 // f64_of of solver.cuh (an F2F conversion occupies the FP64 pipe on GB300).

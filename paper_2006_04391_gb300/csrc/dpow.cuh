@@ -93,13 +93,19 @@ AD_HD bool pow_scaled(const df& x, int e, double a64, const df& ad, const df& ac
   const df t = f * GSM_DPOW_PAIR(kDpRcp, i);
   // ln(1 + t): t - t^2/2 in pairs, t^3/3 - t^4/4 + t^5/5 - t^6/6 in FP32
   const df t2 = t * t;
+  // (the FP32 tails by explicit round-to-nearest operations, so that device
+  // and host builds give the same pairs)
   const float th = t.hi;
-  const float tail =
-      th * th * th * (0.333333333f - th * (0.25f - th * (0.2f - th * 0.166666667f)));
+  const float pt = dfo::fma_rn(-th, dfo::fma_rn(-th, dfo::fma_rn(-th, 0.166666667f, 0.2f), 0.25f), 0.333333333f);
+  const float tail = dfo::mul_rn(dfo::mul_rn(dfo::mul_rn(th, th), th), pt);
   const df ln1p = (t - df{0.5f * t2.hi, 0.5f * t2.lo}) + tail;
   const df lgm = GSM_DPOW_PAIR(kDpLog2, i) + ln1p * GSM_DPOW_PAIR(kDpConst, 0);
   // a (e + E2) in FP64, less its nearest multiple of 1/128 (n1 / 128)
+#if defined(__CUDA_ARCH__)
+  const double ae = __dmul_rn(a64, f64_of((float)(e + E2)));  // rounded, never contracted
+#else
   const double ae = a64 * f64_of((float)(e + E2));
+#endif
   const float aef = f32_of(ae);
   if (!(fabsf(aef) < 4096.0f)) return false;
   const float n1 = rintf(aef * 128.0f);
@@ -114,7 +120,8 @@ AD_HD bool pow_scaled(const df& x, int e, double a64, const df& ad, const df& ac
   const df z = r * GSM_DPOW_PAIR(kDpConst, 1);
   const df z2 = z * z;
   const float zh = z.hi;
-  const float tz = zh * zh * zh * (0.166666667f + zh * (0.0416666667f + zh * 0.00833333333f));
+  const float pz = dfo::fma_rn(zh, dfo::fma_rn(zh, 0.00833333333f, 0.0416666667f), 0.166666667f);
+  const float tz = dfo::mul_rn(dfo::mul_rn(dfo::mul_rn(zh, zh), zh), pz);
   const df em1 = (z + df{0.5f * z2.hi, 0.5f * z2.lo}) + tz;
   const int N = (int)n1 + (int)n2;
   const int j = N & 127;

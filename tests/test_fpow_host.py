@@ -19,7 +19,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 @pytest.fixture(scope="module")
 def plib(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("fpow") / "fpow.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared",
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
                     os.path.join(ROOT, "tests", "native", "fpow_check.cpp"), "-o", out], check=True)
     lib = ctypes.CDLL(out)
     return lib
@@ -66,8 +66,9 @@ def test_special_inputs(plib):
 @pytest.fixture(scope="module")
 def hlib(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("dpow") / "hsc.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I/usr/local/cuda/include",
-                    os.path.join(ROOT, "tests", "native", "host_solver_check.cpp"), "-o", out], check=True)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-I/usr/local/cuda/include", os.path.join(ROOT, "tests", "native", "host_solver_check.cpp"),
+                    "-o", out], check=True)
     lib = ctypes.CDLL(out)
     lib.host_dpow.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_float)]

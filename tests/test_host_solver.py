@@ -20,8 +20,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 @pytest.fixture(scope="module")
 def hlib(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("hsc") / "hsc.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I/usr/local/cuda/include", SRC, "-o", out],
-                   check=True)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-I/usr/local/cuda/include", SRC, "-o", out], check=True)
     return ctypes.CDLL(out)
 
 
